@@ -1,0 +1,315 @@
+"""Benchmark: canonical k-mers/s of the Turtle hot path on one GB300 (or N independent replicas).
+
+A step is one whole pass of the path (pack, extract, Bloom filter, radix sort and
+compaction, exact recount, threshold) over one synthetic library already resident
+in HBM. Default workload: the fly-shaped library (100 Mbp genome + 5% repeat
+copies, 30M x 100 bp reads, 1% substitutions, 0.05% N), k=31, min_count=2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload fly|small|longk] [--scale S]
+
+Prints one JSON line (rank 0). Under torchrun each rank counts its own replica
+library (different seed, same shape): weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "canonical k-mers/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample-reads", type=int, default=0, help="reads in the oracle sample (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name: str, scale: float, rank: int):
+    seed_shift = 1000 * rank
+    if name == "fly":
+        lib = synth.fly(seed=2 + seed_shift, scale=scale)
+        desc = "fly-shaped: %.0f Mbp genome incl. 5%% repeat copies (1-5 kb, 2-20 copies, 2%% divergence), " \
+               "%d x 100 bp reads, 1%% substitutions, 0.05%% N; k=31, min_count=2" % (lib.meta["G"] / 1e6,
+                                                                                     lib.n_reads)
+    elif name == "small":
+        lib = synth.small(seed=1 + seed_shift, scale=scale)
+        desc = "small: 1 Mbp iid genome, %d x 100 bp reads, 1%% substitutions; k=31, min_count=2" % lib.n_reads
+    else:
+        s = synth.longk(seed=3 + seed_shift, scale=scale)
+        n = s.n_reads
+        b, o = s.chunk(0, n)
+        lib = synth.Library("longk", b, o, 64, 2, dict(G=s.genome.size, n_reads=n, R=150))
+        desc = "long-k: %.0f Mbp iid genome, log-normal coverage (median 20x, sigma 1), %d x 150 bp, " \
+               "0.5%% substitutions; k=64, min_count=2" % (s.genome.size / 1e6, n)
+    return lib, desc
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(lib, sample_reads: int):
+    """The oracle as it stands, on the host cores, over the first `sample_reads` reads of the workload."""
+    import oracle
+
+    n = min(sample_reads, lib.n_reads)
+    end = int(lib.offsets[n])
+    b, o = lib.bases[:end], lib.offsets[: n + 1]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, _, nw = oracle.count(b, o, lib.k, lib.min_count, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": nw / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": "first %d reads (%d windows) of the same library, %.1f s" % (n, nw, dt)}
+
+
+def alg_bytes(stage: str, st: dict, lib) -> float:
+    """Algorithmic HBM bytes of one launch of the stage's kernel (byte model, one unit = one window)."""
+    W = st["n_windows"]
+    kw = 8 if lib.k <= 32 else 16
+    R = float(np.diff(lib.offsets[:2].astype(np.int64))[0]) if lib.n_reads else 100.0
+    packed = (R / 4.0) / max(R - lib.k + 1, 1)  # 2-bit packed read bytes per window, one pass
+    firsts = W - st["n_candidates"]
+    if stage == "filter":
+        return W * (packed + 32.0) + 32.0 * firsts + kw * st["n_candidates"]
+    if stage == "recount":
+        return W * (packed + 32.0) + 32.0 * st["n_candidates"]
+    if stage == "sort":  # one onesweep digit pass: every candidate read and written once
+        return 2.0 * kw * st["n_candidates"]
+    return 0.0
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    pkg.load()
+    lib, desc = workload(args.workload, args.scale, rank)
+    bases = torch.from_numpy(lib.bases).cuda()
+    offs = torch.from_numpy(lib.offsets.astype(np.int64)).cuda()
+    ctx = pkg.Context(dev)
+    prm = pkg.Params.default(timing=1)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(dev)
+    stage_ms = {s: [] for s in pkg.STAGES}
+    launches = 0
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)
+        st = ctx.stats()
+        launches += st["launches"]
+        for s in pkg.STAGES:
+            stage_ms[s].append(st["stage_ms"][s])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    W = st["n_windows"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(W)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_all, W_all = float(mx[0]), float(t[1])
+    else:
+        ms_all, W_all = ms, float(W)
+    value = W_all / (ms_all / 1e3)
+
+    # end to end through the host C ABI: H2D of pinned reads, whole path, D2H of the result
+    pin_b = torch.from_numpy(lib.bases).pin_memory()
+    pin_o = torch.from_numpy(lib.offsets.astype(np.uint64).view(np.int64)).pin_memory()
+    keys_n = 0
+    pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count)  # warm the default context
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        keys, counts, nw = pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count)
+        keys_n = len(counts)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e = {"value": W_all / e2e_s, "unit": METRIC,
+           "h2d_bytes_per_step": int(lib.bases.nbytes + lib.offsets.nbytes),
+           "d2h_bytes_per_step": int(keys_n * ((8 if lib.k <= 32 else 16) + 4)), "ms_per_step": e2e_s * 1e3}
+
+    # roofline of the dominant kernel, from the live per-stage CUDA events of the timed steps
+    avg = {s: float(np.mean(v)) for s, v in stage_ms.items()}
+    per_launch = {}
+    for s in ("filter", "sort", "recount"):
+        n_l = st["stage_launches"][s] if s != "sort" else max(st["sort_passes"], 1)
+        per_launch[s] = avg[s] / max(n_l, 1)
+    dom = max(("filter", "recount", "sort"), key=lambda s: avg[s])
+    hbm, src = peaks()
+    ach = alg_bytes(dom, st, lib) / (per_launch[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
+            "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+            "stage_ms": {s: round(v, 3) for s, v in avg.items()}}
+
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64" if lib.k <= 32 else "u128", "data": "synthetic",
+           "config": {"workload": desc, "k": lib.k, "min_count": lib.min_count, "windows": W,
+                      "n_reads": lib.n_reads, "bases": int(lib.bases.size), "candidates": st["n_candidates"],
+                      "unique_candidates": st["n_unique"], "reported": st["n_out"],
+                      "l2": "inputs larger than L2 (%.1f GB of reads resident)" % (lib.bases.nbytes / 1e9),
+                      "parallelism": "replicas%d" % world if world > 1 else "single"},
+           "e2e": e2e, "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+           "sort_passes": st["sort_passes"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = args.cpu_sample_reads or max(1, int(lib.n_reads * 0.1))
+        out["cpu_baseline"] = cpu_baseline(lib, sample)
+    ctx.close()
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain CPU exact counter) on host cores, bounded sample per step."""
+    lib, desc = workload(args.workload, min(args.scale, 1.0), 0)
+    sample = args.cpu_sample_reads or max(1, int(lib.n_reads * 0.05))
+    for _ in range(args.warmup):
+        cpu_baseline(lib, max(1, sample // 10))
+    vals = []
+    t_all = 0.0
+    last = None
+    for _ in range(args.steps):
+        r = cpu_baseline(lib, sample)
+        vals.append(r["value"])
+        last = r
+    v = float(np.median(vals))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64" if lib.k <= 32 else "u128", "data": "synthetic",
+            "config": {"workload": desc, "k": lib.k, "min_count": lib.min_count},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * libturtle: frequent canonical k-mer counting on one GB300 GPU (sm_103a).
+ *
+ * Method: Turtle (Roy, Bhattacharya & Schliep, arXiv:1305.1861). Given a read
+ * library and k <= 64, report every canonical k-mer seen at least min_count
+ * times, with its exact count, in ascending key order:
+ *   - a k-mer and its reverse complement are one object (Sec. 2.1.1);
+ *   - k-mers are taken from reads split at ambiguous calls, 2 bits per base,
+ *     and represented by the numerically smaller of the k-mer and its reverse
+ *     complement (Sec. 2.1.2);
+ *   - a pattern-blocked Bloom filter drops first sightings (Sec. 2.1.3);
+ *   - the survivors are sorted and compacted (Sec. 2.1.4, Alg. 1);
+ *   - an exact second pass recounts every occurrence of each survivor, so the
+ *     result is exact and independent of atomic ordering and of Bloom false
+ *     positives (the paper instead adds 1 to each count, Sec. 2.1.4).
+ *
+ * Conventions shared by every call:
+ *   Reads      read i is bases[offsets[i] .. offsets[i+1]); offsets has n_reads+1
+ *              non-decreasing entries. Bytes other than A/C/G/T/a/c/g/t are
+ *              ambiguous calls: windows containing them are skipped. Bytes
+ *              outside [offsets[0], offsets[n_reads]) belong to no read.
+ *   Encoding   A=0, C=1, G=2, T=3; the first base of a window is the most
+ *              significant 2-bit digit of the low 2k bits; complement is 3-x.
+ *   Keys       k <= 32: one uint64 per key. 33 <= k <= 64: two uint64 per key,
+ *              high word first ({hi, lo}). Keys ascend as unsigned integers.
+ *   Counts     uint32. A count that would pass 2^32-2 fails the call with
+ *              TURTLE_E_OVERFLOW.
+ *   Errors     every int-returning call returns TURTLE_OK (0) or a negative
+ *              TURTLE_E_* code and never throws or aborts. On error, outputs
+ *              hold nothing that needs freeing.
+ *   Streams    `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *              default stream). Calls are stream-ordered; calls that return
+ *              host-visible results synchronise the stream before returning.
+ *   Threads    a turtle_ctx is used by one host thread at a time; distinct
+ *              contexts may be used concurrently.
+ */
+#ifndef TURTLE_H
+#define TURTLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TURTLE_OK 0
+#define TURTLE_E_ARG (-1)       /* invalid argument (k outside 1..64, min_count 0, NULL, bad offsets) */
+#define TURTLE_E_NOMEM (-2)     /* device or host allocation failed */
+#define TURTLE_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define TURTLE_E_OVERFLOW (-4)  /* a count would not fit in uint32 */
+#define TURTLE_E_TIMEOUT (-5)   /* turtle_poll: the job did not finish in time */
+#define TURTLE_E_BUSY (-6)      /* turtle_submit: the job does not fit the server's HBM budget */
+#define TURTLE_E_DEVICE (-7)    /* a device-side check failed (bounded wait expired, table full) */
+#define TURTLE_E_NODEV (-8)     /* no CUDA device is visible */
+#define TURTLE_E_CAPACITY (-9)  /* an output buffer is too small */
+
+/* ------------------------------------------------------------------ params */
+/* Tuning knobs. None of them changes the result, only speed and memory. */
+typedef struct {
+    uint32_t struct_size;          /* sizeof(turtle_params); set by turtle_params_default */
+    float filter_bits_per_window;  /* Bloom filter bits per valid window (rounded up to a power of two
+                                      number of 32-byte sectors); default 4 */
+    uint32_t pattern_bits;         /* bits per precomputed pattern (1..64); default 4 */
+    uint32_t n_patterns;           /* pattern-table entries, power of two, 1..4096; default 1024 */
+    uint64_t pattern_seed;         /* SplitMix64 seed of the pattern table */
+    uint32_t timing;               /* 1: record per-stage CUDA events (see turtle_stats) */
+    uint32_t reserved[7];
+} turtle_params;
+
+/* Fill *p with the defaults above. */
+void turtle_params_default(turtle_params *p);
+
+/* ------------------------------------------------------------------ host-memory form */
+typedef struct {
+    const char *bases;        /* host, caller-owned */
+    const uint64_t *offsets;  /* host, n_reads + 1 entries */
+    uint64_t n_reads;
+} turtle_reads;
+
+typedef struct {
+    int k;
+    uint64_t n;          /* reported pairs */
+    uint64_t *keys;      /* host, library-allocated: n (k <= 32) or 2n (k > 32) words */
+    uint32_t *counts;    /* host, library-allocated: n */
+    uint64_t n_windows;  /* valid windows processed */
+} turtle_result;
+
+/*
+ * Count the canonical k-mers of `reads` (host memory) with count >= min_count.
+ * Copies the reads to the device, runs the whole path there and copies the
+ * result back into library-allocated host arrays owned by *out (free with
+ * turtle_result_free). Uses an internal context on the current device.
+ * min_count == 1 reports every k-mer (the Bloom filter is skipped).
+ */
+int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_result *out);
+
+/* As turtle_count, with explicit params (NULL = defaults) and stream. */
+int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
+                    void *stream, turtle_result *out);
+
+/* Free the arrays of a turtle_result (safe on a zeroed or already freed result). */
+void turtle_result_free(turtle_result *r);
+
+/* Static description of an error code. */
+const char *turtle_strerror(int code);
+
+/* ------------------------------------------------------------------ contexts and the device form */
+/* A context owns device scratch (grown on demand, kept between calls), the
+ * device result of its last call, an error word and timing events. */
+typedef struct turtle_ctx turtle_ctx;
+
+/* Create a context on CUDA device `device`. */
+int turtle_ctx_create(int device, turtle_ctx **ctx);
+/* Destroy a context and free its device memory (synchronises its last stream). */
+void turtle_ctx_destroy(turtle_ctx *ctx);
+
+typedef struct {
+    int k;
+    int key_words;           /* 1 or 2 */
+    uint64_t n;              /* reported pairs */
+    const uint64_t *keys;    /* DEVICE, owned by the context, valid until its next call */
+    const uint32_t *counts;  /* DEVICE, same ownership */
+    uint64_t n_windows;
+} turtle_device_result;
+
+/*
+ * Device-resident form: bases (n_bases bytes) and offsets (n_reads + 1 entries)
+ * are DEVICE pointers, caller-owned, left unchanged. The result stays on the
+ * device in context-owned memory (*out describes it). Synchronises `stream`.
+ */
+int turtle_count_device(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                        uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, void *stream,
+                        turtle_device_result *out);
+
+/* Stages of one turtle_count_device call, in launch order. */
+enum {
+    TURTLE_STAGE_PACK = 0,      /* ASCII -> 2-bit codes, ambiguous-call and read-start bitmaps */
+    TURTLE_STAGE_VALID,         /* valid-window bitmap and window count */
+    TURTLE_STAGE_FILTER,        /* pass 1: extraction + Bloom test-and-set + candidate emission */
+    TURTLE_STAGE_HIST,          /* radix sort: digit histograms of all passes + scan */
+    TURTLE_STAGE_SORT,          /* radix sort: onesweep digit passes */
+    TURTLE_STAGE_RLE,           /* run-length compaction of sorted candidates */
+    TURTLE_STAGE_TABLE,         /* insert unique candidates into the recount table */
+    TURTLE_STAGE_RECOUNT,       /* pass 2: extraction + exact recount */
+    TURTLE_STAGE_THRESHOLD,     /* keep count >= min_count in key order */
+    TURTLE_STAGE_COUNT
+};
+
+typedef struct {
+    uint64_t n_windows, n_candidates, n_unique, n_out;
+    uint64_t filter_bytes, table_bytes, scratch_bytes;
+    uint32_t sort_passes;                       /* LSD digit passes run (8-bit digits) */
+    uint32_t launches;                          /* kernels launched by the last call */
+    uint32_t stage_launches[TURTLE_STAGE_COUNT];
+    float stage_ms[TURTLE_STAGE_COUNT];         /* CUDA-event time per stage (params->timing) */
+} turtle_stats;
+
+/* Statistics of the context's last successful call. */
+int turtle_ctx_stats(const turtle_ctx *ctx, turtle_stats *st);
+/* Name of a stage ("pack", "valid", "filter", ...). */
+const char *turtle_stage_name(int stage);
+
+/* ------------------------------------------------------------------ per-step entry points
+ * Each runs one step of the path on caller-owned DEVICE buffers, for step-wise
+ * checking and reuse. All are stream-ordered and synchronise `stream`.
+ */
+
+/*
+ * Steps a1-a2 (Sec. 2.1.2): canonical key of every window start. For every
+ * position s in [0, n_bases): valid bit s (bit s&63 of valid[s>>6]) is 1 iff
+ * bases[s .. s+k) lies inside one read and holds no ambiguous call; then
+ * keys[s*key_words ..] is its canonical key (other entries are unspecified).
+ * keys: n_bases * key_words uint64; valid: ceil(n_bases/64) uint64.
+ * *n_windows receives the number of valid windows.
+ */
+int turtle_extract(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                   uint64_t n_reads, int k, void *stream, uint64_t *keys, uint64_t *valid, uint64_t *n_windows);
+
+/*
+ * Step a3 (Sec. 2.1.3): pattern-blocked Bloom filter on caller-owned filter
+ * words (4 * n_sectors uint64; n_sectors a power of two; zero it to start).
+ * Block = one 32-byte sector chosen by the top bits of fmix64(key) (128-bit
+ * keys: fmix64(lo ^ fmix64(hi))); the pattern (params->pattern_bits bits from a
+ * SplitMix64 table seeded by params->pattern_seed, entry = low bits of the hash)
+ * lies in the 64-bit word (hash >> 16) & 3 of the sector.
+ * set != 0: test-and-set, seen[i] = 1 iff every pattern bit was already set
+ * when key i's single atomicOr ran (order among concurrent keys unspecified).
+ * set == 0: membership test only. seen: n bytes (may be NULL when set != 0).
+ */
+int turtle_filter(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int key_words, uint64_t *filter,
+                  uint64_t n_sectors, const turtle_params *params, int set, uint8_t *seen, void *stream);
+
+/*
+ * Step a4 (Sec. 2.1.4): sort-and-compact. Sorts n keys (onesweep LSD radix
+ * sort, 8-bit digits, over the low key_bits bits; key_bits = 2k) and writes the
+ * distinct keys ascending to unique (capacity n keys) with their run lengths to
+ * counts (uint32). keys is not modified. *n_unique receives the distinct count.
+ * Scratch comes from the context.
+ */
+int turtle_sort_compact(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int key_words, int key_bits,
+                        uint64_t *unique, uint32_t *counts, uint64_t *n_unique, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TURTLE_H */

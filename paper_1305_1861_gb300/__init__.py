@@ -1,0 +1,281 @@
+"""GB300-native frequent k-mer counting (Turtle, arXiv:1305.1861).
+
+The compute path lives in ``libturtle.so`` (hand-written sm_103a CUDA kernels
+behind the C ABI declared in ``include/turtle.h``).  This package is a thin
+ctypes binding with the same names: it marshals arguments (NumPy arrays, torch
+CUDA tensors and streams to plain pointers) and raises on error codes.  Every
+step of the path runs in the library's kernels; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "TurtleError", "Params", "Context", "load", "build", "turtle_count", "turtle_strerror", "STAGES",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libturtle.so")
+_lib = None
+
+u64 = ctypes.c_uint64
+u32 = ctypes.c_uint32
+_p = ctypes.c_void_p
+
+TURTLE_OK = 0
+ERRORS = {-1: "TURTLE_E_ARG", -2: "TURTLE_E_NOMEM", -3: "TURTLE_E_CUDA", -4: "TURTLE_E_OVERFLOW",
+          -5: "TURTLE_E_TIMEOUT", -6: "TURTLE_E_BUSY", -7: "TURTLE_E_DEVICE", -8: "TURTLE_E_NODEV",
+          -9: "TURTLE_E_CAPACITY"}
+STAGES = ["pack", "valid", "filter", "hist", "sort", "rle", "table", "recount", "threshold"]
+
+
+class TurtleError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s failed: %s (%s)" % (where, ERRORS.get(code, code), turtle_strerror(code)))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("struct_size", u32), ("filter_bits_per_window", ctypes.c_float), ("pattern_bits", u32),
+                ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("reserved", u32 * 7)]
+
+    @classmethod
+    def default(cls, **kw) -> "Params":
+        p = cls()
+        load().turtle_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+
+class _Reads(ctypes.Structure):
+    _fields_ = [("bases", _p), ("offsets", _p), ("n_reads", u64)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n", u64), ("keys", ctypes.POINTER(u64)), ("counts", ctypes.POINTER(u32)),
+                ("n_windows", u64)]
+
+
+class _DeviceResult(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("key_words", ctypes.c_int), ("n", u64), ("keys", _p), ("counts", _p),
+                ("n_windows", u64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_windows", u64), ("n_candidates", u64), ("n_unique", u64), ("n_out", u64),
+                ("filter_bytes", u64), ("table_bytes", u64), ("scratch_bytes", u64), ("sort_passes", u32),
+                ("launches", u32), ("stage_launches", u32 * 9), ("stage_ms", ctypes.c_float * 9)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_launches", "stage_ms")}
+        d["stage_launches"] = {STAGES[i]: int(self.stage_launches[i]) for i in range(9)}
+        d["stage_ms"] = {STAGES[i]: float(self.stage_ms[i]) for i in range(9)}
+        return d
+
+
+def build(force: bool = False) -> str:
+    from . import _nvcc
+    return _nvcc.build(force=force)
+
+
+def load():
+    """Load libturtle.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libturtle.so not built: run paper_1305_1861_gb300.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    sig = {
+        "turtle_params_default": (None, [_p]),
+        "turtle_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "turtle_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+        "turtle_count": (ctypes.c_int, [_p, ctypes.c_int, u32, _p]),
+        "turtle_count_ex": (ctypes.c_int, [_p, ctypes.c_int, u32, _p, _p, _p]),
+        "turtle_result_free": (None, [_p]),
+        "turtle_ctx_create": (ctypes.c_int, [ctypes.c_int, _p]),
+        "turtle_ctx_destroy": (None, [_p]),
+        "turtle_ctx_stats": (ctypes.c_int, [_p, _p]),
+        "turtle_count_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p]),
+        "turtle_extract": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, _p, _p, _p, _p]),
+        "turtle_filter": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, _p, u64, _p, ctypes.c_int, _p, _p]),
+        "turtle_sort_compact": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def turtle_strerror(code: int) -> str:
+    return load().turtle_strerror(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != TURTLE_OK:
+        raise TurtleError(rc, where)
+
+
+def _np(a, dtype):
+    a = np.ascontiguousarray(a)
+    if a.dtype != dtype:
+        a = a.astype(dtype)
+    return a
+
+
+def _shape_keys(flat: np.ndarray, n: int, k: int) -> np.ndarray:
+    return flat.reshape(n, 2) if k > 32 else flat
+
+
+def turtle_count(bases, offsets, k: int, min_count: int = 2, params: Params | None = None, stream=None):
+    """Host-memory form: (keys, counts, n_windows) as NumPy arrays, keys uint64[n] or uint64[n, 2] (hi, lo)."""
+    lib = load()
+    b = _np(bases, np.uint8)
+    o = _np(offsets, np.uint64)
+    reads = _Reads(b.ctypes.data if b.size else None, o.ctypes.data, o.size - 1)
+    res = _Result()
+    rc = lib.turtle_count_ex(ctypes.byref(reads), k, min_count, ctypes.byref(params) if params else None,
+                             _stream_ptr(stream), ctypes.byref(res))
+    _check(rc, "turtle_count")
+    try:
+        w = 2 if k > 32 else 1
+        n = res.n
+        keys = np.ctypeslib.as_array(res.keys, shape=(max(n * w, 1),))[: n * w].copy() if n else \
+            np.zeros(0, dtype=np.uint64)
+        counts = np.ctypeslib.as_array(res.counts, shape=(max(n, 1),))[:n].copy() if n else np.zeros(0, np.uint32)
+        return _shape_keys(keys, n, k), counts, int(res.n_windows)
+    finally:
+        lib.turtle_result_free(ctypes.byref(res))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _CudaArray:
+    """Zero-copy view of library-owned device memory (valid until the context's next call)."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _dptr(t) -> int:
+    return t.data_ptr()
+
+
+class Context:
+    """A libturtle context on one device (owns scratch, the last device result and timing events)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        self._h = _p()
+        _check(self._lib.turtle_ctx_create(device, ctypes.byref(self._h)), "turtle_ctx_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            self._lib.turtle_ctx_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ whole path
+    def turtle_count_device(self, bases, offsets, k: int, min_count: int = 2, params: Params | None = None,
+                            stream=None):
+        """bases: CUDA uint8 tensor; offsets: CUDA int64/uint64 tensor (n_reads + 1).
+
+        Returns (keys, counts, n_windows): torch CUDA views of context-owned memory,
+        valid until this context's next call (clone them to keep them).
+        """
+        import torch
+        assert bases.is_cuda and offsets.is_cuda and bases.dtype == torch.uint8
+        assert offsets.dtype in (torch.int64, torch.uint64) and offsets.is_contiguous() and bases.is_contiguous()
+        out = _DeviceResult()
+        rc = self._lib.turtle_count_device(self._h, _dptr(bases), bases.numel(), _dptr(offsets), offsets.numel() - 1,
+                                           k, min_count, ctypes.byref(params) if params else None,
+                                           _stream_ptr(stream), ctypes.byref(out))
+        _check(rc, "turtle_count_device")
+        return self._views(out)
+
+    def _views(self, out):
+        import torch
+        n, w = int(out.n), int(out.key_words)
+        if n == 0:
+            return (torch.zeros((0, 2) if w == 2 else (0,), dtype=torch.int64, device="cuda"),
+                    torch.zeros(0, dtype=torch.int32, device="cuda"), int(out.n_windows))
+        keys = torch.as_tensor(_CudaArray(out.keys, (n, 2) if w == 2 else (n,), "<i8", self), device="cuda")
+        counts = torch.as_tensor(_CudaArray(out.counts, (n,), "<i4", self), device="cuda")
+        return keys, counts, int(out.n_windows)
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self._lib.turtle_ctx_stats(self._h, ctypes.byref(st)), "turtle_ctx_stats")
+        return st.as_dict()
+
+    # ------------------------------------------------------------ per-step entry points
+    def turtle_extract(self, bases, offsets, k: int, stream=None):
+        """(keys [n_bases(, 2)] int64 CUDA, valid bitmap [ceil(n/64)] int64 CUDA, n_windows)."""
+        import torch
+        n = bases.numel()
+        w = 2 if k > 32 else 1
+        keys = torch.empty((n, 2) if w == 2 else (n,), dtype=torch.int64, device=bases.device)
+        valid = torch.zeros((n + 63) // 64, dtype=torch.int64, device=bases.device)
+        nw = u64()
+        rc = self._lib.turtle_extract(self._h, _dptr(bases), n, _dptr(offsets), offsets.numel() - 1, k,
+                                      _stream_ptr(stream), _dptr(keys), _dptr(valid), ctypes.byref(nw))
+        _check(rc, "turtle_extract")
+        return keys, valid, int(nw.value)
+
+    def turtle_filter(self, keys, filter_words, n_sectors: int, params: Params | None = None, set: bool = True,
+                      stream=None):
+        """Test(-and-set) keys (CUDA int64 [n] or [n, 2]) against filter_words (CUDA int64 [4*n_sectors])."""
+        import torch
+        n = keys.shape[0]
+        w = 2 if keys.dim() == 2 else 1
+        seen = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        rc = self._lib.turtle_filter(self._h, _dptr(keys), n, w, _dptr(filter_words), n_sectors,
+                                     ctypes.byref(params) if params else None, 1 if set else 0, _dptr(seen),
+                                     _stream_ptr(stream))
+        _check(rc, "turtle_filter")
+        return seen
+
+    def turtle_sort_compact(self, keys, key_bits: int, stream=None):
+        """Sort-and-compact CUDA keys: (unique keys, uint32 run lengths as int32) trimmed to n_unique."""
+        import torch
+        n = keys.shape[0]
+        w = 2 if keys.dim() == 2 else 1
+        uniq = torch.empty_like(keys)
+        counts = torch.empty(n, dtype=torch.int32, device=keys.device)
+        nu = u64()
+        rc = self._lib.turtle_sort_compact(self._h, _dptr(keys), n, w, key_bits, _dptr(uniq), _dptr(counts),
+                                           ctypes.byref(nu), _stream_ptr(stream))
+        _check(rc, "turtle_sort_compact")
+        return uniq[: nu.value], counts[: nu.value]

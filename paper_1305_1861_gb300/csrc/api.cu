@@ -1,0 +1,668 @@
+// libturtle C ABI: contexts, device memory, stage orchestration, host <-> device copies.
+//
+// One call of turtle_count_device runs steps a1..a6 on one stream:
+//   pack + valid  -> W (window count)        [sync: sizes the candidate buffer and the filter]
+//   pass 1        -> candidates              [sync: sizes the sort]
+//   radix sort + run-length compaction       [sync: sizes the recount table]
+//   table insert, pass 2 (recount), threshold -> result in key order
+// Scratch comes from a per-context CUDA memory pool whose memory is retained
+// between calls, so repeated calls do not return to the driver.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/turtle.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace turtle;
+
+namespace {
+
+constexpr uint64_t SPLITMIX_GAMMA = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) drives the pattern table of Sec. 2.1.3:
+// pattern j = `bits` distinct positions of a 64-bit word, position = draw >> 58,
+// repeats skipped, draws taken in order from one stream seeded with `seed`.
+void make_patterns(uint64_t seed, uint32_t bits, uint32_t n, std::vector<uint64_t> &out) {
+    out.assign(n, 0);
+    uint64_t x = seed;
+    for (uint32_t j = 0; j < n; j++) {
+        uint64_t m = 0;
+        uint32_t have = 0;
+        while (have < bits) {
+            x += SPLITMIX_GAMMA;
+            uint64_t z = x;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            const uint64_t bit = 1ull << (z >> 58);
+            if (!(m & bit)) {
+                m |= bit;
+                have++;
+            }
+        }
+        out[j] = m;
+    }
+}
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+int log2_exact(uint64_t p) {
+    int b = 0;
+    while ((1ull << b) < p) b++;
+    return b;
+}
+
+// Device counters read back at the sync points.
+enum { C_WINDOWS = 0, C_CAND, C_UNIQUE, C_OUT, C_N };
+
+}  // namespace
+
+struct turtle_ctx {
+    int device = 0;
+    int sms = 1;
+    cudaMemPool_t pool = nullptr;
+    uint32_t *d_err = nullptr;
+    unsigned long long *d_ctr = nullptr;  // C_N counters
+    unsigned long long *h_ctr = nullptr;  // pinned mirror
+    uint32_t *h_err = nullptr;
+    // pattern table cache
+    uint64_t *d_patterns = nullptr;
+    uint64_t pat_seed = 0;
+    uint32_t pat_bits = 0, pat_n = 0;
+    // buffers of the current call (freed at its end) and of the last result (freed at the next call)
+    std::vector<void *> scratch, result;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t ev[2 * TURTLE_STAGE_COUNT] = {};
+    turtle_stats stats{};
+    uint64_t scratch_bytes = 0;
+};
+
+namespace {
+
+struct Fail {
+    int code;
+};
+
+void ck(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) throw Fail{TURTLE_E_NOMEM};
+    if (e != cudaSuccess) throw Fail{TURTLE_E_CUDA};
+}
+
+void *ctx_alloc(turtle_ctx *c, size_t bytes, cudaStream_t s, bool is_result = false) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{TURTLE_E_NOMEM};
+    }
+    (is_result ? c->result : c->scratch).push_back(p);
+    c->scratch_bytes += bytes;
+    return p;
+}
+
+void free_list(std::vector<void *> &v, cudaStream_t s) {
+    for (void *p : v) cudaFreeAsync(p, s);
+    v.clear();
+}
+
+void ctx_begin(turtle_ctx *c, cudaStream_t s) {
+    ck(cudaSetDevice(c->device));
+    if (!c->result.empty()) free_list(c->result, c->last_stream ? c->last_stream : s);
+    if (c->last_stream && c->last_stream != s) ck(cudaStreamSynchronize(c->last_stream));
+    c->last_stream = s;
+    c->scratch_bytes = 0;
+    ck(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), s));
+    ck(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * C_N, s));
+}
+
+void ctx_end(turtle_ctx *c, cudaStream_t s) { free_list(c->scratch, s); }
+
+// Copy the counters and the error word to the host (synchronises s).
+void read_back(turtle_ctx *c, cudaStream_t s) {
+    ck(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(unsigned long long) * C_N, cudaMemcpyDeviceToHost, s));
+    ck(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    const uint32_t e = *c->h_err;
+    if (e & ERR_BAD_OFFSETS) throw Fail{TURTLE_E_ARG};
+    if (e & ERR_COUNT_OVERFLOW) throw Fail{TURTLE_E_OVERFLOW};
+    if (e) throw Fail{TURTLE_E_DEVICE};
+}
+
+const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t s) {
+    if (c->d_patterns && c->pat_seed == p.pattern_seed && c->pat_bits == p.pattern_bits && c->pat_n == p.n_patterns)
+        return c->d_patterns;
+    std::vector<uint64_t> h;
+    make_patterns(p.pattern_seed, p.pattern_bits, p.n_patterns, h);
+    if (c->d_patterns) {
+        ck(cudaStreamSynchronize(s));
+        cudaFree(c->d_patterns);
+        c->d_patterns = nullptr;
+    }
+    ck(cudaMalloc(&c->d_patterns, sizeof(uint64_t) * p.n_patterns));
+    ck(cudaMemcpyAsync(c->d_patterns, h.data(), sizeof(uint64_t) * p.n_patterns, cudaMemcpyHostToDevice, s));
+    ck(cudaStreamSynchronize(s));
+    c->pat_seed = p.pattern_seed;
+    c->pat_bits = p.pattern_bits;
+    c->pat_n = p.n_patterns;
+    return c->d_patterns;
+}
+
+bool params_ok(const turtle_params &p) {
+    return p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
+           (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
+           p.filter_bits_per_window <= 1024.f;
+}
+
+turtle_params resolve(const turtle_params *p) {
+    turtle_params d;
+    turtle_params_default(&d);
+    if (!p) return d;
+    turtle_params r = *p;
+    if (r.struct_size != sizeof(turtle_params)) return d;
+    return r;
+}
+
+struct Timer {
+    turtle_ctx *c;
+    cudaStream_t s;
+    bool on;
+    void start(int st) {
+        if (on) ck(cudaEventRecord(c->ev[2 * st], s));
+    }
+    void stop(int st) {
+        if (on) ck(cudaEventRecord(c->ev[2 * st + 1], s));
+    }
+};
+
+struct DeviceOut {
+    void *keys = nullptr;
+    uint32_t *counts = nullptr;
+    uint64_t n = 0, n_windows = 0;
+};
+
+template <class K>
+void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
+               int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s, DeviceOut &out) {
+    constexpr int KW = sizeof(K) / 8;
+    const LaunchCfg lc{c->sms, s};
+    turtle_stats st{};
+    Timer tm{c, s, prm.timing != 0};
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+
+    const PackLayout L = PackLayout::of(n_bases);
+    uint64_t *P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
+    uint64_t *B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *V = (uint64_t *)ctx_alloc(c, 8 * L.v_words, s);
+    ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
+    ck(cudaMemsetAsync(V + (L.v_words - 2), 0, 16, s));
+
+    tm.start(TURTLE_STAGE_PACK);
+    launch_pack(lc, bases, offsets, n_reads, L, P, B, S, err);
+    tm.stop(TURTLE_STAGE_PACK);
+    st.stage_launches[TURTLE_STAGE_PACK] = 2;
+    tm.start(TURTLE_STAGE_VALID);
+    launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS);
+    tm.stop(TURTLE_STAGE_VALID);
+    st.stage_launches[TURTLE_STAGE_VALID] = 1;
+    read_back(c, s);
+    const uint64_t W = c->h_ctr[C_WINDOWS];
+    st.n_windows = W;
+    out.n_windows = W;
+    if (W == 0) {
+        out.keys = ctx_alloc(c, 16, s, true);
+        out.counts = (uint32_t *)ctx_alloc(c, 16, s, true);
+        out.n = 0;
+        c->stats = st;
+        return;
+    }
+
+    // pass 1: candidates
+    const bool use_filter = min_count >= 2;
+    FilterGeom fg{};
+    if (use_filter) {
+        const double bits = (double)W * prm.filter_bits_per_window;
+        fg.n_sectors = pow2_at_least((uint64_t)(bits / 256.0) + 1);
+        fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+        fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
+        ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
+        fg.patterns = ctx_patterns(c, prm, s);
+        fg.pat_mask = prm.n_patterns - 1;
+        st.filter_bytes = 32 * fg.n_sectors;
+    }
+    K *cand = (K *)ctx_alloc(c, sizeof(K) * W, s);
+    tm.start(TURTLE_STAGE_FILTER);
+    launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, W, err);
+    tm.stop(TURTLE_STAGE_FILTER);
+    st.stage_launches[TURTLE_STAGE_FILTER] = 1;
+    read_back(c, s);
+    const uint64_t n_cand = c->h_ctr[C_CAND];
+    st.n_candidates = n_cand;
+
+    // a4: sort + compact
+    SortScratch ss{};
+    ss.alt = ctx_alloc(c, sizeof(K) * (n_cand ? n_cand : 1), s);
+    const int passes = sort_passes_for(2 * k);
+    ss.hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ss.lookback_words = sort_lookback_words(n_cand, KW);
+    ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
+    ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
+    tm.start(TURTLE_STAGE_SORT);
+    K *sorted = launch_radix_sort<K>(lc, cand, n_cand, 2 * k, ss, err);
+    tm.stop(TURTLE_STAGE_SORT);
+    st.sort_passes = n_cand > 1 ? passes : 0;
+    st.stage_launches[TURTLE_STAGE_SORT] = n_cand > 1 ? passes + 2 : 0;
+    K *unique = sorted == cand ? (K *)ss.alt : cand;
+    uint64_t *starts = nullptr;
+    if (!use_filter) starts = (uint64_t *)ctx_alloc(c, 8 * (n_cand ? n_cand : 1), s);
+    tm.start(TURTLE_STAGE_RLE);
+    launch_rle<K>(lc, sorted, n_cand, unique, starts, ctr + C_UNIQUE, ss.lookback, ss.tile_ctr + 20, err);
+    tm.stop(TURTLE_STAGE_RLE);
+    st.stage_launches[TURTLE_STAGE_RLE] = n_cand ? 1 : 0;
+
+    if (!use_filter) {
+        // every window is a candidate: run lengths are the exact counts (min_count == 1)
+        uint32_t *counts = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s, true);
+        tm.start(TURTLE_STAGE_THRESHOLD);
+        launch_run_counts(lc, starts, ctr + C_UNIQUE, n_cand, n_cand, counts, err);
+        tm.stop(TURTLE_STAGE_THRESHOLD);
+        st.stage_launches[TURTLE_STAGE_THRESHOLD] = 1;
+        read_back(c, s);
+        const uint64_t nu = c->h_ctr[C_UNIQUE];
+        // keep the buffer holding the unique keys alive as part of the result
+        for (auto it = c->scratch.begin(); it != c->scratch.end(); ++it)
+            if (*it == (void *)unique) {
+                c->result.push_back(*it);
+                c->scratch.erase(it);
+                break;
+            }
+        out.keys = unique;
+        out.counts = counts;
+        out.n = nu;
+        st.n_unique = nu;
+        st.n_out = nu;
+    } else {
+        read_back(c, s);
+        const uint64_t nu = c->h_ctr[C_UNIQUE];
+        st.n_unique = nu;
+        const uint64_t slots = pow2_at_least(2 * nu + 16);
+        void *table = ctx_alloc(c, slot_bytes(KW) * slots, s);
+        st.table_bytes = slot_bytes(KW) * slots;
+        tm.start(TURTLE_STAGE_TABLE);
+        launch_table_clear<K>(lc, table, slots);
+        launch_table_insert<K>(lc, unique, ctr + C_UNIQUE, nu, table, slots - 1, err);
+        tm.stop(TURTLE_STAGE_TABLE);
+        st.stage_launches[TURTLE_STAGE_TABLE] = 1;
+        tm.start(TURTLE_STAGE_RECOUNT);
+        launch_pass2<K>(lc, L, k, P, V, table, slots - 1, W >= 0xfffffffeull, err);
+        tm.stop(TURTLE_STAGE_RECOUNT);
+        st.stage_launches[TURTLE_STAGE_RECOUNT] = 1;
+        K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s, true);
+        uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nu ? nu : 1), s, true);
+        tm.start(TURTLE_STAGE_THRESHOLD);
+        launch_threshold<K>(lc, unique, nu, table, slots - 1, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
+                            ss.tile_ctr + 21, err);
+        tm.stop(TURTLE_STAGE_THRESHOLD);
+        st.stage_launches[TURTLE_STAGE_THRESHOLD] = nu ? 1 : 0;
+        read_back(c, s);
+        out.keys = okeys;
+        out.counts = ocounts;
+        out.n = c->h_ctr[C_OUT];
+        st.n_out = out.n;
+    }
+    if (prm.timing) {
+        for (int i = 0; i < TURTLE_STAGE_COUNT; i++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] = ms;
+            else cudaGetLastError();
+        }
+    }
+    for (int i = 0; i < TURTLE_STAGE_COUNT; i++) st.launches += st.stage_launches[i];
+    st.scratch_bytes = c->scratch_bytes;
+    c->stats = st;
+}
+
+int fail_code(cudaStream_t s, turtle_ctx *c, int code) {
+    // leave the context usable: drop this call's buffers
+    cudaGetLastError();
+    if (c) {
+        free_list(c->scratch, s);
+        free_list(c->result, s);
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+    }
+    return code;
+}
+
+int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                      uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, cudaStream_t s,
+                      DeviceOut &o) {
+    if (!c || k < 1 || k > 64 || min_count < 1 || !offsets || (n_bases && !bases)) return TURTLE_E_ARG;
+    const turtle_params prm = resolve(params);
+    if (!params_ok(prm)) return TURTLE_E_ARG;
+    try {
+        ctx_begin(c, s);
+        if (k <= 32) run_count<uint64_t>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
+        else run_count<Key128>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
+        ctx_end(c, s);
+        return TURTLE_OK;
+    } catch (Fail f) {
+        return fail_code(s, c, f.code);
+    } catch (std::bad_alloc &) {
+        return fail_code(s, c, TURTLE_E_NOMEM);
+    }
+}
+
+std::mutex g_default_mu;
+turtle_ctx *g_default[64] = {};
+
+}  // namespace
+
+extern "C" {
+
+void turtle_params_default(turtle_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(turtle_params);
+    p->filter_bits_per_window = 4.0f;
+    p->pattern_bits = 4;
+    p->n_patterns = 1024;
+    p->pattern_seed = 0x7475727469ull;
+    p->timing = 0;
+}
+
+const char *turtle_strerror(int code) {
+    switch (code) {
+    case TURTLE_OK: return "ok";
+    case TURTLE_E_ARG: return "invalid argument";
+    case TURTLE_E_NOMEM: return "out of memory";
+    case TURTLE_E_CUDA: return "CUDA runtime error";
+    case TURTLE_E_OVERFLOW: return "count overflows uint32";
+    case TURTLE_E_TIMEOUT: return "timed out";
+    case TURTLE_E_BUSY: return "job does not fit the HBM budget";
+    case TURTLE_E_DEVICE: return "device-side check failed";
+    case TURTLE_E_NODEV: return "no CUDA device";
+    case TURTLE_E_CAPACITY: return "output buffer too small";
+    default: return "unknown error";
+    }
+}
+
+const char *turtle_stage_name(int stage) {
+    static const char *names[TURTLE_STAGE_COUNT] = {"pack", "valid", "filter", "hist", "sort",
+                                                    "rle", "table", "recount", "threshold"};
+    return stage >= 0 && stage < TURTLE_STAGE_COUNT ? names[stage] : "?";
+}
+
+int turtle_ctx_create(int device, turtle_ctx **out) {
+    if (!out) return TURTLE_E_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return TURTLE_E_NODEV;
+    }
+    if (device < 0 || device >= n) return TURTLE_E_ARG;
+    turtle_ctx *c = new (std::nothrow) turtle_ctx();
+    if (!c) return TURTLE_E_NOMEM;
+    c->device = device;
+    try {
+        ck(cudaSetDevice(device));
+        ck(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        ck(cudaMemPoolCreate(&c->pool, &props));
+        uint64_t keep = ~0ull;
+        ck(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        ck(cudaMalloc(&c->d_err, 64));
+        ck(cudaMalloc(&c->d_ctr, sizeof(unsigned long long) * C_N));
+        ck(cudaMallocHost(&c->h_ctr, sizeof(unsigned long long) * C_N));
+        ck(cudaMallocHost(&c->h_err, 64));
+        for (auto &e : c->ev) ck(cudaEventCreate(&e));
+    } catch (Fail f) {
+        turtle_ctx_destroy(c);
+        return f.code;
+    }
+    *out = c;
+    return TURTLE_OK;
+}
+
+void turtle_ctx_destroy(turtle_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaDeviceSynchronize();
+    for (void *p : c->scratch) cudaFree(p);
+    for (void *p : c->result) cudaFree(p);
+    if (c->d_patterns) cudaFree(c->d_patterns);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_ctr) cudaFree(c->d_ctr);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    cudaGetLastError();
+    delete c;
+}
+
+int turtle_ctx_stats(const turtle_ctx *c, turtle_stats *st) {
+    if (!c || !st) return TURTLE_E_ARG;
+    *st = c->stats;
+    return TURTLE_OK;
+}
+
+int turtle_count_device(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                        uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, void *stream,
+                        turtle_device_result *out) {
+    if (!out) return TURTLE_E_ARG;
+    memset(out, 0, sizeof(*out));
+    DeviceOut o;
+    const int rc = count_device_impl(c, bases, n_bases, offsets, n_reads, k, min_count, params, (cudaStream_t)stream, o);
+    if (rc) return rc;
+    out->k = k;
+    out->key_words = k <= 32 ? 1 : 2;
+    out->n = o.n;
+    out->keys = (const uint64_t *)o.keys;
+    out->counts = o.counts;
+    out->n_windows = o.n_windows;
+    return TURTLE_OK;
+}
+
+static turtle_ctx *default_ctx(int *rc) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        *rc = TURTLE_E_NODEV;
+        return nullptr;
+    }
+    if (dev < 0 || dev >= 64) {
+        *rc = TURTLE_E_ARG;
+        return nullptr;
+    }
+    if (!g_default[dev]) {
+        *rc = turtle_ctx_create(dev, &g_default[dev]);
+        if (*rc) return nullptr;
+    }
+    *rc = TURTLE_OK;
+    return g_default[dev];
+}
+
+int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params, void *stream,
+                    turtle_result *out) {
+    if (!out) return TURTLE_E_ARG;
+    memset(out, 0, sizeof(*out));
+    if (!reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64 || min_count < 1)
+        return TURTLE_E_ARG;
+    for (uint64_t i = 0; i < reads->n_reads; i++)
+        if (reads->offsets[i + 1] < reads->offsets[i]) return TURTLE_E_ARG;
+    std::lock_guard<std::mutex> g(g_default_mu);
+    int rc = 0;
+    turtle_ctx *c = default_ctx(&rc);
+    if (!c) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t n_bases = reads->offsets[reads->n_reads];
+    uint8_t *d_bases = nullptr;
+    uint64_t *d_off = nullptr;
+    try {
+        ck(cudaSetDevice(c->device));
+        ck(cudaSetDevice(c->device));
+        ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
+        ck(cudaMallocFromPoolAsync((void **)&d_off, 8 * (reads->n_reads + 1), c->pool, s));
+        if (n_bases) ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(d_off, reads->offsets, 8 * (reads->n_reads + 1), cudaMemcpyHostToDevice, s));
+    } catch (Fail f) {
+        if (d_bases) cudaFreeAsync(d_bases, s);
+        if (d_off) cudaFreeAsync(d_off, s);
+        return f.code;
+    }
+    DeviceOut o;
+    rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o);
+    cudaFreeAsync(d_bases, s);
+    cudaFreeAsync(d_off, s);
+    if (rc) return rc;
+    const int kw = k <= 32 ? 1 : 2;
+    out->keys = (uint64_t *)malloc(8 * kw * (o.n ? o.n : 1));
+    out->counts = (uint32_t *)malloc(4 * (o.n ? o.n : 1));
+    if (!out->keys || !out->counts) {
+        turtle_result_free(out);
+        return TURTLE_E_NOMEM;
+    }
+    if (cudaMemcpyAsync(out->keys, o.keys, 8 * kw * o.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(out->counts, o.counts, 4 * o.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        turtle_result_free(out);
+        return TURTLE_E_CUDA;
+    }
+    out->k = k;
+    out->n = o.n;
+    out->n_windows = o.n_windows;
+    return TURTLE_OK;
+}
+
+int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_result *out) {
+    return turtle_count_ex(reads, k, min_count, nullptr, nullptr, out);
+}
+
+void turtle_result_free(turtle_result *r) {
+    if (!r) return;
+    free(r->keys);
+    free(r->counts);
+    r->keys = nullptr;
+    r->counts = nullptr;
+    r->n = 0;
+}
+
+int turtle_extract(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
+                   int k, void *stream, uint64_t *keys, uint64_t *valid, uint64_t *n_windows) {
+    if (!c || k < 1 || k > 64 || !offsets || (n_bases && (!bases || !keys || !valid))) return TURTLE_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        ctx_begin(c, s);
+        const LaunchCfg lc{c->sms, s};
+        const PackLayout L = PackLayout::of(n_bases);
+        uint64_t *P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
+        uint64_t *B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+        uint64_t *S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+        uint64_t *V = (uint64_t *)ctx_alloc(c, 8 * L.v_words, s);
+        ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
+        ck(cudaMemsetAsync(V + (L.v_words - 2), 0, 16, s));
+        launch_pack(lc, bases, offsets, n_reads, L, P, B, S, c->d_err);
+        launch_valid(lc, L, k, B, S, V, c->d_ctr + C_WINDOWS);
+        launch_extract(lc, L, k, P, V, keys);
+        if (n_bases) ck(cudaMemcpyAsync(valid, V, 8 * ((n_bases + 63) / 64), cudaMemcpyDeviceToDevice, s));
+        read_back(c, s);
+        if (n_windows) *n_windows = c->h_ctr[C_WINDOWS];
+        ctx_end(c, s);
+        return TURTLE_OK;
+    } catch (Fail f) {
+        return fail_code(s, c, f.code);
+    }
+}
+
+int turtle_filter(turtle_ctx *c, const uint64_t *keys, uint64_t n, int key_words, uint64_t *filter,
+                  uint64_t n_sectors, const turtle_params *params, int set, uint8_t *seen, void *stream) {
+    if (!c || (key_words != 1 && key_words != 2) || !filter || n_sectors == 0 || (n_sectors & (n_sectors - 1)) ||
+        (n && !keys) || (!set && !seen))
+        return TURTLE_E_ARG;
+    const turtle_params prm = resolve(params);
+    if (!params_ok(prm)) return TURTLE_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        ctx_begin(c, s);
+        const LaunchCfg lc{c->sms, s};
+        FilterGeom fg{};
+        fg.words = filter;
+        fg.n_sectors = n_sectors;
+        fg.sector_shift = 64 - log2_exact(n_sectors);
+        fg.patterns = ctx_patterns(c, prm, s);
+        fg.pat_mask = prm.n_patterns - 1;
+        if (n) {
+            if (key_words == 1) launch_filter_keys<uint64_t>(lc, keys, n, fg, set, seen);
+            else launch_filter_keys<Key128>(lc, reinterpret_cast<const Key128 *>(keys), n, fg, set, seen);
+        }
+        read_back(c, s);
+        ctx_end(c, s);
+        return TURTLE_OK;
+    } catch (Fail f) {
+        return fail_code(s, c, f.code);
+    }
+}
+
+int turtle_sort_compact(turtle_ctx *c, const uint64_t *keys, uint64_t n, int key_words, int key_bits,
+                        uint64_t *unique, uint32_t *counts, uint64_t *n_unique, void *stream) {
+    if (!c || (key_words != 1 && key_words != 2) || key_bits < 1 || key_bits > 64 * key_words || !n_unique ||
+        (n && (!keys || !unique || !counts)))
+        return TURTLE_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        ctx_begin(c, s);
+        *n_unique = 0;
+        if (n == 0) {
+            ctx_end(c, s);
+            return TURTLE_OK;
+        }
+        const LaunchCfg lc{c->sms, s};
+        const size_t kb = 8 * key_words;
+        void *a = ctx_alloc(c, kb * n, s);
+        SortScratch ss{};
+        ss.alt = ctx_alloc(c, kb * n, s);
+        ss.hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+        ss.lookback_words = sort_lookback_words(n, key_words);
+        ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
+        ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
+        uint64_t *starts = (uint64_t *)ctx_alloc(c, 8 * n, s);
+        ck(cudaMemcpyAsync(a, keys, kb * n, cudaMemcpyDeviceToDevice, s));
+        if (key_words == 1) {
+            uint64_t *sorted = launch_radix_sort<uint64_t>(lc, (uint64_t *)a, n, key_bits, ss, c->d_err);
+            launch_rle<uint64_t>(lc, sorted, n, unique, starts, c->d_ctr + C_UNIQUE, ss.lookback, ss.tile_ctr + 20,
+                                 c->d_err);
+        } else {
+            Key128 *sorted = launch_radix_sort<Key128>(lc, (Key128 *)a, n, key_bits, ss, c->d_err);
+            launch_rle<Key128>(lc, sorted, n, (Key128 *)unique, starts, c->d_ctr + C_UNIQUE, ss.lookback,
+                               ss.tile_ctr + 20, c->d_err);
+        }
+        launch_run_counts(lc, starts, c->d_ctr + C_UNIQUE, n, n, counts, c->d_err);
+        read_back(c, s);
+        *n_unique = c->h_ctr[C_UNIQUE];
+        ctx_end(c, s);
+        return TURTLE_OK;
+    } catch (Fail f) {
+        return fail_code(s, c, f.code);
+    }
+}
+
+}  // extern "C"

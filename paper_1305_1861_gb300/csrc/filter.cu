@@ -1,0 +1,182 @@
+// Steps a2+a3: canonical extraction and the pattern-blocked Bloom filter (Sec. 2.1.3).
+//
+// Block = one 32-byte DRAM sector chosen by the top bits of the key hash; the
+// precomputed pattern (from a table kept in shared memory, indexed by the low
+// hash bits) lies inside one 64-bit word of that sector, chosen by hash bits
+// 16..17. A probe therefore costs one sector, and test-and-set is a single
+// atomicOr on one word.
+//
+// Why one word: "seen before" must be decided by one linearizable operation.
+// If a pattern spanned several words with one atomic each, two concurrent first
+// sightings of a key could each find a different word not yet set and both
+// conclude "first sighting"; the key would then never become a candidate and
+// the recount could not repair the miss. With one atomicOr per key, among all
+// occurrences of a key at most one can observe its pattern incomplete, so every
+// key seen twice emits at least one candidate (no false negatives, for any
+// interleaving). A plain load that already shows every pattern bit set proves
+// "seen" without the atomic, because bits are never cleared.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace turtle {
+
+constexpr int P1_BLOCK = 256;
+constexpr int P1_WARPS = P1_BLOCK / WARP;
+constexpr int P1_ILP = 4;                    // window starts per lane per warp tile
+constexpr int P1_TILE = WARP * P1_ILP;       // 128 starts per warp tile (two V words)
+constexpr int P1_STAGE = 256;                // keys per candidate flush
+constexpr int P1_BUF = P1_STAGE + WARP;      // warp staging buffer capacity
+
+template <class K>
+__device__ __forceinline__ void flush_full(K *wbuf, int &nbuf, K *cand, unsigned long long *cand_count,
+                                           uint64_t cand_cap, uint32_t *err, int lane) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)P1_STAGE);
+    base = __shfl_sync(FULL, base, 0);
+    if (base + P1_STAGE <= cand_cap) {
+#pragma unroll
+        for (int j = 0; j < P1_STAGE / WARP; j++) store_key(cand + base + lane + WARP * j, wbuf[lane + WARP * j]);
+    } else if (lane == 0) {
+        atomicOr(err, ERR_CAND_OVERFLOW);
+    }
+    const int rem = nbuf - P1_STAGE;
+    K tail;
+    if (lane < rem) tail = wbuf[P1_STAGE + lane];
+    __syncwarp();
+    if (lane < rem) wbuf[lane] = tail;
+    __syncwarp();
+    nbuf = rem;
+}
+
+template <class K, bool USE_FILTER>
+__global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                    uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
+                                                    const uint64_t *__restrict__ patterns, uint32_t pat_mask,
+                                                    K *cand, unsigned long long *cand_count, uint64_t cand_cap,
+                                                    uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    K *s_buf = reinterpret_cast<K *>(smem);
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS);
+    if (USE_FILTER)
+        for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    K *wbuf = s_buf + warp * P1_BUF;
+    int nbuf = 0;
+    const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
+    for (uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp; t < tiles; t += (uint64_t)gridDim.x * P1_WARPS) {
+        const uint64_t base = t * P1_TILE;
+        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+        bool ok[P1_ILP];
+        K key[P1_ILP];
+        uint64_t *addr[P1_ILP];
+        uint64_t mask[P1_ILP];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const int r = lane + WARP * i;
+            const uint64_t s = base + r;
+            ok[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
+            if (ok[i]) {
+                key[i] = canonical<K>(P, s, k);
+                if (USE_FILTER) {
+                    const uint64_t h = key_hash(key[i]);
+                    const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
+                    addr[i] = filter + sector * 4 + ((h >> 16) & 3);
+                    mask[i] = s_pat[h & pat_mask];
+                }
+            }
+        }
+        bool seen[P1_ILP];
+        if (USE_FILTER) {
+            uint64_t w[P1_ILP];
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++) w[i] = ok[i] ? __ldcg(addr[i]) : 0;
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++) {
+                seen[i] = ok[i];
+                if (ok[i] && (w[i] & mask[i]) != mask[i]) {
+                    const uint64_t old = atomicOr((unsigned long long *)addr[i], (unsigned long long)mask[i]);
+                    seen[i] = (old & mask[i]) == mask[i];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++) seen[i] = ok[i];
+        }
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const uint32_t b = __ballot_sync(FULL, seen[i]);
+            if (seen[i]) wbuf[nbuf + __popc(b & lt)] = key[i];
+            nbuf += __popc(b);
+            if (nbuf >= P1_STAGE) flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+        }
+    }
+    __syncwarp();
+    if (nbuf > 0) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)nbuf);
+        base = __shfl_sync(FULL, base, 0);
+        if (base + nbuf <= cand_cap) {
+            for (int j = lane; j < nbuf; j += WARP) store_key(cand + base + j, wbuf[j]);
+        } else if (lane == 0) {
+            atomicOr(err, ERR_CAND_OVERFLOW);
+        }
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys, uint64_t n, uint64_t *filter,
+                                                     int sector_shift, const uint64_t *__restrict__ patterns,
+                                                     uint32_t pat_mask, int set, uint8_t *seen) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const K key = keys[i];
+        const uint64_t h = key_hash(key);
+        const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
+        uint64_t *addr = filter + sector * 4 + ((h >> 16) & 3);
+        const uint64_t m = patterns[h & pat_mask];
+        uint64_t w = __ldcg(addr);
+        bool s = (w & m) == m;
+        if (set && !s) s = (atomicOr((unsigned long long *)addr, (unsigned long long)m) & m) == m;
+        if (seen) seen[i] = s ? 1 : 0;
+    }
+}
+
+template <class K>
+void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                  bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
+                  uint32_t *err) {
+    const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
+    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS + (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
+    auto kern = use_filter ? k_pass1<K, true> : k_pass1<K, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P1_BLOCK, smem);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t need = (tiles + P1_WARPS - 1) / P1_WARPS;
+    uint64_t cap = (uint64_t)c.sms * per_sm;
+    int grid = (int)(need < cap ? (need ? need : 1) : cap);
+    kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
+                                             cand, cand_count, cand_cap, err);
+}
+
+template <class K>
+void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const FilterGeom &f, int set, uint8_t *seen) {
+    uint64_t need = (n + 255) / 256;
+    uint64_t cap = (uint64_t)c.sms * 8;
+    int grid = (int)(need < cap ? (need ? need : 1) : cap);
+    k_filter_keys<K><<<grid, 256, 0, c.stream>>>(keys, n, f.words, f.sector_shift, f.patterns, f.pat_mask, set, seen);
+}
+
+template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
+                                     bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint32_t *);
+template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
+                                   bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, uint32_t *);
+template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
+                                           uint8_t *);
+template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,
+                                         uint8_t *);
+
+}  // namespace turtle

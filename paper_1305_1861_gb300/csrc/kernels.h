@@ -1,0 +1,97 @@
+// Host-side launchers of the libturtle kernels (internal; not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace turtle {
+
+struct Key128;
+
+// Layout sizes derived from n_bases (all in uint64 words).
+struct PackLayout {
+    uint64_t n_bases;
+    uint64_t p_words;  // packed 2-bit codes: 32 bases/word, one per pack group (2 * b_words)
+    uint64_t b_words;  // ambiguous-call bitmap and read-start bitmap: 64 positions/word, +2 padding
+    uint64_t v_words;  // valid-window bitmap: 64 positions/word, +2 padding
+    static PackLayout of(uint64_t n_bases) {
+        PackLayout L;
+        L.n_bases = n_bases;
+        L.b_words = (n_bases + 63) / 64 + 2;
+        L.p_words = 2 * L.b_words;
+        L.v_words = (n_bases + 63) / 64 + 2;
+        return L;
+    }
+};
+
+struct LaunchCfg {
+    int sms;            // multiprocessors on the device
+    cudaStream_t stream;
+};
+
+// a1: P <- 2-bit codes, B <- ambiguous/out-of-read bits, S <- read-start bits (S must be zero on entry).
+void launch_pack(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
+                 const PackLayout &L, uint64_t *P, uint64_t *B, uint64_t *S, uint32_t *err);
+// a1/a2: V <- valid-window bits for k; *n_windows += popcount(V) (zero it first).
+void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *B, const uint64_t *S,
+                  uint64_t *V, unsigned long long *n_windows);
+// a2 alone: keys[s] <- canonical key of every valid window start s.
+void launch_extract(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                    uint64_t *keys);
+
+struct FilterGeom {
+    uint64_t *words;        // 4 * n_sectors uint64
+    uint64_t n_sectors;     // power of two
+    int sector_shift;       // 64 - log2(n_sectors); 64 when n_sectors == 1
+    const uint64_t *patterns;  // device, n_patterns masks
+    uint32_t pat_mask;      // n_patterns - 1
+};
+
+// a2+a3: pass 1. Emits the canonical key of every valid window whose filter test says "seen"
+// (every valid window when use_filter is false) to cand[0 .. *cand_count).
+template <class K>
+void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                  bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
+                  uint32_t *err);
+// a3 alone on a key array.
+template <class K>
+void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const FilterGeom &f, int set, uint8_t *seen);
+
+// a4: radix sort + run-length compaction.
+struct SortScratch {
+    void *alt;               // n keys
+    uint64_t *hist;          // passes * 256
+    uint64_t *lookback;      // max(tiles) * 256 status words (zeroed by the sorter)
+    uint32_t *tile_ctr;      // passes + 2 counters (zeroed by the sorter)
+    uint64_t lookback_words;
+};
+int sort_passes_for(int key_bits);
+uint64_t sort_lookback_words(uint64_t n, int key_words);
+// Sorts keys[0..n) by their low key_bits bits. Returns the buffer that holds the result (keys or scratch.alt).
+template <class K>
+K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err);
+// unique/starts from sorted keys; *n_unique (device) receives the distinct count.
+template <class K>
+void launch_rle(const LaunchCfg &c, const K *sorted, uint64_t n, K *unique, uint64_t *starts,
+                unsigned long long *n_unique, uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err);
+// counts[j] <- starts[j+1] - starts[j] (starts[n_unique] = n), with overflow check.
+void launch_run_counts(const LaunchCfg &c, const uint64_t *starts, const unsigned long long *n_unique, uint64_t n,
+                       uint64_t cap, uint32_t *counts, uint32_t *err);
+
+// a5: recount table.
+template <class K> struct Slot;
+size_t slot_bytes(int key_words);
+template <class K>
+void launch_table_clear(const LaunchCfg &c, void *table, uint64_t slots);
+template <class K>
+void launch_table_insert(const LaunchCfg &c, const K *unique, const unsigned long long *n_unique, uint64_t cap,
+                         void *table, uint64_t mask, uint32_t *err);
+template <class K>
+void launch_pass2(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                  void *table, uint64_t mask, bool check_overflow, uint32_t *err);
+// a6: keep count >= min_count in key order.
+template <class K>
+void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, const void *table, uint64_t mask,
+                      uint32_t min_count, K *out_keys, uint32_t *out_counts, unsigned long long *n_out,
+                      uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err);
+
+}  // namespace turtle

@@ -1,0 +1,159 @@
+// Step a1/a2 support: ASCII reads -> 2-bit codes + bitmaps; valid-window bitmap; per-window keys.
+//
+// Sec. 2.1.2: k-mers are 2-bit encoded and taken from reads split at ambiguous
+// calls. Here every base position of the concatenated library gets a 2-bit code
+// (P), a "bad" bit (B: not A/C/G/T, or outside [offsets[0], offsets[n_reads])) and
+// a read-start bit (S). A window [s, s+k) is valid iff no bad bit lies in
+// [s, s+k) and no read starts in (s, s+k); V holds one bit per start s.
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace turtle {
+
+// 4 ASCII bytes (first base in the low byte) -> 8-bit code group (first base most significant)
+// and 4 bad bits (bit j for byte j).
+__device__ __forceinline__ void decode4(uint32_t x, uint32_t &codes8, uint32_t &bad4) {
+    const uint32_t u = x & 0xDFDFDFDFu;  // fold lower case onto upper case
+    const uint32_t ok = __vcmpeq4(u, 0x41414141u) | __vcmpeq4(u, 0x43434343u) | __vcmpeq4(u, 0x47474747u) |
+                        __vcmpeq4(u, 0x54545454u);
+    const uint32_t t = (u >> 1) & 0x03030303u;          // A->0 C->1 G->3 T->2
+    const uint32_t c = t ^ ((t >> 1) & 0x01010101u);   // A->0 C->1 G->2 T->3
+    codes8 = ((c & 3u) << 6) | (((c >> 8) & 3u) << 4) | (((c >> 16) & 3u) << 2) | ((c >> 24) & 3u);
+    const uint32_t nb = ~ok;
+    bad4 = ((nb >> 7) & 1u) | ((nb >> 14) & 2u) | ((nb >> 21) & 4u) | ((nb >> 28) & 8u);
+}
+
+// One thread per group of 32 positions: P[g] (uint64) and 32 bad bits (half of a B word).
+__global__ void __launch_bounds__(256) k_pack(const uint8_t *__restrict__ bases, uint64_t n_bases,
+                                              const uint64_t *__restrict__ offsets, uint64_t n_reads,
+                                              uint64_t n_groups, uint64_t *__restrict__ P, uint32_t *__restrict__ B32) {
+    const uint64_t lo = offsets[0], hi = offsets[n_reads] < n_bases ? offsets[n_reads] : n_bases;
+    const bool aligned = (((uintptr_t)bases) & 15u) == 0;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p0 = g * 32;
+        uint32_t w[8];
+        if (aligned && p0 + 32 <= n_bases) {
+            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(bases + p0));
+            const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(bases + p0 + 16));
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const uint64_t p = p0 + 4 * i + j;
+                    v |= (uint32_t)(p < n_bases ? bases[p] : (uint8_t)'N') << (8 * j);
+                }
+                w[i] = v;
+            }
+        }
+        uint64_t packed = 0;
+        uint32_t bad = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            uint32_t c8, b4;
+            decode4(w[i], c8, b4);
+            packed |= (uint64_t)c8 << (56 - 8 * i);
+            bad |= b4 << (4 * i);
+        }
+        // positions outside [lo, hi) belong to no read
+        if (p0 < lo) bad |= (lo >= p0 + 32) ? 0xffffffffu : ((1u << (lo - p0)) - 1u);
+        if (p0 + 32 > hi) bad |= (hi <= p0) ? 0xffffffffu : ~((1u << (hi - p0)) - 1u);
+        P[g] = packed;
+        B32[g] = bad;
+    }
+}
+
+// Read-start bits and offsets validation. One thread per offsets entry.
+__global__ void k_mark_starts(const uint64_t *__restrict__ offsets, uint64_t n_reads, uint64_t n_bases,
+                              uint32_t *__restrict__ S32, uint32_t *err) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r <= n_reads;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p = offsets[r];
+        if (r < n_reads && offsets[r + 1] < p) atomicOr(err, ERR_BAD_OFFSETS);
+        if (p > n_bases) atomicOr(err, ERR_BAD_OFFSETS);
+        if (r > 0 && r < n_reads && p < n_bases) atomicOr(S32 + (p >> 5), 1u << (p & 31));
+    }
+}
+
+// OR of x >> j for j in [0, len) (bit s of the result covers positions s .. s+len-1).
+__device__ __forceinline__ unsigned __int128 smear(unsigned __int128 x, int len) {
+    unsigned __int128 acc = 0, cur = x;
+    int span = 1, off = 0;
+    while (len) {
+        if (len & 1) {
+            acc |= cur >> off;
+            off += span;
+        }
+        cur |= cur >> span;
+        span <<= 1;
+        len >>= 1;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) k_valid(const uint64_t *__restrict__ B, const uint64_t *__restrict__ S,
+                                               uint64_t n_words, int k, uint64_t *__restrict__ V,
+                                               unsigned long long *n_windows) {
+    uint32_t mine = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_words;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned __int128 b = ((unsigned __int128)B[i + 1] << 64) | B[i];
+        const unsigned __int128 s = ((unsigned __int128)S[i + 1] << 64) | S[i];
+        const uint64_t badspan = (uint64_t)smear(b, k);
+        const uint64_t startspan = (uint64_t)smear(s >> 1, k - 1);
+        const uint64_t v = ~(badspan | startspan);
+        V[i] = v;
+        mine += __popcll(v);
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) mine += __shfl_xor_sync(FULL, mine, d);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(n_windows, (unsigned long long)mine);
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_extract(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                 uint64_t n_pos, int k, K *__restrict__ keys) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_pos;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        if ((V[s >> 6] >> (s & 63)) & 1) keys[s] = canonical<K>(P, s, k);
+    }
+}
+
+static int grid_for(uint64_t items, int block, int sms, int per_sm) {
+    uint64_t need = (items + block - 1) / block;
+    uint64_t cap = (uint64_t)sms * per_sm;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+void launch_pack(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
+                 const PackLayout &L, uint64_t *P, uint64_t *B, uint64_t *S, uint32_t *err) {
+    const uint64_t n_groups = 2 * L.b_words;  // covers every B word, including the padding (all bad)
+    k_pack<<<grid_for(n_groups, 256, c.sms, 16), 256, 0, c.stream>>>(bases, L.n_bases, offsets, n_reads, n_groups,
+                                                                     P, reinterpret_cast<uint32_t *>(B));
+    k_mark_starts<<<grid_for(n_reads + 1, 256, c.sms, 8), 256, 0, c.stream>>>(offsets, n_reads, L.n_bases,
+                                                                            reinterpret_cast<uint32_t *>(S), err);
+}
+
+void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *B, const uint64_t *S, uint64_t *V,
+                  unsigned long long *n_windows) {
+    const uint64_t n_words = L.v_words - 2;
+    k_valid<<<grid_for(n_words, 256, c.sms, 8), 256, 0, c.stream>>>(B, S, n_words, k, V, n_windows);
+}
+
+void launch_extract(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                    uint64_t *keys) {
+    if (k <= 32)
+        k_extract<uint64_t><<<grid_for(L.n_bases, 256, c.sms, 8), 256, 0, c.stream>>>(P, V, L.n_bases, k, keys);
+    else
+        k_extract<Key128><<<grid_for(L.n_bases, 256, c.sms, 8), 256, 0, c.stream>>>(
+            P, V, L.n_bases, k, reinterpret_cast<Key128 *>(keys));
+}
+
+}  // namespace turtle

@@ -1,0 +1,255 @@
+// Step a4: sort-and-compact of the candidate keys (Sec. 2.1.4, Alg. 1).
+//
+// The paper sorts its candidate array in place with a comparison sort and then
+// merges runs of equal keys. On the GPU the sort is a least-significant-digit
+// radix sort in the onesweep style (Adinets & Merrill 2022): one kernel reads the
+// keys once and builds the 256-bin histograms of every 8-bit digit; then each
+// digit pass is ONE kernel in which a tile ranks its keys locally (warp match +
+// per-warp counters, stable), publishes its per-digit counts, obtains the counts
+// of all earlier tiles through decoupled look-back (one status chain per digit)
+// and scatters its keys, staged through shared memory so that each run of equal
+// digits is written contiguously. Each pass reads and writes every key once.
+// Run-length compaction then keeps the first key of each run (flag = key differs
+// from its predecessor) with an order-preserving single-pass scan.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace turtle {
+
+constexpr int S_BLOCK = 256;
+constexpr int S_WARPS = S_BLOCK / WARP;
+constexpr int BINS = 256;
+constexpr int MAX_PASSES = 16;
+
+template <class K> struct SortCfg;
+template <> struct SortCfg<uint64_t> { static constexpr int ITEMS = 16; };  // 4096 keys (32 KB) per tile
+template <> struct SortCfg<Key128> { static constexpr int ITEMS = 8; };     // 2048 keys (32 KB) per tile
+
+int sort_passes_for(int key_bits) { return (key_bits + 7) / 8; }
+
+uint64_t sort_lookback_words(uint64_t n, int key_words) {
+    const uint64_t tile = (uint64_t)S_BLOCK * (key_words == 1 ? SortCfg<uint64_t>::ITEMS : SortCfg<Key128>::ITEMS);
+    return ((n + tile - 1) / tile + 1) * BINS;
+}
+
+template <class K>
+__global__ void __launch_bounds__(S_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, int passes,
+                                                  uint64_t *__restrict__ hist) {
+    __shared__ uint32_t sh[MAX_PASSES * BINS];
+    for (int i = threadIdx.x; i < passes * BINS; i += S_BLOCK) sh[i] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)S_BLOCK + threadIdx.x; i < n; i += (uint64_t)gridDim.x * S_BLOCK) {
+        const K key = keys[i];
+        for (int p = 0; p < passes; p++) atomicAdd(&sh[p * BINS + KeyT<K>::digit(key, 8 * p)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * BINS; i += S_BLOCK)
+        if (sh[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)sh[i]);
+}
+
+// hist[p][d] -> exclusive prefix over d (in place). One block per pass.
+__global__ void k_scan_bins(uint64_t *hist) {
+    __shared__ uint64_t s[BINS];
+    uint64_t *h = hist + (uint64_t)blockIdx.x * BINS;
+    s[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = 0;
+        for (int d = 0; d < BINS; d++) {
+            const uint64_t v = s[d];
+            s[d] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    h[threadIdx.x] = s[threadIdx.x];
+}
+
+template <class K>
+__global__ void __launch_bounds__(S_BLOCK) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
+                                                      int shift, const uint64_t *__restrict__ bin_base,
+                                                      uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
+                                                      uint32_t *err) {
+    constexpr int ITEMS = SortCfg<K>::ITEMS;
+    constexpr int TILE = S_BLOCK * ITEMS;
+    __shared__ K skeys[TILE];
+    __shared__ uint32_t whist[S_WARPS][BINS];
+    __shared__ uint32_t s_texcl[BINS];
+    __shared__ uint64_t s_glob[BINS];
+    __shared__ uint32_t s_scan[S_WARPS];
+    __shared__ uint32_t s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < S_WARPS * BINS; i += S_BLOCK) (&whist[0][0])[i] = 0;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // tiles start in launch order: look-back always progresses
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t start = tile * TILE;
+    const uint64_t wstart = start + (uint64_t)warp * ITEMS * WARP;
+    const uint32_t lt = lanemask_lt();
+
+    K key[ITEMS];
+    uint32_t rank[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        const uint64_t idx = wstart + i * WARP + lane;
+        if (idx < n) key[i] = in[idx];
+    }
+    // Stable local ranking: order is (warp, row, lane) = input order.
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        const bool valid = wstart + i * WARP + lane < n;
+        const uint32_t d = valid ? KeyT<K>::digit(key[i], shift) : (BINS + lane);
+        const uint32_t peers = __match_any_sync(FULL, d);
+        uint32_t pre = 0;
+        if (valid) pre = whist[warp][d];
+        __syncwarp();
+        if (valid && lane == 31 - __clz(peers)) whist[warp][d] = pre + __popc(peers);
+        __syncwarp();
+        rank[i] = pre + __popc(peers & lt);
+    }
+    __syncthreads();
+    // Thread tid owns digit tid: exclusive offsets over warps, tile count, tile-local digit start.
+    uint32_t tcount = 0;
+#pragma unroll
+    for (int w = 0; w < S_WARPS; w++) {
+        const uint32_t v = whist[w][tid];
+        whist[w][tid] = tcount;
+        tcount += v;
+    }
+    const uint32_t texcl = block_exclusive_scan<S_BLOCK>(tcount, s_scan, nullptr);
+    s_texcl[tid] = texcl;
+    const uint64_t excl = lookback_prefix(lookback + tid, BINS, tile, tcount, epoch, err);
+    s_glob[tid] = bin_base[tid] + excl - texcl;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        if (wstart + i * WARP + lane < n) {
+            const uint32_t d = KeyT<K>::digit(key[i], shift);
+            skeys[s_texcl[d] + whist[warp][d] + rank[i]] = key[i];
+        }
+    }
+    __syncthreads();
+    const uint32_t tile_n = (uint32_t)(n - start < (uint64_t)TILE ? n - start : TILE);
+    for (uint32_t p = tid; p < tile_n; p += S_BLOCK) {
+        const K kk = skeys[p];
+        out[s_glob[KeyT<K>::digit(kk, shift)] + p] = kk;
+    }
+}
+
+template <class K>
+K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err) {
+    const int passes = sort_passes_for(key_bits);
+    if (n <= 1 || passes == 0) return keys;
+    constexpr int TILE = S_BLOCK * SortCfg<K>::ITEMS;
+    const uint64_t tiles = (n + TILE - 1) / TILE;
+    cudaMemsetAsync(s.hist, 0, sizeof(uint64_t) * passes * BINS, c.stream);
+    cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
+    cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
+    uint64_t need = (n + S_BLOCK - 1) / S_BLOCK;
+    const uint64_t cap = (uint64_t)c.sms * 4;
+    k_hist<K><<<(int)(need < cap ? need : cap), S_BLOCK, 0, c.stream>>>(keys, n, passes, s.hist);
+    k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
+    K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
+    for (int p = 0; p < passes; p++) {
+        k_onesweep<K><<<(int)tiles, S_BLOCK, 0, c.stream>>>(src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS,
+                                                           s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err);
+        K *t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// ---------------------------------------------------------------- run-length compaction
+template <class K> struct RleCfg;
+template <> struct RleCfg<uint64_t> { static constexpr int ITEMS = 16; };  // 32 KB of keys per tile
+template <> struct RleCfg<Key128> { static constexpr int ITEMS = 8; };
+
+template <class K>
+__global__ void __launch_bounds__(S_BLOCK) k_rle(const K *__restrict__ sorted, uint64_t n, K *__restrict__ unique,
+                                                 uint64_t *__restrict__ starts, unsigned long long *n_unique,
+                                                 uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err) {
+    constexpr int R_ITEMS = RleCfg<K>::ITEMS;
+    constexpr int R_TILE = S_BLOCK * R_ITEMS;
+    __shared__ K skeys[R_TILE];
+    __shared__ uint32_t s_scan[S_WARPS];
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile, start = tile * R_TILE;
+    const uint32_t tile_n = (uint32_t)(n - start < (uint64_t)R_TILE ? n - start : R_TILE);
+    for (uint32_t i = tid; i < tile_n; i += S_BLOCK) skeys[i] = sorted[start + i];
+    __syncthreads();
+    // blocked: thread tid owns tile positions [tid*R_ITEMS, +R_ITEMS)
+    uint32_t flags = 0, cnt = 0;
+    const uint32_t p0 = tid * R_ITEMS;
+#pragma unroll
+    for (int j = 0; j < R_ITEMS; j++) {
+        const uint32_t p = p0 + j;
+        if (p < tile_n) {
+            bool f;
+            if (p > 0) f = !KeyT<K>::eq(skeys[p], skeys[p - 1]);
+            else f = (start == 0) || !KeyT<K>::eq(skeys[0], sorted[start - 1]);
+            flags |= (uint32_t)f << j;
+            cnt += f;
+        }
+    }
+    uint32_t total;
+    const uint32_t before = block_exclusive_scan<S_BLOCK>(cnt, s_scan, &total);
+    if (tid == 0) s_excl = lookback_prefix(lookback, 1, tile, total, 1, err);
+    __syncthreads();
+    uint64_t pos = s_excl + before;
+#pragma unroll
+    for (int j = 0; j < R_ITEMS; j++) {
+        if ((flags >> j) & 1) {
+            unique[pos] = skeys[p0 + j];
+            starts[pos] = start + p0 + j;
+            pos++;
+        }
+    }
+    if (start + tile_n == n && tid == 0) *n_unique = s_excl + total;
+    (void)R_TILE;
+}
+
+__global__ void k_run_counts(const uint64_t *__restrict__ starts, const unsigned long long *n_unique, uint64_t n,
+                             uint32_t *__restrict__ counts, uint32_t *err) {
+    const uint64_t nu = *n_unique;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nu; j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t end = j + 1 < nu ? starts[j + 1] : n;
+        const uint64_t c = end - starts[j];
+        if (c > 0xfffffffeull) atomicOr(err, ERR_COUNT_OVERFLOW);
+        counts[j] = (uint32_t)(c > 0xfffffffeull ? 0xfffffffeull : c);
+    }
+}
+
+template <class K>
+void launch_rle(const LaunchCfg &c, const K *sorted, uint64_t n, K *unique, uint64_t *starts,
+                unsigned long long *n_unique, uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err) {
+    cudaMemsetAsync(n_unique, 0, sizeof(unsigned long long), c.stream);
+    if (n == 0) return;
+    constexpr int R_TILE = S_BLOCK * RleCfg<K>::ITEMS;
+    const uint64_t tiles = (n + R_TILE - 1) / R_TILE;
+    cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t), c.stream);
+    cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * tiles, c.stream);
+    k_rle<K><<<(int)tiles, S_BLOCK, 0, c.stream>>>(sorted, n, unique, starts, n_unique, lookback, tile_ctr, err);
+}
+
+void launch_run_counts(const LaunchCfg &c, const uint64_t *starts, const unsigned long long *n_unique, uint64_t n,
+                       uint64_t cap, uint32_t *counts, uint32_t *err) {
+    uint64_t need = (cap + 255) / 256;
+    const uint64_t lim = (uint64_t)c.sms * 8;
+    k_run_counts<<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(starts, n_unique, n, counts, err);
+}
+
+template uint64_t *launch_radix_sort<uint64_t>(const LaunchCfg &, uint64_t *, uint64_t, int, const SortScratch &,
+                                               uint32_t *);
+template Key128 *launch_radix_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, const SortScratch &, uint32_t *);
+template void launch_rle<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, uint64_t *, uint64_t *,
+                                   unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
+template void launch_rle<Key128>(const LaunchCfg &, const Key128 *, uint64_t, Key128 *, uint64_t *,
+                                 unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
+
+}  // namespace turtle
