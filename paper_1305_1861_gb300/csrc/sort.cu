@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(S_BLOCK) k_rle(const K *__restrict__ sorted, u
     for (int j = 0; j < R_ITEMS; j++) {
         if ((flags >> j) & 1) {
             unique[pos] = skeys[p0 + j];
-            starts[pos] = start + p0 + j;
+            if (starts) starts[pos] = start + p0 + j;  // run starts are only needed for run lengths
             pos++;
         }
     }
