@@ -54,6 +54,7 @@ extern "C" {
 #define TURTLE_E_DEVICE (-7)    /* a device-side check failed (bounded wait expired, table full) */
 #define TURTLE_E_NODEV (-8)     /* no CUDA device is visible */
 #define TURTLE_E_CAPACITY (-9)  /* an output buffer is too small */
+#define TURTLE_E_TOO_LARGE (-10) /* input exceeds the fixed scratch of turtle_sort_compact_noalloc */
 
 /* ------------------------------------------------------------------ params */
 /* Tuning knobs. None of them changes the result, only speed and memory. */
@@ -200,6 +201,36 @@ int turtle_filter(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int key_wor
  */
 int turtle_sort_compact(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int key_words, int key_bits,
                         uint64_t *unique, uint32_t *counts, uint64_t *n_unique, void *stream);
+
+/*
+ * Allocation-free variant of turtle_sort_compact (no counterpart in the paper:
+ * it exists for callers, not for the method).
+ *
+ * For callers that may not allocate device memory at all -- no cudaMalloc,
+ * cudaFree, memory pool or caching allocator, not even through a context
+ * (turtle_ctx_create allocates) -- because a fixed device-memory budget is
+ * decided up front, because a host framework owns every allocation and only
+ * lends them a stream, or because an allocation could block or fail in a
+ * latency-critical loop. Arguments, results and errors are those of
+ * turtle_sort_compact, without the context.
+ *
+ * Scratch is one array of TURTLE_NOALLOC_SCRATCH_BYTES compiled into the
+ * library's device image: every GPU that loads libturtle keeps it reserved
+ * until the process exits. Limits: n <= TURTLE_NOALLOC_MAX_KEYS64 for 64-bit
+ * keys, n <= TURTLE_NOALLOC_MAX_KEYS128 for 128-bit keys; larger n returns
+ * TURTLE_E_TOO_LARGE before any work is queued.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins. All calls share the one array: calls whose work overlaps on
+ * the GPU (different streams or threads at the same time) race and corrupt
+ * each other's results; serialise them. The array keeps the previous call's
+ * contents; the call clears what must start at zero itself.
+ */
+#define TURTLE_NOALLOC_MAX_KEYS64 (1u << 20)
+#define TURTLE_NOALLOC_MAX_KEYS128 (1u << 19)
+#define TURTLE_NOALLOC_SCRATCH_BYTES 25727232ull
+int turtle_sort_compact_noalloc(const uint64_t *keys, uint64_t n, int key_words, int key_bits, uint64_t *unique,
+                                uint32_t *counts, uint64_t *n_unique, void *stream);
 
 #ifdef __cplusplus
 }

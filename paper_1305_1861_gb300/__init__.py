@@ -28,7 +28,7 @@ _p = ctypes.c_void_p
 TURTLE_OK = 0
 ERRORS = {-1: "TURTLE_E_ARG", -2: "TURTLE_E_NOMEM", -3: "TURTLE_E_CUDA", -4: "TURTLE_E_OVERFLOW",
           -5: "TURTLE_E_TIMEOUT", -6: "TURTLE_E_BUSY", -7: "TURTLE_E_DEVICE", -8: "TURTLE_E_NODEV",
-          -9: "TURTLE_E_CAPACITY"}
+          -9: "TURTLE_E_CAPACITY", -10: "TURTLE_E_TOO_LARGE"}
 STAGES = ["pack", "valid", "filter", "hist", "sort", "rle", "table", "recount", "threshold"]
 
 
@@ -104,6 +104,7 @@ def load():
         "turtle_extract": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, _p, _p, _p, _p]),
         "turtle_filter": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, _p, u64, _p, ctypes.c_int, _p, _p]),
         "turtle_sort_compact": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
+        "turtle_sort_compact_noalloc": (ctypes.c_int, [_p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -166,6 +167,22 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def turtle_sort_compact_noalloc(keys, key_bits: int, unique, counts, stream=None) -> int:
+    """Allocation-free sort-and-compact into caller-owned CUDA buffers; returns n_unique.
+
+    For callers that must not allocate device memory: the library's scratch is a
+    fixed array inside its device image (limits: TURTLE_NOALLOC_MAX_KEYS64 /
+    TURTLE_NOALLOC_MAX_KEYS128 keys). Calls that overlap on the GPU race.
+    """
+    n = keys.shape[0]
+    w = 2 if keys.dim() == 2 else 1
+    nu = u64()
+    rc = load().turtle_sort_compact_noalloc(keys.data_ptr(), n, w, key_bits, unique.data_ptr(), counts.data_ptr(),
+                                            ctypes.byref(nu), _stream_ptr(stream))
+    _check(rc, "turtle_sort_compact_noalloc")
+    return int(nu.value)
 
 
 class _CudaArray:

@@ -393,6 +393,7 @@ const char *turtle_strerror(int code) {
     case TURTLE_E_DEVICE: return "device-side check failed";
     case TURTLE_E_NODEV: return "no CUDA device";
     case TURTLE_E_CAPACITY: return "output buffer too small";
+    case TURTLE_E_TOO_LARGE: return "input larger than the fixed scratch of the allocation-free entry point";
     default: return "unknown error";
     }
 }
