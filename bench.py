@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample-reads", type=int, default=0, help="reads in the oracle sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--filter-bits", type=float, default=0.0, help="Bloom bits per window (0 = library default)")
+    ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1 = default)")
+    ap.add_argument("--recount-windows", action="store_true", help="recount by re-extracting every window")
+    ap.add_argument("--micro", action="store_true",
+                    help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()
 
 
@@ -152,9 +157,12 @@ def alg_bytes(stage: str, st: dict, lib) -> float:
     R = float(np.diff(lib.offsets[:2].astype(np.int64))[0]) if lib.n_reads else 100.0
     packed = (R / 4.0) / max(R - lib.k + 1, 1)  # 2-bit packed read bytes per window, one pass
     firsts = W - st["n_candidates"]
-    if stage == "filter":
-        return W * (packed + 32.0) + 32.0 * firsts + kw * st["n_candidates"]
+    if stage == "filter":  # packed input, one filter sector per window, write-back on first sightings, outputs
+        out = kw * W if st.get("n_firsts") else kw * st["n_candidates"]
+        return W * (packed + 32.0) + 32.0 * firsts + out
     if stage == "recount":
+        if st.get("n_firsts"):  # stream the firsts once, one table sector each, write-back when found
+            return st["n_firsts"] * (kw + 32.0) + 32.0 * st["n_unique"]
         return W * (packed + 32.0) + 32.0 * st["n_candidates"]
     if stage == "sort":  # one onesweep digit pass: every candidate read and written once
         return 2.0 * kw * st["n_candidates"]
@@ -174,6 +182,12 @@ def run_ours(args, rank, world):
     offs = torch.from_numpy(lib.offsets.astype(np.int64)).cuda()
     ctx = pkg.Context(dev)
     prm = pkg.Params.default(timing=1)
+    if args.filter_bits > 0:
+        prm.filter_bits_per_window = args.filter_bits
+    if args.l2_fetch >= 0:
+        prm.l2_fetch_bytes = args.l2_fetch
+    if args.recount_windows:
+        prm.recount_windows = 1
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)
@@ -289,8 +303,63 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _set_l2_fetch(nbytes: int):
+    """cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, nbytes) through the CUDA runtime torch loaded."""
+    import ctypes
+    import glob
+
+    import torch
+
+    cands = glob.glob(os.path.join(os.path.dirname(torch.__file__), "..", "nvidia", "cu*", "lib", "libcudart.so*"))
+    cands += ["libcudart.so.13", "libcudart.so"]
+    for c in cands:
+        try:
+            rt = ctypes.CDLL(c)
+            return rt.cudaDeviceSetLimit(ctypes.c_int(0x05), ctypes.c_size_t(nbytes))
+        except OSError:
+            continue
+    return -1
+
+
+def micro():
+    """Practical ceiling for the hash-probe kernels: random 8-byte reads (one 32-byte sector each) and
+    random 4-byte atomic adds over a table far larger than L2, with torch's gather / index_add kernels,
+    under several L2 fetch-granularity hints (0 = the context default)."""
+    import torch
+
+    n_words = 1 << 29  # 4 GiB of int64
+    table = torch.zeros(n_words, dtype=torch.int64, device="cuda")
+    idx = torch.randint(0, n_words, (1 << 28,), device="cuda")
+    ones = torch.ones(idx.numel(), dtype=torch.int32, device="cuda")
+    t32 = table.view(torch.int32)
+    res = {}
+
+    def timeit(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    for fetch in (0, 32, 64, 128):
+        rc = _set_l2_fetch(fetch) if fetch else 0
+        for name, fn in (("gather_8B", lambda: table[idx]), ("index_add_4B", lambda: t32.index_add_(0, idx * 2, ones))):
+            ms = timeit(fn)
+            res["%s_fetch%d" % (name, fetch)] = {"ms": round(ms, 3), "G_accesses_per_s": round(idx.numel() / ms / 1e6, 2),
+                                                 "set_limit_rc": rc}
+    print(json.dumps({"micro": "random 32-byte sectors over a 4 GiB table", "accesses": idx.numel(), **res}))
+
+
 def main():
     args = parse()
+    if args.micro:
+        micro()
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

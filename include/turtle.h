@@ -66,7 +66,15 @@ typedef struct {
     uint32_t n_patterns;           /* pattern-table entries, power of two, 1..4096; default 1024 */
     uint64_t pattern_seed;         /* SplitMix64 seed of the pattern table */
     uint32_t timing;               /* 1: record per-stage CUDA events (see turtle_stats) */
-    uint32_t reserved[7];
+    uint32_t l2_fetch_bytes;       /* L2 fetch granularity hint for the call (cudaLimitMaxL2FetchGranularity:
+                                      32..128; 0 = leave the context's setting). It is a context-wide
+                                      limit: set at the start of a call and restored before it returns. */
+    uint32_t recount_windows;      /* exact recount (step a5) by: 0 = first sightings (default): each key's
+                                      count is its run length among the sorted candidates plus 1 if one of
+                                      its windows was a first sighting, found by probing the recount table
+                                      with the first-sighting keys only; 1 = re-extracting every window and
+                                      counting it in the table. Both are exact. */
+    uint32_t reserved[5];
 } turtle_params;
 
 /* Fill *p with the defaults above. */
@@ -143,13 +151,13 @@ enum {
     TURTLE_STAGE_SORT,          /* radix sort: onesweep digit passes */
     TURTLE_STAGE_RLE,           /* run-length compaction of sorted candidates */
     TURTLE_STAGE_TABLE,         /* insert unique candidates into the recount table */
-    TURTLE_STAGE_RECOUNT,       /* pass 2: extraction + exact recount */
+    TURTLE_STAGE_RECOUNT,       /* exact recount: first sightings, or pass 2 over every window */
     TURTLE_STAGE_THRESHOLD,     /* keep count >= min_count in key order */
     TURTLE_STAGE_COUNT
 };
 
 typedef struct {
-    uint64_t n_windows, n_candidates, n_unique, n_out;
+    uint64_t n_windows, n_candidates, n_firsts, n_unique, n_out;
     uint64_t filter_bytes, table_bytes, scratch_bytes;
     uint32_t sort_passes;                       /* LSD digit passes run (8-bit digits) */
     uint32_t launches;                          /* kernels launched by the last call */

@@ -40,7 +40,8 @@ class TurtleError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("struct_size", u32), ("filter_bits_per_window", ctypes.c_float), ("pattern_bits", u32),
-                ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("reserved", u32 * 7)]
+                ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("l2_fetch_bytes", u32),
+                ("recount_windows", u32), ("reserved", u32 * 5)]
 
     @classmethod
     def default(cls, **kw) -> "Params":
@@ -66,7 +67,7 @@ class _DeviceResult(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("n_windows", u64), ("n_candidates", u64), ("n_unique", u64), ("n_out", u64),
+    _fields_ = [("n_windows", u64), ("n_candidates", u64), ("n_firsts", u64), ("n_unique", u64), ("n_out", u64),
                 ("filter_bytes", u64), ("table_bytes", u64), ("scratch_bytes", u64), ("sort_passes", u32),
                 ("launches", u32), ("stage_launches", u32 * 9), ("stage_ms", ctypes.c_float * 9)]
 

@@ -61,7 +61,7 @@ int log2_exact(uint64_t p) {
 }
 
 // Device counters read back at the sync points.
-enum { C_WINDOWS = 0, C_CAND, C_UNIQUE, C_OUT, C_N };
+enum { C_WINDOWS = 0, C_CAND, C_UNIQUE, C_OUT, C_FIRST, C_N };
 
 }  // namespace
 
@@ -157,7 +157,7 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
 }
 
 bool params_ok(const turtle_params &p) {
-    return p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
+    return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
            p.filter_bits_per_window <= 1024.f;
 }
@@ -240,14 +240,18 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         fg.pat_mask = prm.n_patterns - 1;
         st.filter_bytes = 32 * fg.n_sectors;
     }
+    const bool firsts_mode = use_filter && !prm.recount_windows;
     K *cand = (K *)ctx_alloc(c, sizeof(K) * W, s);
+    K *firsts = firsts_mode ? (K *)ctx_alloc(c, sizeof(K) * W, s) : nullptr;
     tm.start(TURTLE_STAGE_FILTER);
-    launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, W, err);
+    launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, W, firsts, ctr + C_FIRST, W, err);
     tm.stop(TURTLE_STAGE_FILTER);
     st.stage_launches[TURTLE_STAGE_FILTER] = 1;
     read_back(c, s);
     const uint64_t n_cand = c->h_ctr[C_CAND];
+    const uint64_t n_first = c->h_ctr[C_FIRST];
     st.n_candidates = n_cand;
+    st.n_firsts = n_first;
 
     // a4: sort + compact
     SortScratch ss{};
@@ -264,7 +268,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     st.stage_launches[TURTLE_STAGE_SORT] = n_cand > 1 ? passes + 2 : 0;
     K *unique = sorted == cand ? (K *)ss.alt : cand;
     uint64_t *starts = nullptr;
-    if (!use_filter) starts = (uint64_t *)ctx_alloc(c, 8 * (n_cand ? n_cand : 1), s);
+    if (!use_filter || firsts_mode) starts = (uint64_t *)ctx_alloc(c, 8 * (n_cand ? n_cand : 1), s);
     tm.start(TURTLE_STAGE_RLE);
     launch_rle<K>(lc, sorted, n_cand, unique, starts, ctr + C_UNIQUE, ss.lookback, ss.tile_ctr + 20, err);
     tm.stop(TURTLE_STAGE_RLE);
@@ -292,6 +296,12 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         st.n_unique = nu;
         st.n_out = nu;
     } else {
+        uint32_t *run = nullptr;  // run lengths of the sorted candidates (first-sighting recount only)
+        if (firsts_mode) {
+            run = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s);
+            launch_run_counts(lc, starts, ctr + C_UNIQUE, n_cand, n_cand, run, err);
+            st.stage_launches[TURTLE_STAGE_RLE] += 1;
+        }
         read_back(c, s);
         const uint64_t nu = c->h_ctr[C_UNIQUE];
         st.n_unique = nu;
@@ -300,13 +310,14 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         st.table_bytes = slot_bytes(KW) * slots;
         tm.start(TURTLE_STAGE_TABLE);
         launch_table_clear<K>(lc, table, slots);
-        launch_table_insert<K>(lc, unique, ctr + C_UNIQUE, nu, table, slots - 1, err);
+        launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, slots - 1, err);
         tm.stop(TURTLE_STAGE_TABLE);
         st.stage_launches[TURTLE_STAGE_TABLE] = 1;
         tm.start(TURTLE_STAGE_RECOUNT);
-        launch_pass2<K>(lc, L, k, P, V, table, slots - 1, W >= 0xfffffffeull, err);
+        if (firsts_mode) launch_add_firsts<K>(lc, firsts, n_first, table, slots - 1, err);
+        else launch_pass2<K>(lc, L, k, P, V, table, slots - 1, W >= 0xfffffffeull, err);
         tm.stop(TURTLE_STAGE_RECOUNT);
-        st.stage_launches[TURTLE_STAGE_RECOUNT] = 1;
+        st.stage_launches[TURTLE_STAGE_RECOUNT] = (!firsts_mode || n_first) ? 1 : 0;
         K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s, true);
         uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nu ? nu : 1), s, true);
         tm.start(TURTLE_STAGE_THRESHOLD);
@@ -344,6 +355,24 @@ int fail_code(cudaStream_t s, turtle_ctx *c, int code) {
     return code;
 }
 
+// Scoped L2 fetch-granularity hint: random 8- to 16-byte probes need one 32-byte sector,
+// and a larger fetch on every miss multiplies their DRAM traffic.
+struct L2Fetch {
+    size_t old = 0;
+    bool set = false;
+    explicit L2Fetch(uint32_t bytes) {
+        if (!bytes) return;
+        if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) == cudaSuccess &&
+            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, bytes) == cudaSuccess)
+            set = true;
+        cudaGetLastError();
+    }
+    ~L2Fetch() {
+        if (set) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, old);
+        cudaGetLastError();
+    }
+};
+
 int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
                       uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, cudaStream_t s,
                       DeviceOut &o) {
@@ -352,6 +381,7 @@ int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, con
     if (!params_ok(prm)) return TURTLE_E_ARG;
     try {
         ctx_begin(c, s);
+        L2Fetch l2(prm.l2_fetch_bytes);
         if (k <= 32) run_count<uint64_t>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
         else run_count<Key128>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
         ctx_end(c, s);
@@ -379,6 +409,7 @@ void turtle_params_default(turtle_params *p) {
     p->n_patterns = 1024;
     p->pattern_seed = 0x7475727469ull;
     p->timing = 0;
+    p->l2_fetch_bytes = 0;
 }
 
 const char *turtle_strerror(int code) {

@@ -28,15 +28,15 @@ constexpr int P1_STAGE = 256;                // keys per candidate flush
 constexpr int P1_BUF = P1_STAGE + WARP;      // warp staging buffer capacity
 
 template <class K>
-__device__ __forceinline__ void flush_full(K *wbuf, int &nbuf, K *cand, unsigned long long *cand_count,
-                                           uint64_t cand_cap, uint32_t *err, int lane) {
+__device__ __forceinline__ void flush_full(K *wbuf, int &nbuf, K *out, unsigned long long *cursor,
+                                           uint64_t cap, uint32_t *err, int lane) {
     __syncwarp();
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)P1_STAGE);
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)P1_STAGE);
     base = __shfl_sync(FULL, base, 0);
-    if (base + P1_STAGE <= cand_cap) {
+    if (base + P1_STAGE <= cap) {
 #pragma unroll
-        for (int j = 0; j < P1_STAGE / WARP; j++) store_key(cand + base + lane + WARP * j, wbuf[lane + WARP * j]);
+        for (int j = 0; j < P1_STAGE / WARP; j++) store_key(out + base + lane + WARP * j, wbuf[lane + WARP * j]);
     } else if (lane == 0) {
         atomicOr(err, ERR_CAND_OVERFLOW);
     }
@@ -49,23 +49,45 @@ __device__ __forceinline__ void flush_full(K *wbuf, int &nbuf, K *cand, unsigned
     nbuf = rem;
 }
 
-template <class K, bool USE_FILTER>
+template <class K>
+__device__ __forceinline__ void flush_rest(K *wbuf, int nbuf, K *out, unsigned long long *cursor, uint64_t cap,
+                                           uint32_t *err, int lane) {
+    __syncwarp();
+    if (nbuf <= 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)nbuf);
+    base = __shfl_sync(FULL, base, 0);
+    if (base + nbuf <= cap) {
+        for (int j = lane; j < nbuf; j += WARP) store_key(out + base + j, wbuf[j]);
+    } else if (lane == 0) {
+        atomicOr(err, ERR_CAND_OVERFLOW);
+    }
+}
+
+// Every valid window lands in exactly one stream: "seen" windows go to cand, and
+// (when EMIT_FIRSTS) the windows whose atomicOr completed their pattern go to
+// firsts. Since that atomicOr is one linearizable operation, at most one
+// occurrence of a key can ever be a first.
+template <class K, bool USE_FILTER, bool EMIT_FIRSTS>
 __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
                                                     uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
                                                     const uint64_t *__restrict__ patterns, uint32_t pat_mask,
                                                     K *cand, unsigned long long *cand_count, uint64_t cand_cap,
+                                                    K *firsts, unsigned long long *first_count, uint64_t first_cap,
                                                     uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
     K *s_buf = reinterpret_cast<K *>(smem);
-    uint64_t *s_pat = reinterpret_cast<uint64_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS);
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
     if (USE_FILTER)
         for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    K *wbuf = s_buf + warp * P1_BUF;
-    int nbuf = 0;
+    K *wbuf = s_buf + warp * P1_BUF * NBUF;
+    K *fbuf = wbuf + P1_BUF;  // firsts staging (EMIT_FIRSTS only)
+    int nbuf = 0, nfirst = 0;
     const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
     for (uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp; t < tiles; t += (uint64_t)gridDim.x * P1_WARPS) {
         const uint64_t base = t * P1_TILE;
@@ -112,19 +134,17 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             if (seen[i]) wbuf[nbuf + __popc(b & lt)] = key[i];
             nbuf += __popc(b);
             if (nbuf >= P1_STAGE) flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+            if (EMIT_FIRSTS) {
+                const bool f = ok[i] && !seen[i];
+                const uint32_t bf = __ballot_sync(FULL, f);
+                if (f) fbuf[nfirst + __popc(bf & lt)] = key[i];
+                nfirst += __popc(bf);
+                if (nfirst >= P1_STAGE) flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane);
+            }
         }
     }
-    __syncwarp();
-    if (nbuf > 0) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)nbuf);
-        base = __shfl_sync(FULL, base, 0);
-        if (base + nbuf <= cand_cap) {
-            for (int j = lane; j < nbuf; j += WARP) store_key(cand + base + j, wbuf[j]);
-        } else if (lane == 0) {
-            atomicOr(err, ERR_CAND_OVERFLOW);
-        }
-    }
+    flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+    if (EMIT_FIRSTS) flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane);
 }
 
 template <class K>
@@ -147,10 +167,12 @@ __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys,
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
-                  uint32_t *err) {
+                  K *firsts, unsigned long long *first_count, uint64_t first_cap, uint32_t *err) {
     const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
-    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS + (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
-    auto kern = use_filter ? k_pass1<K, true> : k_pass1<K, false>;
+    const bool emit_firsts = use_filter && firsts != nullptr;
+    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
+                        (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
+    auto kern = emit_firsts ? k_pass1<K, true, true> : (use_filter ? k_pass1<K, true, false> : k_pass1<K, false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P1_BLOCK, smem);
@@ -159,7 +181,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     uint64_t cap = (uint64_t)c.sms * per_sm;
     int grid = (int)(need < cap ? (need ? need : 1) : cap);
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
-                                             cand, cand_count, cand_cap, err);
+                                             cand, cand_count, cand_cap, firsts, first_count, first_cap, err);
 }
 
 template <class K>
@@ -171,9 +193,11 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 }
 
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
-                                     bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint32_t *);
+                                     bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
+                                     unsigned long long *, uint64_t, uint32_t *);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
-                                   bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, uint32_t *);
+                                   bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
+                                   unsigned long long *, uint64_t, uint32_t *);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

@@ -47,11 +47,12 @@ struct FilterGeom {
 };
 
 // a2+a3: pass 1. Emits the canonical key of every valid window whose filter test says "seen"
-// (every valid window when use_filter is false) to cand[0 .. *cand_count).
+// (every valid window when use_filter is false) to cand[0 .. *cand_count); with a filter and a
+// non-null firsts buffer, the other windows (first sightings) go to firsts[0 .. *first_count).
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
-                  uint32_t *err);
+                  K *firsts, unsigned long long *first_count, uint64_t first_cap, uint32_t *err);
 // a3 alone on a key array.
 template <class K>
 void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const FilterGeom &f, int set, uint8_t *seen);
@@ -82,9 +83,13 @@ template <class K> struct Slot;
 size_t slot_bytes(int key_words);
 template <class K>
 void launch_table_clear(const LaunchCfg &c, void *table, uint64_t slots);
+// counts == nullptr: every slot starts at 0; otherwise slot j starts at counts[j].
 template <class K>
-void launch_table_insert(const LaunchCfg &c, const K *unique, const unsigned long long *n_unique, uint64_t cap,
-                         void *table, uint64_t mask, uint32_t *err);
+void launch_table_insert(const LaunchCfg &c, const K *unique, const uint32_t *counts,
+                         const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask, uint32_t *err);
+// a5 (first-sighting form): +1 on the slot of every key of firsts[0 .. n) that is in the table.
+template <class K>
+void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask, uint32_t *err);
 template <class K>
 void launch_pass2(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   void *table, uint64_t mask, bool check_overflow, uint32_t *err);

@@ -50,15 +50,16 @@ __device__ __forceinline__ Slot<Key128> slot_load(const Slot<Key128> *p) {
 __device__ __forceinline__ uint64_t slot_index(uint64_t h) { return h ^ (h >> 29); }
 
 template <class K>
-__global__ void k_table_insert(const K *__restrict__ unique, const unsigned long long *n_unique, Slot<K> *table,
-                               uint64_t mask, uint32_t *err) {
+__global__ void k_table_insert(const K *__restrict__ unique, const uint32_t *__restrict__ counts,
+                               const unsigned long long *n_unique, Slot<K> *table, uint64_t mask, uint32_t *err) {
     const uint64_t nu = *n_unique;
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nu; j += (uint64_t)gridDim.x * blockDim.x) {
         const K key = unique[j];
+        const uint32_t c0 = counts ? counts[j] : 0u;
         uint64_t s = slot_index(key_hash(key)) & mask;
         bool done = false;
         for (uint64_t probe = 0; probe <= mask; probe++, s = (s + 1) & mask) {
-            if (atomicCAS(&table[s].count, EMPTY_COUNT, 0u) == EMPTY_COUNT) {  // distinct keys: claim any free slot
+            if (atomicCAS(&table[s].count, EMPTY_COUNT, c0) == EMPTY_COUNT) {  // distinct keys: claim any free slot
                 slot_put(&table[s], key);
                 done = true;
                 break;
@@ -109,6 +110,50 @@ __global__ void __launch_bounds__(P2_BLOCK) k_pass2(const uint64_t *__restrict__
                     } else {
                         atomicAdd(&table[s[i]].count, 1u);
                     }
+                    break;
+                }
+                s[i] = (s[i] + 1) & mask;
+                sl[i] = slot_load(table + s[i]);
+            }
+        }
+    }
+}
+
+// First-sighting recount. In pass 1 each valid window went either to the
+// candidates (filter said "seen") or to the firsts (its atomicOr completed the
+// pattern), and at most one occurrence of a key can be a first. A candidate key's
+// slot starts at its run length in the sorted candidates; adding 1 for its first
+// sighting, if it has one, gives the exact number of occurrences. Keys absent from
+// the table have all their occurrences among the firsts, so they occur once.
+constexpr int F_ILP = 4;
+
+template <class K>
+__global__ void __launch_bounds__(256) k_add_firsts(const K *__restrict__ firsts, uint64_t n, Slot<K> *table,
+                                                    uint64_t mask, uint32_t *err) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; base < n; base += stride * F_ILP) {
+        K key[F_ILP];
+        uint64_t s[F_ILP];
+        Slot<K> sl[F_ILP];
+        bool ok[F_ILP];
+#pragma unroll
+        for (int i = 0; i < F_ILP; i++) {
+            const uint64_t j = base + i * stride;
+            ok[i] = j < n;
+            if (ok[i]) {
+                key[i] = firsts[j];
+                s[i] = slot_index(key_hash(key[i])) & mask;
+                sl[i] = slot_load(table + s[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < F_ILP; i++) {
+            if (!ok[i]) continue;
+            for (uint64_t probe = 0; probe <= mask; probe++) {
+                if (sl[i].count == EMPTY_COUNT) break;
+                if (slot_has(sl[i], key[i])) {
+                    const uint32_t old = atomicAdd(&table[s[i]].count, 1u);
+                    if (old >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
                     break;
                 }
                 s[i] = (s[i] + 1) & mask;
@@ -197,12 +242,25 @@ void launch_table_clear(const LaunchCfg &c, void *table, uint64_t slots) {
 }
 
 template <class K>
-void launch_table_insert(const LaunchCfg &c, const K *unique, const unsigned long long *n_unique, uint64_t cap,
-                         void *table, uint64_t mask, uint32_t *err) {
+void launch_table_insert(const LaunchCfg &c, const K *unique, const uint32_t *counts,
+                         const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask,
+                         uint32_t *err) {
     uint64_t need = (cap + 255) / 256;
     const uint64_t lim = (uint64_t)c.sms * 8;
     k_table_insert<K><<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(
-        unique, n_unique, reinterpret_cast<Slot<K> *>(table), mask, err);
+        unique, counts, n_unique, reinterpret_cast<Slot<K> *>(table), mask, err);
+}
+
+template <class K>
+void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask, uint32_t *err) {
+    if (n == 0) return;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_add_firsts<K>, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t need = (n + 256 * F_ILP - 1) / (256 * F_ILP);
+    const uint64_t lim = (uint64_t)c.sms * per_sm;
+    k_add_firsts<K><<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(
+        firsts, n, reinterpret_cast<Slot<K> *>(table), mask, err);
 }
 
 template <class K>
@@ -236,8 +294,9 @@ size_t slot_bytes(int key_words) { return key_words == 1 ? sizeof(Slot<uint64_t>
 
 #define INST(K)                                                                                                  \
     template void launch_table_clear<K>(const LaunchCfg &, void *, uint64_t);                                    \
-    template void launch_table_insert<K>(const LaunchCfg &, const K *, const unsigned long long *, uint64_t,     \
-                                         void *, uint64_t, uint32_t *);                                          \
+    template void launch_table_insert<K>(const LaunchCfg &, const K *, const uint32_t *,                         \
+                                         const unsigned long long *, uint64_t, void *, uint64_t, uint32_t *);    \
+    template void launch_add_firsts<K>(const LaunchCfg &, const K *, uint64_t, void *, uint64_t, uint32_t *);     \
     template void launch_pass2<K>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *, \
                                   void *, uint64_t, bool, uint32_t *);                                           \
     template void launch_threshold<K>(const LaunchCfg &, const K *, uint64_t, const void *, uint64_t, uint32_t,  \

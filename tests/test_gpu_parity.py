@@ -188,11 +188,26 @@ def test_count_small_library_all_k(ctx, k, min_count):
     _check_count(ctx, lib.bases, lib.offsets, k, min_count)
 
 
+@pytest.mark.parametrize("k", [5, 31, 32, 33, 64])
+def test_count_recount_by_windows(ctx, k):
+    """The literal second pass (re-extract every window, count it in the table) agrees too."""
+    import paper_1305_1861_gb300 as pkg
+
+    lib = synth.small(seed=40 + k, scale=0.02)
+    st = _check_count(ctx, lib.bases, lib.offsets, k, 2, pkg.Params.default(recount_windows=1))
+    assert st["n_firsts"] == 0
+    st = _check_count(ctx, lib.bases, lib.offsets, k, 2, pkg.Params.default(recount_windows=0))
+    assert st["n_firsts"] + st["n_candidates"] == st["n_windows"]
+
+
 def test_count_mixed_reads_with_ambiguous_calls(ctx):
+    import paper_1305_1861_gb300 as pkg
+
     reads = _mixed_reads(11, 3000, 0, 300)
     bases, offs = brute.pack(reads)
     for k in (7, 31, 40, 64):
-        _check_count(ctx, bases, offs, k, 2)
+        for rw in (0, 1):
+            _check_count(ctx, bases, offs, k, 2, pkg.Params.default(recount_windows=rw))
 
 
 def test_count_small_config_full_size(ctx):
@@ -207,9 +222,10 @@ def test_count_saturated_filter_has_no_false_negatives(ctx):
     import paper_1305_1861_gb300 as pkg
 
     lib = synth.small(seed=7, scale=0.05)
-    p = pkg.Params.default(filter_bits_per_window=0.01, pattern_bits=1, n_patterns=1)
-    st = _check_count(ctx, lib.bases, lib.offsets, 31, 2, p)
-    assert st["filter_bytes"] <= 4096 and st["n_unique"] > st["n_out"]  # false-positive singletons were recounted
+    for rw in (0, 1):
+        p = pkg.Params.default(filter_bits_per_window=0.01, pattern_bits=1, n_patterns=1, recount_windows=rw)
+        st = _check_count(ctx, lib.bases, lib.offsets, 31, 2, p)
+        assert st["filter_bytes"] <= 4096 and st["n_unique"] > st["n_out"]  # false-positive singletons recounted
 
 
 def test_count_one_kmer_above_2_16(ctx):
