@@ -73,6 +73,7 @@ struct turtle_ctx {
     unsigned long long *d_ctr = nullptr;  // C_N counters
     unsigned long long *h_ctr = nullptr;  // pinned mirror
     uint32_t *h_err = nullptr;
+    uint64_t *h_hist = nullptr;  // pinned copy of the sort histograms (16 passes x 256 bins)
     // pattern table cache
     uint64_t *d_patterns = nullptr;
     uint64_t pat_seed = 0;
@@ -243,10 +244,15 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     const bool firsts_mode = use_filter && !prm.recount_windows;
     K *cand = (K *)ctx_alloc(c, sizeof(K) * W, s);
     K *firsts = firsts_mode ? (K *)ctx_alloc(c, sizeof(K) * W, s) : nullptr;
+    const int passes = sort_passes_for(2 * k);
+    uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ck(cudaMemsetAsync(hist, 0, 8 * 256 * passes, s));
     tm.start(TURTLE_STAGE_FILTER);
-    launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, W, firsts, ctr + C_FIRST, W, err);
+    launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, W, firsts, ctr + C_FIRST, W, hist, passes,
+                    err);
     tm.stop(TURTLE_STAGE_FILTER);
     st.stage_launches[TURTLE_STAGE_FILTER] = 1;
+    ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
     read_back(c, s);
     const uint64_t n_cand = c->h_ctr[C_CAND];
     const uint64_t n_first = c->h_ctr[C_FIRST];
@@ -256,16 +262,20 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     // a4: sort + compact
     SortScratch ss{};
     ss.alt = ctx_alloc(c, sizeof(K) * (n_cand ? n_cand : 1), s);
-    const int passes = sort_passes_for(2 * k);
-    ss.hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ss.hist = hist;
+    uint32_t skip = 0;  // digit passes where every candidate has the same digit
+    for (int p = 0; p < passes; p++)
+        for (int d = 0; d < 256; d++)
+            if (c->h_hist[p * 256 + d] == n_cand) skip |= 1u << p;
     ss.lookback_words = sort_lookback_words(n_cand, KW);
     ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
     ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
     tm.start(TURTLE_STAGE_SORT);
-    K *sorted = launch_radix_sort<K>(lc, cand, n_cand, 2 * k, ss, err);
+    int passes_run = 0;
+    K *sorted = launch_radix_sort<K>(lc, cand, n_cand, 2 * k, ss, err, true, skip, &passes_run);
     tm.stop(TURTLE_STAGE_SORT);
-    st.sort_passes = n_cand > 1 ? passes : 0;
-    st.stage_launches[TURTLE_STAGE_SORT] = n_cand > 1 ? passes + 2 : 0;
+    st.sort_passes = (uint32_t)passes_run;
+    st.stage_launches[TURTLE_STAGE_SORT] = n_cand > 1 ? passes_run + 1 : 0;
     K *unique = sorted == cand ? (K *)ss.alt : cand;
     uint64_t *starts = nullptr;
     if (!use_filter || firsts_mode) starts = (uint64_t *)ctx_alloc(c, 8 * (n_cand ? n_cand : 1), s);
@@ -462,6 +472,7 @@ int turtle_ctx_create(int device, turtle_ctx **out) {
         ck(cudaMalloc(&c->d_ctr, sizeof(unsigned long long) * C_N));
         ck(cudaMallocHost(&c->h_ctr, sizeof(unsigned long long) * C_N));
         ck(cudaMallocHost(&c->h_err, 64));
+        ck(cudaMallocHost(&c->h_hist, 8 * 256 * 16));
         for (auto &e : c->ev) ck(cudaEventCreate(&e));
     } catch (Fail f) {
         turtle_ctx_destroy(c);
@@ -483,6 +494,7 @@ void turtle_ctx_destroy(turtle_ctx *c) {
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_hist) cudaFreeHost(c->h_hist);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->pool) cudaMemPoolDestroy(c->pool);

@@ -64,6 +64,16 @@ __device__ __forceinline__ void flush_rest(K *wbuf, int nbuf, K *out, unsigned l
     }
 }
 
+// Digit counts of every radix pass for the keys being flushed (fused into pass 1 so the
+// sorter does not have to read the candidates once more just to histogram them).
+template <class K>
+__device__ __forceinline__ void hist_keys(const K *buf, int count, uint32_t *s_hist, int passes, int lane) {
+    for (int j = lane; j < count; j += WARP) {
+        const K key = buf[j];
+        for (int p = 0; p < passes; p++) atomicAdd(&s_hist[p * 256 + KeyT<K>::digit(key, 8 * p)], 1u);
+    }
+}
+
 // Every valid window lands in exactly one stream: "seen" windows go to cand, and
 // (when EMIT_FIRSTS) the windows whose atomicOr completed their pattern go to
 // firsts. Since that atomicOr is one linearizable operation, at most one
@@ -74,13 +84,15 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     const uint64_t *__restrict__ patterns, uint32_t pat_mask,
                                                     K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                                                     K *firsts, unsigned long long *first_count, uint64_t first_cap,
-                                                    uint32_t *err) {
+                                                    uint64_t *hist, int hist_passes, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
     K *s_buf = reinterpret_cast<K *>(smem);
-    uint64_t *s_pat = reinterpret_cast<uint64_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + 256 * hist_passes);
     if (USE_FILTER)
         for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
+    for (int i = threadIdx.x; i < 256 * hist_passes; i += P1_BLOCK) s_hist[i] = 0;
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -133,7 +145,11 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             const uint32_t b = __ballot_sync(FULL, seen[i]);
             if (seen[i]) wbuf[nbuf + __popc(b & lt)] = key[i];
             nbuf += __popc(b);
-            if (nbuf >= P1_STAGE) flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+            if (nbuf >= P1_STAGE) {
+                __syncwarp();
+                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane);
+                flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+            }
             if (EMIT_FIRSTS) {
                 const bool f = ok[i] && !seen[i];
                 const uint32_t bf = __ballot_sync(FULL, f);
@@ -143,8 +159,13 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             }
         }
     }
+    __syncwarp();
+    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane);
     flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
     if (EMIT_FIRSTS) flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256 * hist_passes; i += P1_BLOCK)
+        if (s_hist[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)s_hist[i]);
 }
 
 template <class K>
@@ -167,10 +188,12 @@ __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys,
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
-                  K *firsts, unsigned long long *first_count, uint64_t first_cap, uint32_t *err) {
+                  K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
+                  uint32_t *err) {
     const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     const bool emit_firsts = use_filter && firsts != nullptr;
-    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
+    if (!hist) hist_passes = 0;
+    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) + 4 * 256 * hist_passes +
                         (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
     auto kern = emit_firsts ? k_pass1<K, true, true> : (use_filter ? k_pass1<K, true, false> : k_pass1<K, false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -181,7 +204,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     uint64_t cap = (uint64_t)c.sms * per_sm;
     int grid = (int)(need < cap ? (need ? need : 1) : cap);
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
-                                             cand, cand_count, cand_cap, firsts, first_count, first_cap, err);
+                                             cand, cand_count, cand_cap, firsts, first_count, first_cap, hist,
+                                             hist_passes, err);
 }
 
 template <class K>
@@ -194,10 +218,10 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
-                                     unsigned long long *, uint64_t, uint32_t *);
+                                     unsigned long long *, uint64_t, uint64_t *, int, uint32_t *);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
-                                   unsigned long long *, uint64_t, uint32_t *);
+                                   unsigned long long *, uint64_t, uint64_t *, int, uint32_t *);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

@@ -49,10 +49,12 @@ struct FilterGeom {
 // a2+a3: pass 1. Emits the canonical key of every valid window whose filter test says "seen"
 // (every valid window when use_filter is false) to cand[0 .. *cand_count); with a filter and a
 // non-null firsts buffer, the other windows (first sightings) go to firsts[0 .. *first_count).
+// hist (non-null): += the 256-bin digit counts of the candidates for radix passes 0..hist_passes-1.
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
-                  K *firsts, unsigned long long *first_count, uint64_t first_cap, uint32_t *err);
+                  K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
+                  uint32_t *err);
 // a3 alone on a key array.
 template <class K>
 void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const FilterGeom &f, int set, uint8_t *seen);
@@ -68,8 +70,11 @@ struct SortScratch {
 int sort_passes_for(int key_bits);
 uint64_t sort_lookback_words(uint64_t n, int key_words);
 // Sorts keys[0..n) by their low key_bits bits. Returns the buffer that holds the result (keys or scratch.alt).
+// hist_ready: s.hist already holds the digit counts of every pass (e.g. accumulated by pass 1);
+// bit p of skip_mask skips digit pass p (only valid when every key has the same digit p).
 template <class K>
-K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err);
+K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err,
+                     bool hist_ready = false, uint32_t skip_mask = 0, int *passes_run = nullptr);
 // unique/starts from sorted keys; *n_unique (device) receives the distinct count.
 template <class K>
 void launch_rle(const LaunchCfg &c, const K *sorted, uint64_t n, K *unique, uint64_t *starts,

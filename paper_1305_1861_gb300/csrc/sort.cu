@@ -66,10 +66,10 @@ __global__ void k_scan_bins(uint64_t *hist) {
 }
 
 template <class K>
-__global__ void __launch_bounds__(S_BLOCK) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
-                                                      int shift, const uint64_t *__restrict__ bin_base,
-                                                      uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
-                                                      uint32_t *err) {
+__global__ void __launch_bounds__(S_BLOCK, 3) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
+                                                         int shift, const uint64_t *__restrict__ bin_base,
+                                                         uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
+                                                         uint32_t *err) {
     constexpr int ITEMS = SortCfg<K>::ITEMS;
     constexpr int TILE = S_BLOCK * ITEMS;
     __shared__ K skeys[TILE];
@@ -85,50 +85,54 @@ __global__ void __launch_bounds__(S_BLOCK) k_onesweep(const K *__restrict__ in, 
     __syncthreads();
     const uint64_t tile = s_tile;
     const uint64_t start = tile * TILE;
-    const uint64_t wstart = start + (uint64_t)warp * ITEMS * WARP;
+    const uint64_t wstart = start + (uint64_t)warp * ITEMS * WARP;  // warp w owns a contiguous run of the tile
     const uint32_t lt = lanemask_lt();
 
     K key[ITEMS];
-    uint32_t rank[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
         const uint64_t idx = wstart + i * WARP + lane;
         if (idx < n) key[i] = in[idx];
     }
-    // Stable local ranking: order is (warp, row, lane) = input order.
+    // 1. early counts: per-warp digit counts (order-free shared atomics)
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++)
+        if (wstart + i * WARP + lane < n) atomicAdd(&whist[warp][KeyT<K>::digit(key[i], shift)], 1u);
+    __syncthreads();
+    // 2. thread tid owns digit tid: tile count, publish it, tile-local start, per-warp starts
+    uint32_t tcount = 0;
+#pragma unroll
+    for (int w = 0; w < S_WARPS; w++) tcount += whist[w][tid];
+    if (tile > 0) st_relaxed(lookback + tile * BINS + tid, lb_pack(LB_AGG, epoch, tcount));
+    const uint32_t texcl = block_exclusive_scan<S_BLOCK>(tcount, s_scan, nullptr);
+    s_texcl[tid] = texcl;
+    {
+        uint32_t run = texcl;
+#pragma unroll
+        for (int w = 0; w < S_WARPS; w++) {
+            const uint32_t v = whist[w][tid];
+            whist[w][tid] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    // 3. stable ranking straight into shared memory: rows in order, lanes in order within a row.
+    //    The leader of each group of equal digits advances the warp's counter by the group size;
+    //    a warp's shared-memory atomics complete in issue order, so rows cannot overtake each other.
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
         const bool valid = wstart + i * WARP + lane < n;
         const uint32_t d = valid ? KeyT<K>::digit(key[i], shift) : (BINS + lane);
         const uint32_t peers = __match_any_sync(FULL, d);
-        uint32_t pre = 0;
-        if (valid) pre = whist[warp][d];
-        __syncwarp();
-        if (valid && lane == 31 - __clz(peers)) whist[warp][d] = pre + __popc(peers);
-        __syncwarp();
-        rank[i] = pre + __popc(peers & lt);
+        const int leader = 31 - __clz(peers);
+        uint32_t pos = 0;
+        if (valid && lane == leader) pos = atomicAdd(&whist[warp][d], (uint32_t)__popc(peers));
+        pos = __shfl_sync(FULL, pos, leader);
+        if (valid) skeys[pos + __popc(peers & lt)] = key[i];
     }
-    __syncthreads();
-    // Thread tid owns digit tid: exclusive offsets over warps, tile count, tile-local digit start.
-    uint32_t tcount = 0;
-#pragma unroll
-    for (int w = 0; w < S_WARPS; w++) {
-        const uint32_t v = whist[w][tid];
-        whist[w][tid] = tcount;
-        tcount += v;
-    }
-    const uint32_t texcl = block_exclusive_scan<S_BLOCK>(tcount, s_scan, nullptr);
-    s_texcl[tid] = texcl;
+    // 4. global offsets of this tile's digits (predecessors have usually published by now)
     const uint64_t excl = lookback_prefix(lookback + tid, BINS, tile, tcount, epoch, err);
     s_glob[tid] = bin_base[tid] + excl - texcl;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        if (wstart + i * WARP + lane < n) {
-            const uint32_t d = KeyT<K>::digit(key[i], shift);
-            skeys[s_texcl[d] + whist[warp][d] + rank[i]] = key[i];
-        }
-    }
     __syncthreads();
     const uint32_t tile_n = (uint32_t)(n - start < (uint64_t)TILE ? n - start : TILE);
     for (uint32_t p = tid; p < tile_n; p += S_BLOCK) {
@@ -138,22 +142,28 @@ __global__ void __launch_bounds__(S_BLOCK) k_onesweep(const K *__restrict__ in, 
 }
 
 template <class K>
-K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err) {
+K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err,
+                     bool hist_ready, uint32_t skip_mask, int *passes_run) {
     const int passes = sort_passes_for(key_bits);
+    if (passes_run) *passes_run = 0;
     if (n <= 1 || passes == 0) return keys;
     constexpr int TILE = S_BLOCK * SortCfg<K>::ITEMS;
     const uint64_t tiles = (n + TILE - 1) / TILE;
-    cudaMemsetAsync(s.hist, 0, sizeof(uint64_t) * passes * BINS, c.stream);
     cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
     cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
-    uint64_t need = (n + S_BLOCK - 1) / S_BLOCK;
-    const uint64_t cap = (uint64_t)c.sms * 4;
-    k_hist<K><<<(int)(need < cap ? need : cap), S_BLOCK, 0, c.stream>>>(keys, n, passes, s.hist);
+    if (!hist_ready) {
+        cudaMemsetAsync(s.hist, 0, sizeof(uint64_t) * passes * BINS, c.stream);
+        uint64_t need = (n + S_BLOCK - 1) / S_BLOCK;
+        const uint64_t cap = (uint64_t)c.sms * 4;
+        k_hist<K><<<(int)(need < cap ? need : cap), S_BLOCK, 0, c.stream>>>(keys, n, passes, s.hist);
+    }
     k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
     K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
     for (int p = 0; p < passes; p++) {
+        if ((skip_mask >> p) & 1u) continue;  // every key has the same digit here: the pass would be a copy
         k_onesweep<K><<<(int)tiles, S_BLOCK, 0, c.stream>>>(src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS,
                                                            s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err);
+        if (passes_run) (*passes_run)++;
         K *t = src;
         src = dst;
         dst = t;
@@ -245,8 +255,9 @@ void launch_run_counts(const LaunchCfg &c, const uint64_t *starts, const unsigne
 }
 
 template uint64_t *launch_radix_sort<uint64_t>(const LaunchCfg &, uint64_t *, uint64_t, int, const SortScratch &,
-                                               uint32_t *);
-template Key128 *launch_radix_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, const SortScratch &, uint32_t *);
+                                               uint32_t *, bool, uint32_t, int *);
+template Key128 *launch_radix_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, const SortScratch &, uint32_t *,
+                                           bool, uint32_t, int *);
 template void launch_rle<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, uint64_t *, uint64_t *,
                                    unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
 template void launch_rle<Key128>(const LaunchCfg &, const Key128 *, uint64_t, Key128 *, uint64_t *,
