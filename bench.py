@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--filter-bits", type=float, default=0.0, help="Bloom bits per window (0 = library default)")
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1 = default)")
     ap.add_argument("--recount-windows", action="store_true", help="recount by re-extracting every window")
+    ap.add_argument("--member-filter", action="store_true", help="screen first sightings with a membership bitmap")
     ap.add_argument("--micro", action="store_true",
                     help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()
@@ -188,6 +189,8 @@ def run_ours(args, rank, world):
         prm.l2_fetch_bytes = args.l2_fetch
     if args.recount_windows:
         prm.recount_windows = 1
+    if args.member_filter:
+        prm.member_filter = 1
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)

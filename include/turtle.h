@@ -74,7 +74,9 @@ typedef struct {
                                       its windows was a first sighting, found by probing the recount table
                                       with the first-sighting keys only; 1 = re-extracting every window and
                                       counting it in the table. Both are exact. */
-    uint32_t reserved[5];
+    uint32_t member_filter;        /* 1: screen first-sighting keys with a small membership bitmap of the
+                                      candidates before probing the recount table (default 0: probe all) */
+    uint32_t reserved[4];
 } turtle_params;
 
 /* Fill *p with the defaults above. */

@@ -315,23 +315,33 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         read_back(c, s);
         const uint64_t nu = c->h_ctr[C_UNIQUE];
         st.n_unique = nu;
-        const uint64_t slots = pow2_at_least(2 * nu + 16);
-        void *table = ctx_alloc(c, slot_bytes(KW) * slots, s);
-        st.table_bytes = slot_bytes(KW) * slots;
+        // load factor <= 0.4: a line overflows into the next one rarely
+        const uint64_t lines = pow2_at_least((uint64_t)(nu / (0.4 * slots_per_line(KW))) + 1);
+        const uint64_t mask = lines - 1;
+        void *table = ctx_alloc(c, 128 * lines, s);
+        st.table_bytes = 128 * lines;
+        uint64_t member_words = 0;
+        uint64_t *member = nullptr;
+        if (firsts_mode && prm.member_filter) {  // ~4.5 bits per candidate key: L2-resident
+            member_words = pow2_at_least(nu / 16 + 1);
+            member = (uint64_t *)ctx_alloc(c, 8 * member_words, s);
+            ck(cudaMemsetAsync(member, 0, 8 * member_words, s));
+        }
         tm.start(TURTLE_STAGE_TABLE);
-        launch_table_clear<K>(lc, table, slots);
-        launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, slots - 1, err);
+        launch_table_clear<K>(lc, table, lines);
+        launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, mask, member, member_words, err);
         tm.stop(TURTLE_STAGE_TABLE);
         st.stage_launches[TURTLE_STAGE_TABLE] = 1;
         tm.start(TURTLE_STAGE_RECOUNT);
-        if (firsts_mode) launch_add_firsts<K>(lc, firsts, n_first, table, slots - 1, err);
-        else launch_pass2<K>(lc, L, k, P, V, table, slots - 1, W >= 0xfffffffeull, err);
+        if (firsts_mode)
+            launch_add_firsts<K>(lc, firsts, n_first, table, mask, member, member_words, W >= 0xfffffffeull, err);
+        else launch_pass2<K>(lc, L, k, P, V, table, mask, W >= 0xfffffffeull, err);
         tm.stop(TURTLE_STAGE_RECOUNT);
         st.stage_launches[TURTLE_STAGE_RECOUNT] = (!firsts_mode || n_first) ? 1 : 0;
         K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s, true);
         uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nu ? nu : 1), s, true);
         tm.start(TURTLE_STAGE_THRESHOLD);
-        launch_threshold<K>(lc, unique, nu, table, slots - 1, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
+        launch_threshold<K>(lc, unique, nu, table, mask, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
                             ss.tile_ctr + 21, err);
         tm.stop(TURTLE_STAGE_THRESHOLD);
         st.stage_launches[TURTLE_STAGE_THRESHOLD] = nu ? 1 : 0;

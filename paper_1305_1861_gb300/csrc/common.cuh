@@ -104,6 +104,28 @@ template <> __device__ __forceinline__ Key128 canonical<Key128>(const uint64_t *
 }
 
 // ---------------------------------------------------------------- key loads/stores
+__device__ __forceinline__ uint64_t load_stream(const uint64_t *p) { return __ldcs(p); }  // read once
+__device__ __forceinline__ Key128 load_stream(const Key128 *p) {
+    const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(p));
+    Key128 k;
+    k.hi = v.x;
+    k.lo = v.y;
+    return k;
+}
+__device__ __forceinline__ uint64_t shfl_key(uint64_t k, int src) { return __shfl_sync(FULL, k, src); }
+__device__ __forceinline__ Key128 shfl_key(Key128 k, int src) {
+    Key128 r;
+    r.hi = __shfl_sync(FULL, k.hi, src);
+    r.lo = __shfl_sync(FULL, k.lo, src);
+    return r;
+}
+__device__ __forceinline__ uint64_t shfl_up_key(uint64_t k) { return __shfl_up_sync(FULL, k, 1); }
+__device__ __forceinline__ Key128 shfl_up_key(Key128 k) {
+    Key128 r;
+    r.hi = __shfl_up_sync(FULL, k.hi, 1);
+    r.lo = __shfl_up_sync(FULL, k.lo, 1);
+    return r;
+}
 __device__ __forceinline__ void store_key(uint64_t *p, uint64_t k) { *p = k; }
 __device__ __forceinline__ void store_key(Key128 *p, Key128 k) { *p = k; }
 
@@ -163,6 +185,53 @@ __device__ __forceinline__ uint64_t lookback_prefix(uint64_t *status, uint64_t s
         --j;
     }
     st_relaxed(status + tile * stride, lb_pack(LB_INC, epoch, excl + aggregate));
+    return excl;
+}
+
+// Warp-wide decoupled look-back: all 32 lanes of ONE warp call this; lane l inspects
+// predecessor tile-1-l, so one round trip covers 32 predecessors. Returns the exclusive
+// prefix in every lane and publishes the inclusive one. Bounded like lookback_prefix.
+__device__ __forceinline__ uint64_t lookback_prefix_warp(uint64_t *status, uint64_t tile, uint64_t aggregate,
+                                                         uint32_t epoch, uint32_t *err) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed(status, lb_pack(LB_INC, epoch, aggregate));
+        return 0;
+    }
+    if (lane == 0) st_relaxed(status + tile, lb_pack(LB_AGG, epoch, aggregate));
+    uint64_t excl = 0;
+    int64_t base = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (base >= 0) {
+        const int64_t j = base - lane;
+        uint64_t v = 0;
+        bool ready = true, inc = true;  // lanes before tile 0 act as an inclusive prefix of 0
+        if (j >= 0) {
+            v = ld_relaxed(status + j);
+            const uint64_t st = v & (3ull << 62);
+            ready = ((uint32_t)(v >> 40) & 0x3fffffu) == (epoch & 0x3fffffu) && st != 0;
+            inc = ready && st == LB_INC;
+        }
+        const uint32_t inc_mask = __ballot_sync(FULL, inc);
+        const uint32_t ready_mask = __ballot_sync(FULL, ready);
+        const int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;  // nearest predecessor with a prefix
+        const uint32_t need = first_inc >= 31 ? FULL : ((2u << first_inc) - 1u);
+        if ((ready_mask & need) != need) {
+            if (++spins > LB_SPIN_LIMIT) {
+                if (lane == 0) atomicOr(err, ERR_LOOKBACK);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        uint64_t c = (lane <= first_inc && j >= 0) ? (v & LB_VALUE) : 0;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+        excl += c;
+        if (first_inc < 32) break;
+        base -= 32;
+    }
+    if (lane == 0) st_relaxed(status + tile, lb_pack(LB_INC, epoch, excl + aggregate));
     return excl;
 }
 

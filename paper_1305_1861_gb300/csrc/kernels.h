@@ -83,18 +83,23 @@ void launch_rle(const LaunchCfg &c, const K *sorted, uint64_t n, K *unique, uint
 void launch_run_counts(const LaunchCfg &c, const uint64_t *starts, const unsigned long long *n_unique, uint64_t n,
                        uint64_t cap, uint32_t *counts, uint32_t *err);
 
-// a5: recount table.
+// a5: recount table: lines of 128 bytes (8 slots of 16 B for 64-bit keys, 4 of 32 B for 128-bit);
+// `mask` arguments below are line masks (number of lines - 1, a power of two minus one).
 template <class K> struct Slot;
 size_t slot_bytes(int key_words);
+int slots_per_line(int key_words);
 template <class K>
-void launch_table_clear(const LaunchCfg &c, void *table, uint64_t slots);
-// counts == nullptr: every slot starts at 0; otherwise slot j starts at counts[j].
+void launch_table_clear(const LaunchCfg &c, void *table, uint64_t lines);
+// counts == nullptr: every slot starts at 0; otherwise slot j starts at counts[j]. member (optional,
+// member_words a power of two, zeroed) receives the membership bitmap of the inserted keys.
 template <class K>
 void launch_table_insert(const LaunchCfg &c, const K *unique, const uint32_t *counts,
-                         const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask, uint32_t *err);
+                         const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask,
+                         uint64_t *member, uint64_t member_words, uint32_t *err);
 // a5 (first-sighting form): +1 on the slot of every key of firsts[0 .. n) that is in the table.
 template <class K>
-void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask, uint32_t *err);
+void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask,
+                       const uint64_t *member, uint64_t member_words, bool check_overflow, uint32_t *err);
 template <class K>
 void launch_pass2(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   void *table, uint64_t mask, bool check_overflow, uint32_t *err);

@@ -173,55 +173,73 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
 
 // ---------------------------------------------------------------- run-length compaction
 template <class K> struct RleCfg;
-template <> struct RleCfg<uint64_t> { static constexpr int ITEMS = 16; };  // 32 KB of keys per tile
-template <> struct RleCfg<Key128> { static constexpr int ITEMS = 8; };
+template <> struct RleCfg<uint64_t> { static constexpr int ITEMS = 16; };  // 4096 keys per tile
+template <> struct RleCfg<Key128> { static constexpr int ITEMS = 8; };     // 2048 keys per tile
 
+// Warp w of a tile owns a contiguous run of ITEMS rows of 32 keys (coalesced loads,
+// no shared staging). A key starts a run iff it differs from its predecessor; the
+// run starts of a row are ranked by ballot, rows are summed in order, warps by a
+// block scan, tiles by decoupled look-back.
 template <class K>
-__global__ void __launch_bounds__(S_BLOCK) k_rle(const K *__restrict__ sorted, uint64_t n, K *__restrict__ unique,
+__global__ void __launch_bounds__(S_BLOCK, 4) k_rle(const K *__restrict__ sorted, uint64_t n, K *__restrict__ unique,
                                                  uint64_t *__restrict__ starts, unsigned long long *n_unique,
                                                  uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err) {
     constexpr int R_ITEMS = RleCfg<K>::ITEMS;
     constexpr int R_TILE = S_BLOCK * R_ITEMS;
-    __shared__ K skeys[R_TILE];
+    __shared__ uint32_t s_warp[S_WARPS];
     __shared__ uint32_t s_scan[S_WARPS];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_excl;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
     __syncthreads();
     const uint64_t tile = s_tile, start = tile * R_TILE;
-    const uint32_t tile_n = (uint32_t)(n - start < (uint64_t)R_TILE ? n - start : R_TILE);
-    for (uint32_t i = tid; i < tile_n; i += S_BLOCK) skeys[i] = sorted[start + i];
-    __syncthreads();
-    // blocked: thread tid owns tile positions [tid*R_ITEMS, +R_ITEMS)
-    uint32_t flags = 0, cnt = 0;
-    const uint32_t p0 = tid * R_ITEMS;
+    const uint64_t wstart = start + (uint64_t)warp * R_ITEMS * WARP;
+    const uint32_t lt = lanemask_lt();
+    K key[R_ITEMS];
+    uint32_t ball[R_ITEMS];
+    uint32_t wcount = 0;
+    // all loads first (one memory latency per tile, not per row) ...
 #pragma unroll
-    for (int j = 0; j < R_ITEMS; j++) {
-        const uint32_t p = p0 + j;
-        if (p < tile_n) {
-            bool f;
-            if (p > 0) f = !KeyT<K>::eq(skeys[p], skeys[p - 1]);
-            else f = (start == 0) || !KeyT<K>::eq(skeys[0], sorted[start - 1]);
-            flags |= (uint32_t)f << j;
-            cnt += f;
-        }
+    for (int i = 0; i < R_ITEMS; i++) {
+        const uint64_t idx = wstart + (uint64_t)i * WARP + lane;
+        if (idx < n) key[i] = sorted[idx];
     }
+    K before{};  // key just before this warp's run
+    if (lane == 0 && wstart > 0 && wstart < n) before = sorted[wstart - 1];
+    // ... then flags: the predecessor of lane l is lane l-1 of the same row, of lane 0 the last lane of the row before
+#pragma unroll
+    for (int i = 0; i < R_ITEMS; i++) {
+        const uint64_t idx = wstart + (uint64_t)i * WARP + lane;
+        K prev = shfl_up_key(key[i]);
+        const K last_prev_row = shfl_key(i ? key[i - 1] : before, 31);
+        if (lane == 0) prev = i ? last_prev_row : before;
+        const bool f = idx < n && (idx == 0 || !KeyT<K>::eq(key[i], prev));
+        ball[i] = __ballot_sync(FULL, f);
+        wcount += __popc(ball[i]);
+    }
+    if (lane == 0) s_warp[warp] = wcount;
+    __syncthreads();
     uint32_t total;
-    const uint32_t before = block_exclusive_scan<S_BLOCK>(cnt, s_scan, &total);
-    if (tid == 0) s_excl = lookback_prefix(lookback, 1, tile, total, 1, err);
+    const uint32_t wexcl = block_exclusive_scan<S_BLOCK>(tid < S_WARPS ? s_warp[tid] : 0u, s_scan, &total);
     __syncthreads();
-    uint64_t pos = s_excl + before;
-#pragma unroll
-    for (int j = 0; j < R_ITEMS; j++) {
-        if ((flags >> j) & 1) {
-            unique[pos] = skeys[p0 + j];
-            if (starts) starts[pos] = start + p0 + j;  // run starts are only needed for run lengths
-            pos++;
-        }
+    if (tid < S_WARPS) s_warp[tid] = wexcl;  // exclusive start of each warp inside the tile
+    if (warp == 0) {
+        const uint64_t e = lookback_prefix_warp(lookback, tile, total, 1, err);
+        if (lane == 0) s_excl = e;
     }
-    if (start + tile_n == n && tid == 0) *n_unique = s_excl + total;
-    (void)R_TILE;
+    __syncthreads();
+    uint64_t pos = s_excl + s_warp[warp];
+#pragma unroll
+    for (int i = 0; i < R_ITEMS; i++) {
+        if ((ball[i] >> lane) & 1u) {
+            const uint64_t o = pos + __popc(ball[i] & lt);
+            unique[o] = key[i];
+            if (starts) starts[o] = wstart + (uint64_t)i * WARP + lane;  // run starts only for run lengths
+        }
+        pos += __popc(ball[i]);
+    }
+    if (start + R_TILE >= n && tid == 0) *n_unique = s_excl + total;
 }
 
 __global__ void k_run_counts(const uint64_t *__restrict__ starts, const unsigned long long *n_unique, uint64_t n,

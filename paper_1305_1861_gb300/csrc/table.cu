@@ -47,24 +47,47 @@ __device__ __forceinline__ Slot<Key128> slot_load(const Slot<Key128> *p) {
     s.count = c;
     return s;
 }
-__device__ __forceinline__ uint64_t slot_index(uint64_t h) { return h ^ (h >> 29); }
+// Probe sequence of a key: start at slot p of line L (both from the hash), wrap inside the
+// 128-byte line, then continue in the next lines. Insertion claims the first free slot of
+// this sequence and slots are never freed, so a lookup that meets a free slot knows the key
+// is absent. Most keys are decided within their first line: one DRAM line per probe.
+template <class K> struct TableLine {
+    static constexpr int S = 128 / (int)sizeof(Slot<K>);  // slots per 128-byte line (8 or 4)
+};
+template <class K>
+__device__ __forceinline__ uint64_t probe_slot(uint64_t h, uint64_t j, uint64_t line_mask) {
+    constexpr int S = TableLine<K>::S;
+    const uint64_t g = h ^ (h >> 29);
+    const uint64_t line = ((g >> 3) + j / S) & line_mask;
+    return line * S + (uint64_t)((g + j) & (S - 1));
+}
+
+// Membership bitmap of the table's keys: two bits of one 64-bit word per key. It is
+// small enough to stay in L2, so most probes of absent keys never reach the table.
+__device__ __forceinline__ uint64_t member_word(uint64_t h, uint64_t word_mask) { return (h >> 24) & word_mask; }
+__device__ __forceinline__ uint64_t member_bits(uint64_t h) { return (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)); }
 
 template <class K>
 __global__ void k_table_insert(const K *__restrict__ unique, const uint32_t *__restrict__ counts,
-                               const unsigned long long *n_unique, Slot<K> *table, uint64_t mask, uint32_t *err) {
+                               const unsigned long long *n_unique, Slot<K> *table, uint64_t mask,
+                               uint64_t *member, uint64_t member_mask, uint32_t *err) {
     const uint64_t nu = *n_unique;
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nu; j += (uint64_t)gridDim.x * blockDim.x) {
         const K key = unique[j];
         const uint32_t c0 = counts ? counts[j] : 0u;
-        uint64_t s = slot_index(key_hash(key)) & mask;
+        const uint64_t h = key_hash(key);
+        const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
         bool done = false;
-        for (uint64_t probe = 0; probe <= mask; probe++, s = (s + 1) & mask) {
+        for (uint64_t probe = 0; probe < n_slots; probe++) {
+            const uint64_t s = probe_slot<K>(h, probe, mask);
             if (atomicCAS(&table[s].count, EMPTY_COUNT, c0) == EMPTY_COUNT) {  // distinct keys: claim any free slot
                 slot_put(&table[s], key);
                 done = true;
                 break;
             }
         }
+        if (member) atomicOr((unsigned long long *)&member[member_word(h, member_mask)],
+                             (unsigned long long)member_bits(h));
         if (!done) atomicOr(err, ERR_TABLE_FULL);
     }
 }
@@ -85,7 +108,7 @@ __global__ void __launch_bounds__(P2_BLOCK) k_pass2(const uint64_t *__restrict__
         const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
         bool ok[P2_ILP];
         K key[P2_ILP];
-        uint64_t s[P2_ILP];
+        uint64_t h[P2_ILP];
         Slot<K> sl[P2_ILP];
 #pragma unroll
         for (int i = 0; i < P2_ILP; i++) {
@@ -94,26 +117,27 @@ __global__ void __launch_bounds__(P2_BLOCK) k_pass2(const uint64_t *__restrict__
             ok[i] = pos < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
             if (ok[i]) {
                 key[i] = canonical<K>(P, pos, k);
-                s[i] = slot_index(key_hash(key[i])) & mask;
-                sl[i] = slot_load(table + s[i]);
+                h[i] = key_hash(key[i]);
+                sl[i] = slot_load(table + probe_slot<K>(h[i], 0, mask));
             }
         }
+        const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
 #pragma unroll
         for (int i = 0; i < P2_ILP; i++) {
             if (!ok[i]) continue;
-            for (uint64_t probe = 0; probe <= mask; probe++) {
+            for (uint64_t probe = 0; probe < n_slots;) {
                 if (sl[i].count == EMPTY_COUNT) break;  // key absent: not a candidate
                 if (slot_has(sl[i], key[i])) {
+                    unsigned int *cnt = &table[probe_slot<K>(h[i], probe, mask)].count;
                     if (check_overflow) {
-                        const uint32_t old = atomicAdd(&table[s[i]].count, 1u);
+                        const uint32_t old = atomicAdd(cnt, 1u);
                         if (old >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);  // would pass 2^32-2
                     } else {
-                        atomicAdd(&table[s[i]].count, 1u);
+                        atomicAdd(cnt, 1u);
                     }
                     break;
                 }
-                s[i] = (s[i] + 1) & mask;
-                sl[i] = slot_load(table + s[i]);
+                if (++probe < n_slots) sl[i] = slot_load(table + probe_slot<K>(h[i], probe, mask));
             }
         }
     }
@@ -128,36 +152,47 @@ __global__ void __launch_bounds__(P2_BLOCK) k_pass2(const uint64_t *__restrict__
 constexpr int F_ILP = 4;
 
 template <class K>
-__global__ void __launch_bounds__(256) k_add_firsts(const K *__restrict__ firsts, uint64_t n, Slot<K> *table,
-                                                    uint64_t mask, uint32_t *err) {
+__global__ void __launch_bounds__(256, 6) k_add_firsts(const K *__restrict__ firsts, uint64_t n, Slot<K> *table,
+                                                    uint64_t mask, const uint64_t *__restrict__ member,
+                                                    uint64_t member_mask, int check_overflow, uint32_t *err) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
     for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; base < n; base += stride * F_ILP) {
         K key[F_ILP];
-        uint64_t s[F_ILP];
-        Slot<K> sl[F_ILP];
+        uint64_t h[F_ILP], mw[F_ILP];
         bool ok[F_ILP];
 #pragma unroll
         for (int i = 0; i < F_ILP; i++) {
             const uint64_t j = base + i * stride;
             ok[i] = j < n;
             if (ok[i]) {
-                key[i] = firsts[j];
-                s[i] = slot_index(key_hash(key[i])) & mask;
-                sl[i] = slot_load(table + s[i]);
+                key[i] = load_stream(firsts + j);
+                h[i] = key_hash(key[i]);
+                mw[i] = member ? __ldcg(member + member_word(h[i], member_mask)) : 0;
             }
+        }
+        Slot<K> sl[F_ILP];
+#pragma unroll
+        for (int i = 0; i < F_ILP; i++) {  // first probes of every possible member, issued together
+            const uint64_t mb = member_bits(h[i]);
+            ok[i] = ok[i] && (!member || (mw[i] & mb) == mb);  // else certainly not a candidate key
+            if (ok[i]) sl[i] = slot_load(table + probe_slot<K>(h[i], 0, mask));
         }
 #pragma unroll
         for (int i = 0; i < F_ILP; i++) {
             if (!ok[i]) continue;
-            for (uint64_t probe = 0; probe <= mask; probe++) {
+            for (uint64_t probe = 0; probe < n_slots;) {
                 if (sl[i].count == EMPTY_COUNT) break;
                 if (slot_has(sl[i], key[i])) {
-                    const uint32_t old = atomicAdd(&table[s[i]].count, 1u);
-                    if (old >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
+                    unsigned int *cnt = &table[probe_slot<K>(h[i], probe, mask)].count;
+                    if (check_overflow) {
+                        if (atomicAdd(cnt, 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
+                    } else {
+                        atomicAdd(cnt, 1u);  // result unused: a fire-and-forget reduction
+                    }
                     break;
                 }
-                s[i] = (s[i] + 1) & mask;
-                sl[i] = slot_load(table + s[i]);
+                if (++probe < n_slots) sl[i] = slot_load(table + probe_slot<K>(h[i], probe, mask));
             }
         }
     }
@@ -168,9 +203,10 @@ constexpr int T_TILE = P2_BLOCK * T_ITEMS;
 
 template <class K>
 __device__ __forceinline__ uint32_t table_count(const Slot<K> *table, uint64_t mask, K key) {
-    uint64_t s = slot_index(key_hash(key)) & mask;
-    for (uint64_t probe = 0; probe <= mask; probe++, s = (s + 1) & mask) {
-        const Slot<K> sl = slot_load(table + s);
+    const uint64_t h = key_hash(key);
+    const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
+    for (uint64_t probe = 0; probe < n_slots; probe++) {
+        const Slot<K> sl = slot_load(table + probe_slot<K>(h, probe, mask));
         if (sl.count == EMPTY_COUNT) return EMPTY_COUNT;
         if (slot_has(sl, key)) return sl.count;
     }
@@ -220,7 +256,10 @@ __global__ void __launch_bounds__(P2_BLOCK) k_threshold(const K *__restrict__ un
     }
     uint32_t total = 0;
     for (int j = 0; j < T_ITEMS; j++) total += (uint32_t)s_rowtot[j];
-    if (tid == 0) s_excl = lookback_prefix(lookback, 1, tile, total, 1, err);
+    if (tid < WARP) {
+        const uint64_t e = lookback_prefix_warp(lookback, tile, total, 1, err);
+        if (tid == 0) s_excl = e;
+    }
     __syncthreads();
     row_base = s_excl;
 #pragma unroll
@@ -237,22 +276,24 @@ __global__ void __launch_bounds__(P2_BLOCK) k_threshold(const K *__restrict__ un
 }
 
 template <class K>
-void launch_table_clear(const LaunchCfg &c, void *table, uint64_t slots) {
-    cudaMemsetAsync(table, 0xff, sizeof(Slot<K>) * slots, c.stream);
+void launch_table_clear(const LaunchCfg &c, void *table, uint64_t lines) {
+    cudaMemsetAsync(table, 0xff, 128 * lines, c.stream);
 }
 
 template <class K>
 void launch_table_insert(const LaunchCfg &c, const K *unique, const uint32_t *counts,
                          const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask,
-                         uint32_t *err) {
+                         uint64_t *member, uint64_t member_words, uint32_t *err) {
     uint64_t need = (cap + 255) / 256;
     const uint64_t lim = (uint64_t)c.sms * 8;
     k_table_insert<K><<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(
-        unique, counts, n_unique, reinterpret_cast<Slot<K> *>(table), mask, err);
+        unique, counts, n_unique, reinterpret_cast<Slot<K> *>(table), mask, member,
+        member_words ? member_words - 1 : 0, err);
 }
 
 template <class K>
-void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask, uint32_t *err) {
+void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask,
+                       const uint64_t *member, uint64_t member_words, bool check_overflow, uint32_t *err) {
     if (n == 0) return;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_add_firsts<K>, 256, 0);
@@ -260,7 +301,8 @@ void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *ta
     uint64_t need = (n + 256 * F_ILP - 1) / (256 * F_ILP);
     const uint64_t lim = (uint64_t)c.sms * per_sm;
     k_add_firsts<K><<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(
-        firsts, n, reinterpret_cast<Slot<K> *>(table), mask, err);
+        firsts, n, reinterpret_cast<Slot<K> *>(table), mask, member, member_words ? member_words - 1 : 0,
+        check_overflow ? 1 : 0, err);
 }
 
 template <class K>
@@ -291,12 +333,15 @@ void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, co
 }
 
 size_t slot_bytes(int key_words) { return key_words == 1 ? sizeof(Slot<uint64_t>) : sizeof(Slot<Key128>); }
+int slots_per_line(int key_words) { return key_words == 1 ? TableLine<uint64_t>::S : TableLine<Key128>::S; }
 
 #define INST(K)                                                                                                  \
     template void launch_table_clear<K>(const LaunchCfg &, void *, uint64_t);                                    \
     template void launch_table_insert<K>(const LaunchCfg &, const K *, const uint32_t *,                         \
-                                         const unsigned long long *, uint64_t, void *, uint64_t, uint32_t *);    \
-    template void launch_add_firsts<K>(const LaunchCfg &, const K *, uint64_t, void *, uint64_t, uint32_t *);     \
+                                         const unsigned long long *, uint64_t, void *, uint64_t, uint64_t *,     \
+                                         uint64_t, uint32_t *);                                                  \
+    template void launch_add_firsts<K>(const LaunchCfg &, const K *, uint64_t, void *, uint64_t,                 \
+                                       const uint64_t *, uint64_t, bool, uint32_t *);                            \
     template void launch_pass2<K>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *, \
                                   void *, uint64_t, bool, uint32_t *);                                           \
     template void launch_threshold<K>(const LaunchCfg &, const K *, uint64_t, const void *, uint64_t, uint32_t,  \
