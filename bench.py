@@ -233,6 +233,10 @@ def run_ours(args, rank, world):
     value = W_all / (ms_all / 1e3)
 
     # end to end through the host C ABI: H2D of pinned reads, whole path, D2H of the result
+    st_dev = dict(st)
+    ctx.close()  # give the device-resident context's memory back before the host-form calls
+    del bases
+    torch.cuda.empty_cache()
     pin_b = torch.from_numpy(lib.bases).pin_memory()
     pin_o = torch.from_numpy(lib.offsets.astype(np.uint64).view(np.int64)).pin_memory()
     keys_n = 0
@@ -275,11 +279,12 @@ def run_ours(args, rank, world):
                       "l2": "inputs larger than L2 (%.1f GB of reads resident)" % (lib.bases.nbytes / 1e9),
                       "parallelism": "replicas%d" % world if world > 1 else "single"},
            "e2e": e2e, "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-           "sort_passes": st["sort_passes"]}
+           "sort_passes": st["sort_passes"], "super_partitions": st["super_partitions"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = args.cpu_sample_reads or max(1, int(lib.n_reads * 0.1))
+        frac = 0.01 if lib.k > 32 else 0.1  # about 10-30 s of oracle work
+        sample = args.cpu_sample_reads or max(1, int(lib.n_reads * frac))
         out["cpu_baseline"] = cpu_baseline(lib, sample)
-    ctx.close()
+    del st_dev
     return out
 
 

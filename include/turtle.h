@@ -76,7 +76,14 @@ typedef struct {
                                       counting it in the table. Both are exact. */
     uint32_t member_filter;        /* 1: screen first-sighting keys with a small membership bitmap of the
                                       candidates before probing the recount table (default 0: probe all) */
-    uint32_t reserved[4];
+    uint32_t budget_mib;           /* device-memory budget (MiB) for one super-partition's working set;
+                                      0 = 80% of the free memory at the start of the call. Inputs whose
+                                      working set exceeds it are processed in consecutive key ranges. */
+    uint32_t stream_chunk_mib;     /* host-memory calls: copy the reads to the device in chunks of this many
+                                      MiB through two pinned buffers, packing each chunk as it lands (the
+                                      ASCII is never resident whole); 0 = chunks of 1 GiB when the reads
+                                      exceed a quarter of the free device memory, else one copy */
+    uint32_t reserved[2];
 } turtle_params;
 
 /* Fill *p with the defaults above. */
@@ -161,7 +168,8 @@ enum {
 typedef struct {
     uint64_t n_windows, n_candidates, n_firsts, n_unique, n_out;
     uint64_t filter_bytes, table_bytes, scratch_bytes;
-    uint32_t sort_passes;                       /* LSD digit passes run (8-bit digits) */
+    uint32_t sort_passes;                       /* LSD digit passes run (8-bit digits), last super-partition */
+    uint32_t super_partitions;                  /* key ranges the call was split into (1 = none) */
     uint32_t launches;                          /* kernels launched by the last call */
     uint32_t stage_launches[TURTLE_STAGE_COUNT];
     float stage_ms[TURTLE_STAGE_COUNT];         /* CUDA-event time per stage (params->timing) */
@@ -211,6 +219,50 @@ int turtle_filter(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int key_wor
  */
 int turtle_sort_compact(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int key_words, int key_bits,
                         uint64_t *unique, uint32_t *counts, uint64_t *n_unique, void *stream);
+
+/* ------------------------------------------------------------------ served form
+ * A request loop for many counting jobs (continuous batching). Jobs are admitted in
+ * arrival order as soon as a worker is idle and the job's device-memory footprint
+ * estimate fits in what is left of the HBM budget; admitted jobs run concurrently on
+ * separate streams and overlap on the device. Each result equals turtle_count on the
+ * same reads. Reads stay in caller-owned host memory until the job's poll returns.
+ */
+typedef struct turtle_server turtle_server;
+
+typedef struct {
+    const char *bases;        /* host, caller-owned, valid until turtle_poll returns the result */
+    const uint64_t *offsets;  /* host, n_reads + 1 entries */
+    uint64_t n_reads;
+    int k;
+    uint32_t min_count;
+} turtle_job;
+
+typedef struct {
+    double queue_ms;  /* submit -> admitted */
+    double run_ms;    /* admitted -> result ready */
+    double total_ms;  /* submit -> result ready */
+} turtle_job_times;
+
+typedef struct {
+    uint64_t budget_bytes, admitted_bytes, peak_admitted_bytes;
+    uint64_t submitted, completed, failed, queued, running, peak_running, peak_queued;
+} turtle_server_stats;
+
+/* Start a server on `device` with `max_concurrent` workers (1..64), each owning a context and
+ * a stream. hbm_budget_bytes = 0 takes half of the free device memory. params may be NULL. */
+int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_concurrent, const turtle_params *params,
+                         turtle_server **server);
+/* Queue a job; *ticket identifies it. TURTLE_E_BUSY: its footprint estimate exceeds the whole
+ * budget, so it could never be admitted. */
+int turtle_submit(turtle_server *server, const turtle_job *job, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: forever) for a job. On completion fills *out (free with
+ * turtle_result_free), optionally *times, forgets the ticket and returns the job's status;
+ * TURTLE_E_TIMEOUT if it is not done yet (the ticket stays valid); TURTLE_E_ARG for an
+ * unknown ticket. */
+int turtle_poll(turtle_server *server, uint64_t ticket, int timeout_ms, turtle_result *out, turtle_job_times *times);
+int turtle_server_stats_get(turtle_server *server, turtle_server_stats *stats);
+/* Stop accepting work, let running jobs finish, drop queued ones, free everything. */
+void turtle_server_destroy(turtle_server *server);
 
 /*
  * Allocation-free variant of turtle_sort_compact (no counterpart in the paper:

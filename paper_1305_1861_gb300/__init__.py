@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "TurtleError", "Params", "Context", "load", "build", "turtle_count", "turtle_strerror", "STAGES",
+    "TurtleError", "Params", "Context", "Server", "load", "build", "turtle_count", "turtle_strerror", "STAGES",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,7 +41,8 @@ class TurtleError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("struct_size", u32), ("filter_bits_per_window", ctypes.c_float), ("pattern_bits", u32),
                 ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("l2_fetch_bytes", u32),
-                ("recount_windows", u32), ("member_filter", u32), ("reserved", u32 * 4)]
+                ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
+                ("stream_chunk_mib", u32), ("reserved", u32 * 2)]
 
     @classmethod
     def default(cls, **kw) -> "Params":
@@ -69,7 +70,7 @@ class _DeviceResult(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n_windows", u64), ("n_candidates", u64), ("n_firsts", u64), ("n_unique", u64), ("n_out", u64),
                 ("filter_bytes", u64), ("table_bytes", u64), ("scratch_bytes", u64), ("sort_passes", u32),
-                ("launches", u32), ("stage_launches", u32 * 9), ("stage_ms", ctypes.c_float * 9)]
+                ("super_partitions", u32), ("launches", u32), ("stage_launches", u32 * 9), ("stage_ms", ctypes.c_float * 9)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_launches", "stage_ms")}
@@ -106,6 +107,11 @@ def load():
         "turtle_filter": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, _p, u64, _p, ctypes.c_int, _p, _p]),
         "turtle_sort_compact": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
         "turtle_sort_compact_noalloc": (ctypes.c_int, [_p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
+        "turtle_server_create": (ctypes.c_int, [ctypes.c_int, u64, ctypes.c_int, _p, _p]),
+        "turtle_submit": (ctypes.c_int, [_p, _p, _p]),
+        "turtle_poll": (ctypes.c_int, [_p, u64, ctypes.c_int, _p, _p]),
+        "turtle_server_stats_get": (ctypes.c_int, [_p, _p]),
+        "turtle_server_destroy": (None, [_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +190,78 @@ def turtle_sort_compact_noalloc(keys, key_bits: int, unique, counts, stream=None
                                             ctypes.byref(nu), _stream_ptr(stream))
     _check(rc, "turtle_sort_compact_noalloc")
     return int(nu.value)
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("bases", _p), ("offsets", _p), ("n_reads", u64), ("k", ctypes.c_int), ("min_count", u32)]
+
+
+class JobTimes(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, u64) for n in ("budget_bytes", "admitted_bytes", "peak_admitted_bytes", "submitted", "completed",
+                                   "failed", "queued", "running", "peak_running", "peak_queued")]
+
+
+class Server:
+    """Served form: continuous batching of counting jobs admitted by device-memory footprint."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_concurrent: int = 4,
+                 params: Params | None = None):
+        self._lib = load()
+        self._h = _p()
+        self._keep = {}
+        _check(self._lib.turtle_server_create(device, hbm_budget_bytes, max_concurrent,
+                                              ctypes.byref(params) if params else None, ctypes.byref(self._h)),
+               "turtle_server_create")
+
+    def submit(self, bases, offsets, k: int, min_count: int = 2) -> int:
+        b = _np(bases, np.uint8)
+        o = _np(offsets, np.uint64)
+        job = _Job(b.ctypes.data if b.size else None, o.ctypes.data, o.size - 1, k, min_count)
+        t = u64()
+        _check(self._lib.turtle_submit(self._h, ctypes.byref(job), ctypes.byref(t)), "turtle_submit")
+        self._keep[t.value] = (b, o, k)  # host reads must outlive the job
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(keys, counts, n_windows, JobTimes); raises TurtleError (TURTLE_E_TIMEOUT when not done yet)."""
+        res = _Result()
+        tm = JobTimes()
+        rc = self._lib.turtle_poll(self._h, ticket, timeout_ms, ctypes.byref(res), ctypes.byref(tm))
+        if rc == -5:
+            raise TurtleError(rc, "turtle_poll")
+        k = self._keep.pop(ticket, (None, None, 31))[2]
+        try:
+            _check(rc, "turtle_poll")
+            w = 2 if k > 32 else 1
+            n = res.n
+            keys = np.ctypeslib.as_array(res.keys, shape=(max(n * w, 1),))[: n * w].copy() if n else \
+                np.zeros(0, dtype=np.uint64)
+            counts = np.ctypeslib.as_array(res.counts, shape=(max(n, 1),))[:n].copy() if n else \
+                np.zeros(0, np.uint32)
+            return _shape_keys(keys, n, k), counts, int(res.n_windows), tm
+        finally:
+            self._lib.turtle_result_free(ctypes.byref(res))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.turtle_server_stats_get(self._h, ctypes.byref(st)), "turtle_server_stats_get")
+        return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.turtle_server_destroy(self._h)
+            self._h = _p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _CudaArray:

@@ -7,15 +7,18 @@
 //   table insert, pass 2 (recount), threshold -> result in key order
 // Scratch comes from a per-context CUDA memory pool whose memory is retained
 // between calls, so repeated calls do not return to the driver.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/turtle.h"
 #include "common.cuh"
+#include "host.h"
 #include "kernels.h"
 
 using namespace turtle;
@@ -84,6 +87,11 @@ struct turtle_ctx {
     cudaEvent_t ev[2 * TURTLE_STAGE_COUNT] = {};
     turtle_stats stats{};
     uint64_t scratch_bytes = 0;
+    // streamed input: two pinned host buffers, a copy stream and their events
+    cudaStream_t copy_stream = nullptr;
+    void *pinned[2] = {nullptr, nullptr};
+    size_t pinned_bytes = 0;
+    cudaEvent_t ev_h2d[2] = {}, ev_packed[2] = {};
 };
 
 namespace {
@@ -125,7 +133,21 @@ void ctx_begin(turtle_ctx *c, cudaStream_t s) {
     ck(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * C_N, s));
 }
 
-void ctx_end(turtle_ctx *c, cudaStream_t s) { free_list(c->scratch, s); }
+// Free this call's scratch. The pool keeps freed memory for the next call, but never more
+// than a quarter of the device: giant calls (key-range super-partitions) give the rest back.
+void ctx_end(turtle_ctx *c, cudaStream_t s) {
+    free_list(c->scratch, s);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        uint64_t reserved = 0;
+        if (cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            reserved > total_b / 4) {
+            cudaStreamSynchronize(s);
+            cudaMemPoolTrimTo(c->pool, total_b / 4);
+        }
+    }
+    cudaGetLastError();
+}
 
 // Copy the counters and the error word to the host (synchronises s).
 void read_back(turtle_ctx *c, cudaStream_t s) {
@@ -184,6 +206,11 @@ struct Timer {
     }
 };
 
+// Reads already packed on the device (streamed input): P, B and S filled, S marked.
+struct PrePacked {
+    uint64_t *P, *B, *S;
+};
+
 struct DeviceOut {
     void *keys = nullptr;
     uint32_t *counts = nullptr;
@@ -192,7 +219,8 @@ struct DeviceOut {
 
 template <class K>
 void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
-               int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s, DeviceOut &out) {
+               int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s, DeviceOut &out,
+               const PrePacked *pre = nullptr) {
     constexpr int KW = sizeof(K) / 8;
     const LaunchCfg lc{c->sms, s};
     turtle_stats st{};
@@ -201,17 +229,26 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     unsigned long long *ctr = c->d_ctr;
 
     const PackLayout L = PackLayout::of(n_bases);
-    uint64_t *P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
-    uint64_t *B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
-    uint64_t *S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *P, *B, *S;
+    if (pre) {
+        P = pre->P;
+        B = pre->B;
+        S = pre->S;
+    } else {
+        P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
+        B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+        S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+        ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
+    }
     uint64_t *V = (uint64_t *)ctx_alloc(c, 8 * L.v_words, s);
-    ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
     ck(cudaMemsetAsync(V + (L.v_words - 2), 0, 16, s));
 
-    tm.start(TURTLE_STAGE_PACK);
-    launch_pack(lc, bases, offsets, n_reads, L, P, B, S, err);
-    tm.stop(TURTLE_STAGE_PACK);
-    st.stage_launches[TURTLE_STAGE_PACK] = 2;
+    if (!pre) {
+        tm.start(TURTLE_STAGE_PACK);
+        launch_pack(lc, bases, offsets, n_reads, L, P, B, S, err);
+        tm.stop(TURTLE_STAGE_PACK);
+        st.stage_launches[TURTLE_STAGE_PACK] = 2;
+    }
     tm.start(TURTLE_STAGE_VALID);
     launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS);
     tm.stop(TURTLE_STAGE_VALID);
@@ -228,131 +265,232 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         return;
     }
 
-    // pass 1: candidates
     const bool use_filter = min_count >= 2;
-    FilterGeom fg{};
-    if (use_filter) {
-        const double bits = (double)W * prm.filter_bits_per_window;
-        fg.n_sectors = pow2_at_least((uint64_t)(bits / 256.0) + 1);
-        fg.sector_shift = 64 - log2_exact(fg.n_sectors);
-        fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
-        ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
-        fg.patterns = ctx_patterns(c, prm, s);
-        fg.pat_mask = prm.n_patterns - 1;
-        st.filter_bytes = 32 * fg.n_sectors;
-    }
     const bool firsts_mode = use_filter && !prm.recount_windows;
-    K *cand = (K *)ctx_alloc(c, sizeof(K) * W, s);
-    K *firsts = firsts_mode ? (K *)ctx_alloc(c, sizeof(K) * W, s) : nullptr;
     const int passes = sort_passes_for(2 * k);
-    uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
-    ck(cudaMemsetAsync(hist, 0, 8 * 256 * passes, s));
-    tm.start(TURTLE_STAGE_FILTER);
-    launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, W, firsts, ctr + C_FIRST, W, hist, passes,
-                    err);
-    tm.stop(TURTLE_STAGE_FILTER);
-    st.stage_launches[TURTLE_STAGE_FILTER] = 1;
-    ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
-    read_back(c, s);
-    const uint64_t n_cand = c->h_ctr[C_CAND];
-    const uint64_t n_first = c->h_ctr[C_FIRST];
-    st.n_candidates = n_cand;
-    st.n_firsts = n_first;
+    const uint64_t *patterns = use_filter ? ctx_patterns(c, prm, s) : nullptr;
 
-    // a4: sort + compact
-    SortScratch ss{};
-    ss.alt = ctx_alloc(c, sizeof(K) * (n_cand ? n_cand : 1), s);
-    ss.hist = hist;
-    uint32_t skip = 0;  // digit passes where every candidate has the same digit
-    for (int p = 0; p < passes; p++)
-        for (int d = 0; d < 256; d++)
-            if (c->h_hist[p * 256 + d] == n_cand) skip |= 1u << p;
-    ss.lookback_words = sort_lookback_words(n_cand, KW);
-    ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
-    ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
-    tm.start(TURTLE_STAGE_SORT);
-    int passes_run = 0;
-    K *sorted = launch_radix_sort<K>(lc, cand, n_cand, 2 * k, ss, err, true, skip, &passes_run);
-    tm.stop(TURTLE_STAGE_SORT);
-    st.sort_passes = (uint32_t)passes_run;
-    st.stage_launches[TURTLE_STAGE_SORT] = n_cand > 1 ? passes_run + 1 : 0;
-    K *unique = sorted == cand ? (K *)ss.alt : cand;
-    uint64_t *starts = nullptr;
-    if (!use_filter || firsts_mode) starts = (uint64_t *)ctx_alloc(c, 8 * (n_cand ? n_cand : 1), s);
-    tm.start(TURTLE_STAGE_RLE);
-    launch_rle<K>(lc, sorted, n_cand, unique, starts, ctr + C_UNIQUE, ss.lookback, ss.tile_ctr + 20, err);
-    tm.stop(TURTLE_STAGE_RLE);
-    st.stage_launches[TURTLE_STAGE_RLE] = n_cand ? 1 : 0;
-
-    if (!use_filter) {
-        // every window is a candidate: run lengths are the exact counts (min_count == 1)
-        uint32_t *counts = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s, true);
-        tm.start(TURTLE_STAGE_THRESHOLD);
-        launch_run_counts(lc, starts, ctr + C_UNIQUE, n_cand, n_cand, counts, err);
-        tm.stop(TURTLE_STAGE_THRESHOLD);
-        st.stage_launches[TURTLE_STAGE_THRESHOLD] = 1;
-        read_back(c, s);
-        const uint64_t nu = c->h_ctr[C_UNIQUE];
-        // keep the buffer holding the unique keys alive as part of the result
-        for (auto it = c->scratch.begin(); it != c->scratch.end(); ++it)
-            if (*it == (void *)unique) {
-                c->result.push_back(*it);
-                c->scratch.erase(it);
-                break;
-            }
-        out.keys = unique;
-        out.counts = counts;
-        out.n = nu;
-        st.n_unique = nu;
-        st.n_out = nu;
+    // Super-partitions (key routing, Sec. 2.1.5): when the post-filter working set of all windows does
+    // not fit in free device memory, split the key space into consecutive key ranges and run the rest
+    // of the path once per range; outputs are appended in key order.
+    // candidates + first sightings share one buffer; sort buffer; run starts and lengths; filter; table
+    const double bytes_per_window = 2.0 * sizeof(K) + 12.0 + (use_filter ? prm.filter_bits_per_window / 8.0 : 0.0) +
+                                    8.0;
+    size_t free_b = 0, total_b = 0;
+    ck(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = prm.budget_mib ? (double)prm.budget_mib * (1 << 20) : 0.8 * (double)free_b;
+    constexpr int PART_BITS = 6;
+    std::vector<std::pair<uint32_t, uint32_t>> groups;  // [part_lo, part_hi) of each super-partition
+    std::vector<uint64_t> group_w;
+    if ((double)W * bytes_per_window <= budget) {
+        groups.push_back({0u, 1u << PART_BITS});
+        group_w.push_back(W);
     } else {
-        uint32_t *run = nullptr;  // run lengths of the sorted candidates (first-sighting recount only)
-        if (firsts_mode) {
-            run = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s);
-            launch_run_counts(lc, starts, ctr + C_UNIQUE, n_cand, n_cand, run, err);
-            st.stage_launches[TURTLE_STAGE_RLE] += 1;
-        }
+        unsigned long long *pc = (unsigned long long *)ctx_alloc(c, 8 << PART_BITS, s);
+        ck(cudaMemsetAsync(pc, 0, 8 << PART_BITS, s));
+        launch_part_count<K>(lc, L, k, P, V, PART_BITS, pc);
+        std::vector<unsigned long long> cnt(1 << PART_BITS);
+        ck(cudaMemcpyAsync(cnt.data(), pc, 8 << PART_BITS, cudaMemcpyDeviceToHost, s));
         read_back(c, s);
-        const uint64_t nu = c->h_ctr[C_UNIQUE];
-        st.n_unique = nu;
-        // load factor <= 0.4: a line overflows into the next one rarely
-        const uint64_t lines = pow2_at_least((uint64_t)(nu / (0.4 * slots_per_line(KW))) + 1);
-        const uint64_t mask = lines - 1;
-        void *table = ctx_alloc(c, 128 * lines, s);
-        st.table_bytes = 128 * lines;
-        uint64_t member_words = 0;
-        uint64_t *member = nullptr;
-        if (firsts_mode && prm.member_filter) {  // ~4.5 bits per candidate key: L2-resident
-            member_words = pow2_at_least(nu / 16 + 1);
-            member = (uint64_t *)ctx_alloc(c, 8 * member_words, s);
-            ck(cudaMemsetAsync(member, 0, 8 * member_words, s));
+        // balanced groups: as many as the budget needs, each near the average size
+        const double n_groups = std::ceil((double)W * bytes_per_window / budget);
+        const double target = (double)W / n_groups;
+        uint32_t lo = 0;
+        uint64_t acc = 0;
+        for (uint32_t p = 0; p < (1u << PART_BITS); p++) {
+            const double next = (double)(acc + cnt[p]);
+            if (p > lo && (next * bytes_per_window > budget || next > 1.02 * target)) {
+                groups.push_back({lo, p});
+                group_w.push_back(acc);
+                lo = p;
+                acc = 0;
+            }
+            acc += cnt[p];
         }
-        tm.start(TURTLE_STAGE_TABLE);
-        launch_table_clear<K>(lc, table, lines);
-        launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, mask, member, member_words, err);
-        tm.stop(TURTLE_STAGE_TABLE);
-        st.stage_launches[TURTLE_STAGE_TABLE] = 1;
-        tm.start(TURTLE_STAGE_RECOUNT);
-        if (firsts_mode)
-            launch_add_firsts<K>(lc, firsts, n_first, table, mask, member, member_words, W >= 0xfffffffeull, err);
-        else launch_pass2<K>(lc, L, k, P, V, table, mask, W >= 0xfffffffeull, err);
-        tm.stop(TURTLE_STAGE_RECOUNT);
-        st.stage_launches[TURTLE_STAGE_RECOUNT] = (!firsts_mode || n_first) ? 1 : 0;
-        K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s, true);
-        uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nu ? nu : 1), s, true);
-        tm.start(TURTLE_STAGE_THRESHOLD);
-        launch_threshold<K>(lc, unique, nu, table, mask, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
-                            ss.tile_ctr + 21, err);
-        tm.stop(TURTLE_STAGE_THRESHOLD);
-        st.stage_launches[TURTLE_STAGE_THRESHOLD] = nu ? 1 : 0;
+        groups.push_back({lo, 1u << PART_BITS});
+        group_w.push_back(acc);
+    }
+    const bool parted = groups.size() > 1;
+    st.super_partitions = (uint32_t)groups.size();
+
+    struct PartOut {
+        void *keys;
+        uint32_t *counts;
+        uint64_t n;
+    };
+    std::vector<PartOut> outs;
+    for (size_t g = 0; g < groups.size(); g++) {
+        const uint64_t Wg = group_w[g];
+        if (Wg == 0) continue;
+        const size_t mark = c->scratch.size();  // this super-partition's scratch is freed at its end
+        ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
+        // pass 1: candidates (and first sightings)
+        FilterGeom fg{};
+        if (use_filter) {
+            const double bits = (double)Wg * prm.filter_bits_per_window;
+            fg.n_sectors = pow2_at_least((uint64_t)(bits / 256.0) + 1);
+            fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+            fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
+            ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
+            fg.patterns = patterns;
+            fg.pat_mask = prm.n_patterns - 1;
+            st.filter_bytes = 32 * fg.n_sectors > st.filter_bytes ? 32 * fg.n_sectors : st.filter_bytes;
+        }
+        K *cand = (K *)ctx_alloc(c, sizeof(K) * Wg, s);
+        K *firsts = firsts_mode ? cand : nullptr;  // first sightings fill the same buffer from the top
+        uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+        ck(cudaMemsetAsync(hist, 0, 8 * 256 * passes, s));
+        tm.start(TURTLE_STAGE_FILTER);
+        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wg, firsts, ctr + C_FIRST, Wg, hist,
+                        passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second, err);
+        tm.stop(TURTLE_STAGE_FILTER);
+        st.stage_launches[TURTLE_STAGE_FILTER] += 1;
+        ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
         read_back(c, s);
+        const uint64_t n_cand = c->h_ctr[C_CAND];
+        const uint64_t n_first = c->h_ctr[C_FIRST];
+        const K *first_keys = firsts_mode ? cand + (Wg - n_first) : nullptr;
+        st.n_candidates += n_cand;
+        st.n_firsts += n_first;
+
+        // a4: sort + compact
+        SortScratch ss{};
+        ss.alt = ctx_alloc(c, sizeof(K) * (n_cand ? n_cand : 1), s);
+        ss.hist = hist;
+        uint32_t skip = 0;  // digit passes where every candidate has the same digit
+        for (int p = 0; p < passes; p++)
+            for (int d = 0; d < 256; d++)
+                if (c->h_hist[p * 256 + d] == n_cand) skip |= 1u << p;
+        ss.lookback_words = sort_lookback_words(n_cand, KW);
+        ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
+        ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
+        tm.start(TURTLE_STAGE_SORT);
+        int passes_run = 0;
+        K *sorted = launch_radix_sort<K>(lc, cand, n_cand, 2 * k, ss, err, true, skip, &passes_run);
+        tm.stop(TURTLE_STAGE_SORT);
+        st.sort_passes = (uint32_t)passes_run;
+        st.stage_launches[TURTLE_STAGE_SORT] += n_cand > 1 ? passes_run + 1 : 0;
+        K *unique = sorted == cand ? (K *)ss.alt : cand;
+        uint64_t *starts = nullptr;
+        if (!use_filter || firsts_mode) starts = (uint64_t *)ctx_alloc(c, 8 * (n_cand ? n_cand : 1), s);
+        tm.start(TURTLE_STAGE_RLE);
+        launch_rle<K>(lc, sorted, n_cand, unique, starts, ctr + C_UNIQUE, ss.lookback, ss.tile_ctr + 20, err);
+        tm.stop(TURTLE_STAGE_RLE);
+        st.stage_launches[TURTLE_STAGE_RLE] += n_cand ? 1 : 0;
+
+        PartOut po{};
+        if (!use_filter) {
+            // every window is a candidate: run lengths are the exact counts (min_count == 1)
+            uint32_t *counts = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s, !parted);
+            tm.start(TURTLE_STAGE_THRESHOLD);
+            launch_run_counts(lc, starts, ctr + C_UNIQUE, n_cand, n_cand, counts, err);
+            tm.stop(TURTLE_STAGE_THRESHOLD);
+            st.stage_launches[TURTLE_STAGE_THRESHOLD] += 1;
+            read_back(c, s);
+            const uint64_t nu = c->h_ctr[C_UNIQUE];
+            if (!parted) {  // keep the buffer holding the unique keys alive as part of the result
+                for (auto it = c->scratch.begin(); it != c->scratch.end(); ++it)
+                    if (*it == (void *)unique) {
+                        c->result.push_back(*it);
+                        c->scratch.erase(it);
+                        break;
+                    }
+            }
+            po = PartOut{unique, counts, nu};
+            st.n_unique += nu;
+        } else {
+            uint32_t *run = nullptr;  // run lengths of the sorted candidates (first-sighting recount only)
+            if (firsts_mode) {
+                run = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s);
+                launch_run_counts(lc, starts, ctr + C_UNIQUE, n_cand, n_cand, run, err);
+                st.stage_launches[TURTLE_STAGE_RLE] += 1;
+            }
+            read_back(c, s);
+            const uint64_t nu = c->h_ctr[C_UNIQUE];
+            st.n_unique += nu;
+            // load factor <= 0.4: a line overflows into the next one rarely
+            const uint64_t lines = pow2_at_least((uint64_t)(nu / (0.4 * slots_per_line(KW))) + 1);
+            const uint64_t mask = lines - 1;
+            void *table = ctx_alloc(c, 128 * lines, s);
+            st.table_bytes = 128 * lines > st.table_bytes ? 128 * lines : st.table_bytes;
+            uint64_t member_words = 0;
+            uint64_t *member = nullptr;
+            if (firsts_mode && prm.member_filter) {  // ~4.5 bits per candidate key: L2-resident
+                member_words = pow2_at_least(nu / 16 + 1);
+                member = (uint64_t *)ctx_alloc(c, 8 * member_words, s);
+                ck(cudaMemsetAsync(member, 0, 8 * member_words, s));
+            }
+            tm.start(TURTLE_STAGE_TABLE);
+            launch_table_clear<K>(lc, table, lines);
+            launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, mask, member, member_words, err);
+            tm.stop(TURTLE_STAGE_TABLE);
+            st.stage_launches[TURTLE_STAGE_TABLE] += 1;
+            tm.start(TURTLE_STAGE_RECOUNT);
+            if (firsts_mode)
+                launch_add_firsts<K>(lc, first_keys, n_first, table, mask, member, member_words, W >= 0xfffffffeull,
+                                     err);
+            else
+                launch_pass2<K>(lc, L, k, P, V, table, mask, W >= 0xfffffffeull, err);
+            tm.stop(TURTLE_STAGE_RECOUNT);
+            st.stage_launches[TURTLE_STAGE_RECOUNT] += (!firsts_mode || n_first) ? 1 : 0;
+            K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s, !parted);
+            uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nu ? nu : 1), s, !parted);
+            tm.start(TURTLE_STAGE_THRESHOLD);
+            launch_threshold<K>(lc, unique, nu, table, mask, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
+                                ss.tile_ctr + 21, err);
+            tm.stop(TURTLE_STAGE_THRESHOLD);
+            st.stage_launches[TURTLE_STAGE_THRESHOLD] += nu ? 1 : 0;
+            read_back(c, s);
+            po = PartOut{okeys, ocounts, c->h_ctr[C_OUT]};
+        }
+        if (prm.timing) {  // accumulate this super-partition's stage times (events are reused per part)
+            for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] += ms;
+                else cudaGetLastError();
+                ck(cudaEventRecord(c->ev[2 * i], s));  // an empty interval unless the stage runs again
+                ck(cudaEventRecord(c->ev[2 * i + 1], s));
+            }
+        }
+        if (parted) {
+            // keep only this part's output: move it out of the part's scratch range
+            for (void *keep : {po.keys, (void *)po.counts})
+                for (size_t i = mark; i < c->scratch.size(); i++)
+                    if (c->scratch[i] == keep) {
+                        c->scratch.erase(c->scratch.begin() + i);
+                        break;
+                    }
+            for (size_t i = mark; i < c->scratch.size(); i++) cudaFreeAsync(c->scratch[i], s);
+            c->scratch.resize(mark);
+            c->scratch.push_back(po.keys);
+            c->scratch.push_back(po.counts);
+        }
+        outs.push_back(po);
+    }
+    if (!parted) {
+        out.keys = outs.empty() ? ctx_alloc(c, 16, s, true) : outs[0].keys;
+        out.counts = outs.empty() ? (uint32_t *)ctx_alloc(c, 16, s, true) : outs[0].counts;
+        out.n = outs.empty() ? 0 : outs[0].n;
+    } else {
+        uint64_t total = 0;
+        for (auto &o : outs) total += o.n;
+        K *okeys = (K *)ctx_alloc(c, sizeof(K) * (total ? total : 1), s, true);
+        uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (total ? total : 1), s, true);
+        uint64_t at = 0;
+        for (auto &o : outs) {
+            if (o.n) {
+                ck(cudaMemcpyAsync(okeys + at, o.keys, sizeof(K) * o.n, cudaMemcpyDeviceToDevice, s));
+                ck(cudaMemcpyAsync(ocounts + at, o.counts, 4 * o.n, cudaMemcpyDeviceToDevice, s));
+            }
+            at += o.n;
+        }
         out.keys = okeys;
         out.counts = ocounts;
-        out.n = c->h_ctr[C_OUT];
-        st.n_out = out.n;
+        out.n = total;
     }
+    st.n_out = out.n;
     if (prm.timing) {
-        for (int i = 0; i < TURTLE_STAGE_COUNT; i++) {
+        for (int i = 0; i < TURTLE_STAGE_FILTER; i++) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] = ms;
             else cudaGetLastError();
@@ -404,6 +542,89 @@ int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, con
         L2Fetch l2(prm.l2_fetch_bytes);
         if (k <= 32) run_count<uint64_t>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
         else run_count<Key128>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
+        ctx_end(c, s);
+        return TURTLE_OK;
+    } catch (Fail f) {
+        return fail_code(s, c, f.code);
+    } catch (std::bad_alloc &) {
+        return fail_code(s, c, TURTLE_E_NOMEM);
+    }
+}
+
+// memcpy with several host threads (pageable source -> pinned staging buffer).
+void par_memcpy(void *dst, const void *src, size_t n) {
+    const int T = n >= (64u << 20) ? 8 : 1;
+    if (T == 1) {
+        memcpy(dst, src, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; t++) {
+        const size_t a = n * t / T, b = n * (t + 1) / T;
+        th.emplace_back([=]() { memcpy((char *)dst + a, (const char *)src + a, b - a); });
+    }
+    for (auto &x : th) x.join();
+}
+
+// Stream host reads to the device in chunks through two pinned buffers: while chunk i is
+// copied host->device on the copy stream and packed on `s`, chunk i+1 is staged by the host.
+// Only the 2-bit codes and bitmaps stay on the device; the ASCII is never resident as a whole.
+void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off,
+                   size_t chunk, cudaStream_t s, PrePacked &pp, const LaunchCfg &lc) {
+    const PackLayout L = PackLayout::of(n_bases);
+    pp.P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
+    pp.B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    pp.S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    ck(cudaMemsetAsync(pp.S, 0, 8 * L.b_words, s));
+    chunk = (chunk + 63) & ~(size_t)63;  // chunk starts fall on 64-position boundaries (whole bitmap words)
+    if (c->pinned_bytes < chunk) {
+        for (auto &pb : c->pinned)
+            if (pb) {
+                cudaFreeHost(pb);
+                pb = nullptr;
+            }
+        c->pinned_bytes = 0;
+        for (auto &pb : c->pinned) ck(cudaMallocHost(&pb, chunk));
+        c->pinned_bytes = chunk;
+    }
+    uint8_t *stage[2];
+    for (auto &st : stage) st = (uint8_t *)ctx_alloc(c, chunk, s);
+    for (int i = 0; i < 2; i++) ck(cudaEventRecord(c->ev_packed[i], s));  // both staging buffers start free
+    for (int i = 0; i < 2; i++) ck(cudaEventRecord(c->ev_h2d[i], c->copy_stream));
+    const uint64_t n_chunks = n_bases ? (n_bases + chunk - 1) / chunk : 0;
+    for (uint64_t i = 0; i < n_chunks; i++) {
+        const int b = (int)(i & 1);
+        const uint64_t c0 = i * chunk, c1 = c0 + chunk < n_bases ? c0 + chunk : n_bases;
+        ck(cudaEventSynchronize(c->ev_h2d[b]));  // the pinned buffer's previous copy has finished
+        par_memcpy(c->pinned[b], reads->bases + c0, c1 - c0);
+        ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0));  // its staging buffer was packed
+        ck(cudaMemcpyAsync(stage[b], c->pinned[b], c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
+        ck(cudaEventRecord(c->ev_h2d[b], c->copy_stream));
+        ck(cudaStreamWaitEvent(s, c->ev_h2d[b], 0));
+        const uint64_t g0 = c0 / 32, g1 = i + 1 == n_chunks ? L.pack_groups() : c1 / 32;
+        launch_pack_groups(lc, stage[b] - c0, d_off, reads->n_reads, L, g0, g1, pp.P, pp.B);
+        ck(cudaEventRecord(c->ev_packed[b], s));
+    }
+    if (n_chunks == 0) launch_pack_groups(lc, nullptr, d_off, reads->n_reads, L, 0, L.pack_groups(), pp.P, pp.B);
+    launch_mark_starts(lc, d_off, reads->n_reads, L, pp.S, c->d_err);
+}
+
+// Host-memory input streamed through pinned double buffers, then the path on the packed reads.
+int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off, int k,
+                        uint32_t min_count, const turtle_params *params, size_t chunk, cudaStream_t s,
+                        DeviceOut &o) {
+    const turtle_params prm = resolve(params);
+    if (!params_ok(prm)) return TURTLE_E_ARG;
+    try {
+        ctx_begin(c, s);
+        L2Fetch l2(prm.l2_fetch_bytes);
+        const LaunchCfg lc{c->sms, s};
+        PrePacked pp{};
+        pack_streamed(c, reads, n_bases, d_off, chunk, s, pp, lc);
+        if (k <= 32) run_count<uint64_t>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp);
+        else run_count<Key128>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp);
+        c->stats.stage_launches[TURTLE_STAGE_PACK] = (uint32_t)((n_bases + chunk - 1) / chunk + 1);
+        c->stats.launches += c->stats.stage_launches[TURTLE_STAGE_PACK];
         ctx_end(c, s);
         return TURTLE_OK;
     } catch (Fail f) {
@@ -484,6 +705,9 @@ int turtle_ctx_create(int device, turtle_ctx **out) {
         ck(cudaMallocHost(&c->h_err, 64));
         ck(cudaMallocHost(&c->h_hist, 8 * 256 * 16));
         for (auto &e : c->ev) ck(cudaEventCreate(&e));
+        for (auto &e : c->ev_h2d) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &e : c->ev_packed) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ck(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     } catch (Fail f) {
         turtle_ctx_destroy(c);
         return f.code;
@@ -507,6 +731,13 @@ void turtle_ctx_destroy(turtle_ctx *c) {
     if (c->h_hist) cudaFreeHost(c->h_hist);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->ev_h2d)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : c->ev_packed)
+        if (e) cudaEventDestroy(e);
+    for (auto &pb : c->pinned)
+        if (pb) cudaFreeHost(pb);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
@@ -554,28 +785,46 @@ static turtle_ctx *default_ctx(int *rc) {
     return g_default[dev];
 }
 
-int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params, void *stream,
-                    turtle_result *out) {
+}  // extern "C"
+
+uint64_t footprint_estimate(uint64_t n_bases, uint64_t n_reads, int k, uint32_t min_count, const turtle_params *p) {
+    turtle_params d;
+    turtle_params_default(&d);
+    const turtle_params &prm = (p && p->struct_size == sizeof(turtle_params)) ? *p : d;
+    const double kb = k <= 32 ? 8.0 : 16.0;
+    const double filter = min_count >= 2 ? prm.filter_bits_per_window / 8.0 : 0.0;
+    const double per_base = 1.0 + 0.25 + 3.0 / 8.0 + 2.0 * kb + 12.0 + filter + 8.0;  // windows <= bases
+    return (uint64_t)(per_base * (double)n_bases) + 8 * (n_reads + 1) + (64ull << 20);
+}
+
+// Host-memory form on a given context: copy (or stream) the reads in, run the path, copy the result out.
+int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
+                    void *stream, turtle_result *out) {
     if (!out) return TURTLE_E_ARG;
     memset(out, 0, sizeof(*out));
     if (!reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64 || min_count < 1)
         return TURTLE_E_ARG;
-    for (uint64_t i = 0; i < reads->n_reads; i++)
-        if (reads->offsets[i + 1] < reads->offsets[i]) return TURTLE_E_ARG;
-    std::lock_guard<std::mutex> g(g_default_mu);
+    // every offsets pair is checked on the device while packing (TURTLE_E_ARG)
     int rc = 0;
-    turtle_ctx *c = default_ctx(&rc);
-    if (!c) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t n_bases = reads->offsets[reads->n_reads];
+    const turtle_params prm = resolve(params);
+    size_t chunk = (size_t)prm.stream_chunk_mib << 20;
+    if (!chunk) {  // stream when the ASCII would take more than a quarter of the free device memory
+        size_t free_b = 0, total_b = 0;
+        if (cudaSetDevice(c->device) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+            n_bases > free_b / 4)
+            chunk = (size_t)1 << 30;
+        cudaGetLastError();
+    }
+    const bool streamed = chunk != 0;
     uint8_t *d_bases = nullptr;
     uint64_t *d_off = nullptr;
     try {
         ck(cudaSetDevice(c->device));
-        ck(cudaSetDevice(c->device));
-        ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
+        if (!streamed) ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
         ck(cudaMallocFromPoolAsync((void **)&d_off, 8 * (reads->n_reads + 1), c->pool, s));
-        if (n_bases) ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
+        if (n_bases && !streamed) ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
         ck(cudaMemcpyAsync(d_off, reads->offsets, 8 * (reads->n_reads + 1), cudaMemcpyHostToDevice, s));
     } catch (Fail f) {
         if (d_bases) cudaFreeAsync(d_bases, s);
@@ -583,8 +832,9 @@ int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const 
         return f.code;
     }
     DeviceOut o;
-    rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o);
-    cudaFreeAsync(d_bases, s);
+    if (streamed) rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o);
+    else rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o);
+    if (d_bases) cudaFreeAsync(d_bases, s);
     cudaFreeAsync(d_off, s);
     if (rc) return rc;
     const int kw = k <= 32 ? 1 : 2;
@@ -605,6 +855,22 @@ int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const 
     out->n = o.n;
     out->n_windows = o.n_windows;
     return TURTLE_OK;
+}
+
+extern "C" {
+
+int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params, void *stream,
+                    turtle_result *out) {
+    if (!out) return TURTLE_E_ARG;
+    memset(out, 0, sizeof(*out));
+    if (!reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64 || min_count < 1)
+        return TURTLE_E_ARG;  // argument errors are reported before any device is touched
+    if (reads->offsets[reads->n_reads] < reads->offsets[0]) return TURTLE_E_ARG;  // the device checks every pair
+    std::lock_guard<std::mutex> g(g_default_mu);
+    int rc = 0;
+    turtle_ctx *c = default_ctx(&rc);
+    if (!c) return rc;
+    return count_host_impl(c, reads, k, min_count, params, stream, out);
 }
 
 int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_result *out) {

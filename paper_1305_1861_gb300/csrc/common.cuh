@@ -103,6 +103,30 @@ template <> __device__ __forceinline__ Key128 canonical<Key128>(const uint64_t *
     return canonical_at128(P, s, k);
 }
 
+// ---------------------------------------------------------------- key-range parts
+// Monotone map of a canonical key to [0, 2^62): v = top 31 bits of the 2k-bit key,
+// f(v) = v * (2^32 - v), which is increasing on [0, 2^31). For random sequence the
+// canonical key min(x, rc(x)) has density 2(1 - u) on u in [0, 1), whose CDF
+// u(2 - u) equals f(v) / 2^62: equal slices of f hold about equal numbers of keys.
+// Part p of 2^bits takes the keys with f(v) >> (62 - bits) == p; since f is
+// monotone, parts are ordered key ranges.
+__device__ __forceinline__ uint64_t top31(uint64_t key, int k) {
+    const int b = 2 * k;
+    return b >= 31 ? key >> (b - 31) : key << (31 - b);
+}
+__device__ __forceinline__ uint64_t top31(Key128 key, int k) {
+    const int b = 2 * k;  // 66..128 bits: the top 31 start inside hi or straddle hi/lo
+    const int sh = b - 31;
+    if (sh >= 64) return key.hi >> (sh - 64);
+    return (key.hi << (64 - sh)) | (key.lo >> sh);
+}
+template <class K>
+__device__ __forceinline__ uint32_t key_part(K key, int k, int part_bits) {
+    if (part_bits == 0) return 0;
+    const uint64_t v = top31(key, k);
+    return (uint32_t)((v * ((1ull << 32) - v)) >> (62 - part_bits));
+}
+
 // ---------------------------------------------------------------- key loads/stores
 __device__ __forceinline__ uint64_t load_stream(const uint64_t *p) { return __ldcs(p); }  // read once
 __device__ __forceinline__ Key128 load_stream(const Key128 *p) {

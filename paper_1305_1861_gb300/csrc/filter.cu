@@ -27,14 +27,17 @@ constexpr int P1_TILE = WARP * P1_ILP;       // 128 starts per warp tile (two V 
 constexpr int P1_STAGE = 256;                // keys per candidate flush
 constexpr int P1_BUF = P1_STAGE + WARP;      // warp staging buffer capacity
 
+// A stream written with `down` fills its buffer from the top: entry j lands at cap-1-j, so
+// candidates (from the bottom) and first sightings (from the top) can share one buffer.
 template <class K>
 __device__ __forceinline__ void flush_full(K *wbuf, int &nbuf, K *out, unsigned long long *cursor,
-                                           uint64_t cap, uint32_t *err, int lane) {
+                                           uint64_t cap, uint32_t *err, int lane, bool down = false) {
     __syncwarp();
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(cursor, (unsigned long long)P1_STAGE);
     base = __shfl_sync(FULL, base, 0);
     if (base + P1_STAGE <= cap) {
+        if (down) base = cap - base - P1_STAGE;
 #pragma unroll
         for (int j = 0; j < P1_STAGE / WARP; j++) store_key(out + base + lane + WARP * j, wbuf[lane + WARP * j]);
     } else if (lane == 0) {
@@ -51,13 +54,14 @@ __device__ __forceinline__ void flush_full(K *wbuf, int &nbuf, K *out, unsigned 
 
 template <class K>
 __device__ __forceinline__ void flush_rest(K *wbuf, int nbuf, K *out, unsigned long long *cursor, uint64_t cap,
-                                           uint32_t *err, int lane) {
+                                           uint32_t *err, int lane, bool down = false) {
     __syncwarp();
     if (nbuf <= 0) return;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(cursor, (unsigned long long)nbuf);
     base = __shfl_sync(FULL, base, 0);
     if (base + nbuf <= cap) {
+        if (down) base = cap - base - nbuf;
         for (int j = lane; j < nbuf; j += WARP) store_key(out + base + j, wbuf[j]);
     } else if (lane == 0) {
         atomicOr(err, ERR_CAND_OVERFLOW);
@@ -84,7 +88,8 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     const uint64_t *__restrict__ patterns, uint32_t pat_mask,
                                                     K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                                                     K *firsts, unsigned long long *first_count, uint64_t first_cap,
-                                                    uint64_t *hist, int hist_passes, uint32_t *err) {
+                                                    uint64_t *hist, int hist_passes, int part_bits, uint32_t part_lo,
+                                                    uint32_t part_hi, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
     K *s_buf = reinterpret_cast<K *>(smem);
@@ -115,6 +120,12 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             ok[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
             if (ok[i]) {
                 key[i] = canonical<K>(P, s, k);
+                if (part_bits) {  // keys of other key ranges wait for their own super-partition
+                    const uint32_t pt = key_part(key[i], k, part_bits);
+                    ok[i] = pt >= part_lo && pt < part_hi;
+                }
+            }
+            if (ok[i]) {
                 if (USE_FILTER) {
                     const uint64_t h = key_hash(key[i]);
                     const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
@@ -155,18 +166,47 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                 const uint32_t bf = __ballot_sync(FULL, f);
                 if (f) fbuf[nfirst + __popc(bf & lt)] = key[i];
                 nfirst += __popc(bf);
-                if (nfirst >= P1_STAGE) flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane);
+                if (nfirst >= P1_STAGE) flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
             }
         }
     }
     __syncwarp();
     hist_keys(wbuf, nbuf, s_hist, hist_passes, lane);
     flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
-    if (EMIT_FIRSTS) flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane);
+    if (EMIT_FIRSTS) flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
     __syncthreads();
     for (int i = threadIdx.x; i < 256 * hist_passes; i += P1_BLOCK)
         if (s_hist[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)s_hist[i]);
 }
+
+// Number of valid windows in each of the 2^part_bits key-range parts (sizes the super-partitions).
+template <class K>
+__global__ void __launch_bounds__(256) k_part_count(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                    uint64_t n_pos, int k, int part_bits,
+                                                    unsigned long long *counts) {
+    extern __shared__ uint32_t s_cnt[];
+    const int nparts = 1 << part_bits;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_pos; s += (uint64_t)gridDim.x * blockDim.x)
+        if ((V[s >> 6] >> (s & 63)) & 1) atomicAdd(&s_cnt[key_part(canonical<K>(P, s, k), k, part_bits)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(&counts[i], (unsigned long long)s_cnt[i]);
+}
+
+template <class K>
+void launch_part_count(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                       int part_bits, unsigned long long *counts) {
+    uint64_t need = (L.n_bases + 255) / 256;
+    const uint64_t cap = (uint64_t)c.sms * 8;
+    k_part_count<K><<<(int)(need < cap ? (need ? need : 1) : cap), 256, 4u << part_bits, c.stream>>>(
+        P, V, L.n_bases, k, part_bits, counts);
+}
+template void launch_part_count<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
+                                          const uint64_t *, int, unsigned long long *);
+template void launch_part_count<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
+                                        const uint64_t *, int, unsigned long long *);
 
 template <class K>
 __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys, uint64_t n, uint64_t *filter,
@@ -189,7 +229,7 @@ template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
-                  uint32_t *err) {
+                  int part_bits, uint32_t part_lo, uint32_t part_hi, uint32_t *err) {
     const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     const bool emit_firsts = use_filter && firsts != nullptr;
     if (!hist) hist_passes = 0;
@@ -205,7 +245,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     int grid = (int)(need < cap ? (need ? need : 1) : cap);
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
                                              cand, cand_count, cand_cap, firsts, first_count, first_cap, hist,
-                                             hist_passes, err);
+                                             hist_passes, part_bits, part_lo, part_hi, err);
 }
 
 template <class K>
@@ -218,10 +258,11 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
-                                     unsigned long long *, uint64_t, uint64_t *, int, uint32_t *);
+                                     unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, uint32_t *);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
-                                   unsigned long long *, uint64_t, uint64_t *, int, uint32_t *);
+                                   unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
+                                   uint32_t *);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

@@ -21,6 +21,7 @@ struct PackLayout {
         L.v_words = (n_bases + 63) / 64 + 2;
         return L;
     }
+    uint64_t pack_groups() const { return 2 * b_words; }  // groups of 32 positions, padding included
 };
 
 struct LaunchCfg {
@@ -31,6 +32,11 @@ struct LaunchCfg {
 // a1: P <- 2-bit codes, B <- ambiguous/out-of-read bits, S <- read-start bits (S must be zero on entry).
 void launch_pack(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
                  const PackLayout &L, uint64_t *P, uint64_t *B, uint64_t *S, uint32_t *err);
+// a1 in pieces: groups [g_begin, g_end) of 32 positions (bases indexed by absolute position), and S.
+void launch_pack_groups(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
+                        const PackLayout &L, uint64_t g_begin, uint64_t g_end, uint64_t *P, uint64_t *B);
+void launch_mark_starts(const LaunchCfg &c, const uint64_t *offsets, uint64_t n_reads, const PackLayout &L,
+                        uint64_t *S, uint32_t *err);
 // a1/a2: V <- valid-window bits for k; *n_windows += popcount(V) (zero it first).
 void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *B, const uint64_t *S,
                   uint64_t *V, unsigned long long *n_windows);
@@ -48,13 +54,19 @@ struct FilterGeom {
 
 // a2+a3: pass 1. Emits the canonical key of every valid window whose filter test says "seen"
 // (every valid window when use_filter is false) to cand[0 .. *cand_count); with a filter and a
-// non-null firsts buffer, the other windows (first sightings) go to firsts[0 .. *first_count).
+// non-null firsts buffer, the other windows (first sightings) fill firsts[first_cap - *first_count ..
+// first_cap) from the top, so firsts may be the candidate buffer itself (cand + first_cap == end).
 // hist (non-null): += the 256-bin digit counts of the candidates for radix passes 0..hist_passes-1.
+// part_bits > 0: only windows whose key lies in key-range parts [part_lo, part_hi) of 2^part_bits take part.
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
-                  uint32_t *err);
+                  int part_bits, uint32_t part_lo, uint32_t part_hi, uint32_t *err);
+// Valid windows per key-range part (counts: 2^part_bits zeroed counters).
+template <class K>
+void launch_part_count(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                       int part_bits, unsigned long long *counts);
 // a3 alone on a key array.
 template <class K>
 void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const FilterGeom &f, int set, uint8_t *seen);

@@ -26,12 +26,15 @@ __device__ __forceinline__ void decode4(uint32_t x, uint32_t &codes8, uint32_t &
 }
 
 // One thread per group of 32 positions: P[g] (uint64) and 32 bad bits (half of a B word).
+// `bases` is indexed by absolute position; for a streamed chunk it is the staging buffer
+// shifted back by the chunk's first position, and only groups [g_begin, g_end) are touched.
 __global__ void __launch_bounds__(256) k_pack(const uint8_t *__restrict__ bases, uint64_t n_bases,
                                               const uint64_t *__restrict__ offsets, uint64_t n_reads,
-                                              uint64_t n_groups, uint64_t *__restrict__ P, uint32_t *__restrict__ B32) {
+                                              uint64_t g_begin, uint64_t g_end, uint64_t *__restrict__ P,
+                                              uint32_t *__restrict__ B32) {
     const uint64_t lo = offsets[0], hi = offsets[n_reads] < n_bases ? offsets[n_reads] : n_bases;
     const bool aligned = (((uintptr_t)bases) & 15u) == 0;
-    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_groups;
+    for (uint64_t g = g_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < g_end;
          g += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t p0 = g * 32;
         uint32_t w[8];
@@ -132,13 +135,24 @@ static int grid_for(uint64_t items, int block, int sms, int per_sm) {
     return (int)(need < cap ? need : cap);
 }
 
-void launch_pack(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
-                 const PackLayout &L, uint64_t *P, uint64_t *B, uint64_t *S, uint32_t *err) {
-    const uint64_t n_groups = 2 * L.b_words;  // covers every B word, including the padding (all bad)
-    k_pack<<<grid_for(n_groups, 256, c.sms, 16), 256, 0, c.stream>>>(bases, L.n_bases, offsets, n_reads, n_groups,
-                                                                     P, reinterpret_cast<uint32_t *>(B));
+void launch_pack_groups(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
+                        const PackLayout &L, uint64_t g_begin, uint64_t g_end, uint64_t *P, uint64_t *B) {
+    if (g_end <= g_begin) return;
+    k_pack<<<grid_for(g_end - g_begin, 256, c.sms, 16), 256, 0, c.stream>>>(
+        bases, L.n_bases, offsets, n_reads, g_begin, g_end, P, reinterpret_cast<uint32_t *>(B));
+}
+
+void launch_mark_starts(const LaunchCfg &c, const uint64_t *offsets, uint64_t n_reads, const PackLayout &L,
+                        uint64_t *S, uint32_t *err) {
     k_mark_starts<<<grid_for(n_reads + 1, 256, c.sms, 8), 256, 0, c.stream>>>(offsets, n_reads, L.n_bases,
                                                                             reinterpret_cast<uint32_t *>(S), err);
+}
+
+void launch_pack(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offsets, uint64_t n_reads,
+                 const PackLayout &L, uint64_t *P, uint64_t *B, uint64_t *S, uint32_t *err) {
+    // every B word, including the padding (all bad)
+    launch_pack_groups(c, bases, offsets, n_reads, L, 0, L.pack_groups(), P, B);
+    launch_mark_starts(c, offsets, n_reads, L, S, err);
 }
 
 void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *B, const uint64_t *S, uint64_t *V,

@@ -273,3 +273,29 @@ def test_fly_shaped_scaled_with_repeats_and_n(ctx):
     """Fly-shaped library at 1/100 scale (1 Mbp + repeats, 300k reads, 0.05% N): exact."""
     lib = synth.fly(seed=2, scale=0.01)
     _check_count(ctx, lib.bases, lib.offsets, 31, 2)
+
+
+@pytest.mark.parametrize("k,min_count,rw", [(31, 2, 0), (31, 2, 1), (31, 1, 0), (64, 2, 0), (64, 3, 1), (17, 2, 0)])
+def test_count_in_key_range_super_partitions(ctx, k, min_count, rw):
+    """A 1 MiB budget forces the key space into many consecutive ranges; the output must not change."""
+    import paper_1305_1861_gb300 as pkg
+
+    lib = synth.longk(seed=9, scale=0.002, k=k)
+    b, o = lib.chunk(0, lib.n_reads)
+    p = pkg.Params.default(budget_mib=1, recount_windows=rw)
+    st = _check_count(ctx, b, o, k, min_count, p)
+    assert st["super_partitions"] > 4
+    st = _check_count(ctx, b, o, k, min_count, pkg.Params.default(recount_windows=rw))
+    assert st["super_partitions"] == 1
+
+
+@pytest.mark.parametrize("k,chunk_mib", [(31, 1), (64, 1), (45, 2)])
+def test_host_form_streamed_through_pinned_chunks(have_gpu, k, chunk_mib):
+    """Host reads streamed in small chunks (many chunk boundaries inside reads): same result."""
+    import paper_1305_1861_gb300 as pkg
+
+    lib = synth.longk(seed=5, scale=0.001, k=k)  # ~35 Mbase: tens of 1-2 MiB chunks
+    b, o = lib.chunk(0, lib.n_reads)
+    keys, counts, nw = pkg.turtle_count(b, o, k, 2, pkg.Params.default(stream_chunk_mib=chunk_mib))
+    ok, oc, onw = oracle.count(b, o, k, 2)
+    assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
