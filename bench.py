@@ -31,6 +31,10 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "canonical k-mers/s"
+HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/served vs plain"
+# DRAM bytes (read + write) per unit measured by ncu on the 1/10-scale fly-shaped case (64-bit keys),
+# see profiles/: scaled to a full launch by the units that launch processes.
+NCU_BYTES_PER_UNIT = {"sort": 16.14, "filter": 131.23, "recount": 204.65}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -41,7 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk"])
+    ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk", "served", "batched"])
+    ap.add_argument("--jobs", type=int, default=1000, help="served: number of jobs (Poisson arrivals, 50/s)")
+    ap.add_argument("--workers", type=int, default=8, help="served: concurrent jobs on the device")
+    ap.add_argument("--saturate-jobs", type=int, default=300,
+                    help="served: also submit this many jobs at once (no arrival gaps) to compare capacity")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample-reads", type=int, default=0, help="reads in the oracle sample (0 = auto)")
@@ -266,11 +274,14 @@ def run_ours(args, rank, world):
     dom = max(("filter", "recount", "sort"), key=lambda s: avg[s])
     hbm, src = peaks()
     ach = alg_bytes(dom, st, lib) / (per_launch[dom] / 1e3) / 1e9
+    units = {"sort": st["n_candidates"], "filter": W, "recount": st["n_firsts"]}[dom]
+    traffic = NCU_BYTES_PER_UNIT[dom] * units if lib.k <= 32 and units else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
-            "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
+            "traffic_note": "ncu dram bytes per unit on the 1/10-scale case x units per launch" if traffic else None,
             "stage_ms": {s: round(v, 3) for s, v in avg.items()}}
 
-    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+    out = {"metric": HEADLINE, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u64" if lib.k <= 32 else "u128", "data": "synthetic",
            "config": {"workload": desc, "k": lib.k, "min_count": lib.min_count, "windows": W,
@@ -302,7 +313,7 @@ def run_reference(args, rank, world):
         vals.append(r["value"])
         last = r
     v = float(np.median(vals))
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+    return {"impl": "reference", "metric": HEADLINE, "value": v, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64" if lib.k <= 32 else "u128", "data": "synthetic",
             "config": {"workload": desc, "k": lib.k, "min_count": lib.min_count},
@@ -363,8 +374,119 @@ def micro():
     print(json.dumps({"micro": "random 32-byte sectors over a 4 GiB table", "accesses": idx.numel(), **res}))
 
 
+def run_served(args):
+    """Served form: Poisson arrivals (50 jobs/s) of 1-50 Mbase libraries, k in {25,31,63}, min_count in {2,3}.
+
+    The same arrival stream is driven through the server twice: with `--workers` concurrent jobs
+    (continuous batching) and with one worker (the plain per-library form behind a FIFO queue).
+    """
+    import queue
+
+    import paper_1305_1861_gb300 as pkg
+
+    specs = synth.served_jobs(seed=5, n_jobs=args.jobs, rate=50.0, scale=args.scale)
+    jobs = []
+    for sp in specs:
+        lib = synth.library_from_spec(sp)
+        jobs.append((lib.bases, lib.offsets, sp["k"], sp["min_count"], sp["t"]))
+
+    def drive(workers, jobs=jobs, paced=True):
+        srv = pkg.Server(0, hbm_budget_bytes=0, max_concurrent=workers)
+        for b, o, k, m, _ in jobs[:4]:  # warm every worker's context
+            srv.poll(srv.submit(b, o, k, m))
+        pending = queue.Queue()
+        lat, windows, done_at = [], 0, [0.0]
+
+        def collect():
+            nonlocal windows
+            while True:
+                t = pending.get()
+                if t is None:
+                    return
+                _, _, nw, tm = srv.poll(t)
+                lat.append(tm.total_ms)
+                windows += nw
+                done_at[0] = time.perf_counter()
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for b, o, k, m, at in jobs:
+            delay = at - (time.perf_counter() - t0)
+            if paced and delay > 0:
+                time.sleep(delay)
+            pending.put(srv.submit(b, o, k, m))
+        pending.put(None)
+        th.join()
+        st = srv.stats()
+        srv.close()
+        span = done_at[0] - t0
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(np.mean(lat)), "kmers_per_s": windows / span, "makespan_s": span,
+                "windows": windows, "peak_running": st["peak_running"], "peak_queued": st["peak_queued"],
+                "peak_admitted_gb": st["peak_admitted_bytes"] / 1e9}
+
+    served = drive(args.workers)
+    plain = drive(1)
+    burst = jobs[: args.saturate_jobs]
+    sat_served = drive(args.workers, burst, paced=False)
+    sat_plain = drive(1, burst, paced=False)
+    return {"metric": "served: p50/p99 job latency and aggregate canonical k-mers/s", "value": served["kmers_per_s"],
+            "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "served: %d jobs, Poisson arrivals 50/s, read bases log-uniform %.1f-%.0f Mbase, "
+                                   "100 bp, 1%% substitutions, k in {25,31,63}, min_count in {2,3}"
+                                   % (len(jobs), 1.0 * args.scale, 50.0 * args.scale),
+                       "workers": args.workers},
+            "served": served, "plain_fifo_1_worker": plain,
+            "p99_speedup_vs_plain": plain["p99_ms"] / served["p99_ms"],
+            "saturated": {"jobs": len(burst), "served": sat_served, "plain_fifo_1_worker": sat_plain,
+                          "throughput_vs_plain": sat_served["kmers_per_s"] / sat_plain["kmers_per_s"]}}
+
+
+def run_batched(args):
+    """Batched form: 64 libraries (genome log-uniform 0.1-20 Mbp, coverage U(10,60), 100/150 bp, 1% errors,
+    k in {21,31,55}) counted by turtle_count_batch vs 64 sequential turtle_count calls (host memory, end to end)."""
+    import paper_1305_1861_gb300 as pkg
+
+    specs = synth.batched_specs(seed=4, n_libs=64, scale=args.scale)
+    libs = [synth.library_from_spec(sp) for sp in specs]
+    jobs = [(lib.bases, lib.offsets, lib.k, lib.min_count) for lib in libs]
+
+    def plain():
+        return [pkg.turtle_count(b, o, k, m) for b, o, k, m in jobs]
+
+    def batched():
+        return pkg.turtle_count_batch(jobs)
+
+    res = {}
+    for name, fn in (("plain_64_calls", plain), ("batched", batched)):
+        for _ in range(max(1, args.warmup)):
+            out = fn()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            out = fn()
+        dt = (time.perf_counter() - t0) / args.steps
+        W = sum(o[2] for o in out)
+        res[name] = {"s_per_batch": dt, "kmers_per_s": W / dt, "windows": W}
+    ok = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(plain(), batched()))
+    return {"metric": "batched vs plain: canonical k-mers/s over 64 libraries", "value": res["batched"]["kmers_per_s"],
+            "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "steps": args.steps,
+            "config": {"workload": "batched: 64 libraries, genome log-uniform %.3g-%.3g Mbp, coverage U(10,60), "
+                                   "R in {100,150}, 1%% substitutions, k in {21,31,55}, min_count 2; %.2f Gbase"
+                                   % (0.1 * args.scale, 20 * args.scale, sum(l.bases.size for l in libs) / 1e9)},
+            "batched": res["batched"], "plain": res["plain_64_calls"],
+            "speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched"]["s_per_batch"],
+            "identical_results": ok}
+
+
 def main():
     args = parse()
+    if args.workload == "batched":
+        print(json.dumps(run_batched(args)), flush=True)
+        return
+    if args.workload == "served":
+        print(json.dumps(run_served(args)), flush=True)
+        return
     if args.micro:
         micro()
         return

@@ -237,6 +237,19 @@ typedef struct {
     uint32_t min_count;
 } turtle_job;
 
+/*
+ * Batched form: count many libraries (jobs, host memory) with one pipeline per group
+ * instead of one per library. Libraries with the same k and min_count are concatenated
+ * on the device and every window's key carries its library index in the key bits above
+ * 2k, so each stage is one launch for the whole group and libraries never mix; a group
+ * holds up to 64 libraries (fewer when 2k leaves less room: k = 31 takes 4 per run,
+ * k = 32 and k = 64 one). outs[i] receives job i's result, identical to turtle_count on
+ * that job (free each with turtle_result_free). Uses the internal context of the
+ * current device.
+ */
+int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_params *params, void *stream,
+                       turtle_result *outs);
+
 typedef struct {
     double queue_ms;  /* submit -> admitted */
     double run_ms;    /* admitted -> result ready */

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 __all__ = [
-    "TurtleError", "Params", "Context", "Server", "load", "build", "turtle_count", "turtle_strerror", "STAGES",
+    "TurtleError", "Params", "Context", "Server", "load", "build", "turtle_count", "turtle_count_batch",
+    "turtle_strerror", "STAGES",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +108,7 @@ def load():
         "turtle_filter": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, _p, u64, _p, ctypes.c_int, _p, _p]),
         "turtle_sort_compact": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
         "turtle_sort_compact_noalloc": (ctypes.c_int, [_p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
+        "turtle_count_batch": (ctypes.c_int, [_p, ctypes.c_size_t, _p, _p, _p]),
         "turtle_server_create": (ctypes.c_int, [ctypes.c_int, u64, ctypes.c_int, _p, _p]),
         "turtle_submit": (ctypes.c_int, [_p, _p, _p]),
         "turtle_poll": (ctypes.c_int, [_p, u64, ctypes.c_int, _p, _p]),
@@ -203,6 +205,35 @@ class JobTimes(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, u64) for n in ("budget_bytes", "admitted_bytes", "peak_admitted_bytes", "submitted", "completed",
                                    "failed", "queued", "running", "peak_running", "peak_queued")]
+
+
+def turtle_count_batch(jobs, params: Params | None = None, stream=None):
+    """Batched form. jobs: [(bases, offsets, k, min_count)] in host memory -> [(keys, counts, n_windows)]."""
+    lib = load()
+    keep = []
+    arr = (_Job * max(len(jobs), 1))()
+    for i, (b, o, k, m) in enumerate(jobs):
+        b = _np(b, np.uint8)
+        o = _np(o, np.uint64)
+        keep.append((b, o))
+        arr[i] = _Job(b.ctypes.data if b.size else None, o.ctypes.data, o.size - 1, k, m)
+    outs = (_Result * max(len(jobs), 1))()
+    rc = lib.turtle_count_batch(arr, len(jobs), ctypes.byref(params) if params else None, _stream_ptr(stream), outs)
+    _check(rc, "turtle_count_batch")
+    res = []
+    try:
+        for i, (_, _, k, _) in enumerate(jobs):
+            r = outs[i]
+            w = 2 if k > 32 else 1
+            n = r.n
+            keys = np.ctypeslib.as_array(r.keys, shape=(max(n * w, 1),))[: n * w].copy() if n else \
+                np.zeros(0, dtype=np.uint64)
+            counts = np.ctypeslib.as_array(r.counts, shape=(max(n, 1),))[:n].copy() if n else np.zeros(0, np.uint32)
+            res.append((_shape_keys(keys, n, k), counts, int(r.n_windows)))
+    finally:
+        for i in range(len(jobs)):
+            lib.turtle_result_free(ctypes.byref(outs[i]))
+    return res
 
 
 class Server:

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -211,6 +212,14 @@ struct PrePacked {
     uint64_t *P, *B, *S;
 };
 
+// Batched form: positions [lib_starts[l], lib_starts[l+1]) are library l; keys carry l above their 2k bits.
+struct BatchTag {
+    const uint64_t *lib_starts;  // device, n_libs + 1
+    int n_libs;
+    int tag_bits;
+    unsigned long long *lib_windows;  // device, n_libs counters (zeroed by run_count)
+};
+
 struct DeviceOut {
     void *keys = nullptr;
     uint32_t *counts = nullptr;
@@ -220,7 +229,7 @@ struct DeviceOut {
 template <class K>
 void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
                int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s, DeviceOut &out,
-               const PrePacked *pre = nullptr) {
+               const PrePacked *pre = nullptr, const BatchTag *tag = nullptr) {
     constexpr int KW = sizeof(K) / 8;
     const LaunchCfg lc{c->sms, s};
     turtle_stats st{};
@@ -253,6 +262,10 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS);
     tm.stop(TURTLE_STAGE_VALID);
     st.stage_launches[TURTLE_STAGE_VALID] = 1;
+    if (tag) {
+        ck(cudaMemsetAsync(tag->lib_windows, 0, 8 * tag->n_libs, s));
+        launch_lib_windows(lc, L, V, tag->lib_starts, tag->n_libs, tag->lib_windows);
+    }
     read_back(c, s);
     const uint64_t W = c->h_ctr[C_WINDOWS];
     st.n_windows = W;
@@ -267,7 +280,8 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
 
     const bool use_filter = min_count >= 2;
     const bool firsts_mode = use_filter && !prm.recount_windows;
-    const int passes = sort_passes_for(2 * k);
+    const int key_bits = 2 * k + (tag ? tag->tag_bits : 0);
+    const int passes = sort_passes_for(key_bits);
     const uint64_t *patterns = use_filter ? ctx_patterns(c, prm, s) : nullptr;
 
     // Super-partitions (key routing, Sec. 2.1.5): when the post-filter working set of all windows does
@@ -282,7 +296,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     constexpr int PART_BITS = 6;
     std::vector<std::pair<uint32_t, uint32_t>> groups;  // [part_lo, part_hi) of each super-partition
     std::vector<uint64_t> group_w;
-    if ((double)W * bytes_per_window <= budget) {
+    if (tag || (double)W * bytes_per_window <= budget) {  // batches are sized by the caller: one range
         groups.push_back({0u, 1u << PART_BITS});
         group_w.push_back(W);
     } else {
@@ -342,7 +356,8 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         ck(cudaMemsetAsync(hist, 0, 8 * 256 * passes, s));
         tm.start(TURTLE_STAGE_FILTER);
         launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wg, firsts, ctr + C_FIRST, Wg, hist,
-                        passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second, err);
+                        passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
+                        tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, err);
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;
         ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
@@ -366,7 +381,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
         tm.start(TURTLE_STAGE_SORT);
         int passes_run = 0;
-        K *sorted = launch_radix_sort<K>(lc, cand, n_cand, 2 * k, ss, err, true, skip, &passes_run);
+        K *sorted = launch_radix_sort<K>(lc, cand, n_cand, key_bits, ss, err, true, skip, &passes_run);
         tm.stop(TURTLE_STAGE_SORT);
         st.sort_passes = (uint32_t)passes_run;
         st.stage_launches[TURTLE_STAGE_SORT] += n_cand > 1 ? passes_run + 1 : 0;
@@ -634,6 +649,84 @@ int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bas
     }
 }
 
+// One batched run: libraries `idx` (same k and min_count) concatenated on the device, counted by
+// one pipeline with library-tagged keys, results split back per library into outs[].
+template <class K>
+int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, int tag_bits,
+              const turtle_params *params, cudaStream_t s, turtle_result *outs) {
+    const int k = jobs[idx[0]].k;
+    const uint32_t min_count = jobs[idx[0]].min_count;
+    const int n_libs = (int)idx.size();
+    const turtle_params prm = resolve(params);
+    if (!params_ok(prm)) return TURTLE_E_ARG;
+    std::vector<uint64_t> lib_starts(n_libs + 1, 0), entry_starts(n_libs + 1, 0);
+    for (int l = 0; l < n_libs; l++) {
+        const turtle_job &j = jobs[idx[l]];
+        lib_starts[l + 1] = lib_starts[l] + (j.offsets[j.n_reads] - j.offsets[0]);
+        entry_starts[l + 1] = entry_starts[l] + j.n_reads;
+    }
+    const uint64_t n_bases = lib_starts[n_libs], n_reads = entry_starts[n_libs];
+    std::vector<unsigned long long> lib_windows(n_libs, 0);
+    DeviceOut o;
+    try {
+        ctx_begin(c, s);
+        const LaunchCfg lc{c->sms, s};
+        uint8_t *d_bases = (uint8_t *)ctx_alloc(c, n_bases ? n_bases : 16, s);
+        uint64_t *d_src = (uint64_t *)ctx_alloc(c, 8 * (n_reads + n_libs), s);
+        uint64_t *d_off = (uint64_t *)ctx_alloc(c, 8 * (n_reads + 1), s);
+        uint64_t *d_tab = (uint64_t *)ctx_alloc(c, 8 * 2 * (n_libs + 1), s);  // lib_starts, entry_starts
+        unsigned long long *d_lw = (unsigned long long *)ctx_alloc(c, 8 * n_libs, s);
+        for (int l = 0; l < n_libs; l++) {  // one copy per library straight into place
+            const turtle_job &j = jobs[idx[l]];
+            const uint64_t nb = lib_starts[l + 1] - lib_starts[l];
+            if (nb) ck(cudaMemcpyAsync(d_bases + lib_starts[l], j.bases + j.offsets[0], nb, cudaMemcpyHostToDevice, s));
+            ck(cudaMemcpyAsync(d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), cudaMemcpyHostToDevice, s));
+        }
+        ck(cudaMemcpyAsync(d_tab, lib_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
+        ck(cudaMemcpyAsync(d_tab + n_libs + 1, entry_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
+        launch_batch_offsets(lc, d_src, d_tab + n_libs + 1, d_tab, n_libs, d_off, n_reads + 1);
+        BatchTag tag{d_tab, n_libs, tag_bits, d_lw};
+        L2Fetch l2(prm.l2_fetch_bytes);
+        run_count<K>(c, d_bases, n_bases, d_off, n_reads, k, min_count, prm, s, o, nullptr, &tag);
+        // split on the device: library boundaries + tag bits cleared, then one copy per library
+        std::vector<uint64_t> starts(n_libs + 1, ~0ull);
+        if (tag_bits) {
+            uint64_t *d_starts = (uint64_t *)ctx_alloc(c, 8 * n_libs, s);
+            ck(cudaMemsetAsync(d_starts, 0xff, 8 * n_libs, s));
+            launch_split_tags<K>(lc, (K *)o.keys, o.n, 2 * k, d_starts);
+            ck(cudaMemcpyAsync(starts.data(), d_starts, 8 * n_libs, cudaMemcpyDeviceToHost, s));
+        } else {
+            starts[0] = 0;
+        }
+        ck(cudaMemcpyAsync(lib_windows.data(), d_lw, 8 * n_libs, cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        starts[n_libs] = o.n;
+        for (int l = n_libs - 1; l >= 0; l--)
+            if (starts[l] == ~0ull) starts[l] = starts[l + 1];  // no entries: an empty range
+        const int kw = sizeof(K) / 8;
+        for (int l = 0; l < n_libs; l++) {
+            turtle_result &r = outs[idx[l]];
+            r.k = k;
+            r.n = starts[l + 1] - starts[l];
+            r.n_windows = lib_windows[l];
+            r.keys = (uint64_t *)malloc(8 * kw * (r.n ? r.n : 1));
+            r.counts = (uint32_t *)malloc(4 * (r.n ? r.n : 1));
+            if (!r.keys || !r.counts) throw Fail{TURTLE_E_NOMEM};
+            if (r.n) {
+                ck(cudaMemcpyAsync(r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, cudaMemcpyDeviceToHost, s));
+                ck(cudaMemcpyAsync(r.counts, o.counts + starts[l], 4 * r.n, cudaMemcpyDeviceToHost, s));
+            }
+        }
+        ck(cudaStreamSynchronize(s));
+        ctx_end(c, s);
+    } catch (Fail f) {
+        return fail_code(s, c, f.code);
+    } catch (std::bad_alloc &) {
+        return fail_code(s, c, TURTLE_E_NOMEM);
+    }
+    return TURTLE_OK;
+}
+
 std::mutex g_default_mu;
 turtle_ctx *g_default[64] = {};
 
@@ -871,6 +964,44 @@ int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const 
     turtle_ctx *c = default_ctx(&rc);
     if (!c) return rc;
     return count_host_impl(c, reads, k, min_count, params, stream, out);
+}
+
+int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_params *params, void *stream,
+                       turtle_result *outs) {
+    if ((n_jobs && (!jobs || !outs))) return TURTLE_E_ARG;
+    for (size_t i = 0; i < n_jobs; i++) {
+        memset(&outs[i], 0, sizeof(turtle_result));
+        const turtle_job &j = jobs[i];
+        if (!j.offsets || (j.n_reads && !j.bases) || j.k < 1 || j.k > 64 || j.min_count < 1 ||
+            j.offsets[j.n_reads] < j.offsets[0])
+            return TURTLE_E_ARG;
+    }
+    std::lock_guard<std::mutex> g(g_default_mu);
+    int rc = 0;
+    turtle_ctx *c = default_ctx(&rc);
+    if (!c) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // group by (k, min_count); a run holds as many libraries as the spare key bits can tag (<= 64)
+    std::map<std::pair<int, uint32_t>, std::vector<size_t>> groups;
+    for (size_t i = 0; i < n_jobs; i++) groups[{jobs[i].k, jobs[i].min_count}].push_back(i);
+    for (auto &kv : groups) {
+        const int k = kv.first.first;
+        const int room = (2 * k <= 64 ? 64 : 128) - 2 * k;
+        const size_t per_run = room >= 6 ? 64 : ((size_t)1 << room);
+        const std::vector<size_t> &all = kv.second;
+        for (size_t a = 0; a < all.size(); a += per_run) {
+            std::vector<size_t> idx(all.begin() + a, all.begin() + std::min(all.size(), a + per_run));
+            int tag_bits = 0;
+            while (((size_t)1 << tag_bits) < idx.size()) tag_bits++;
+            rc = 2 * k + tag_bits <= 64 ? batch_run<uint64_t>(c, jobs, idx, tag_bits, params, s, outs)
+                                        : batch_run<Key128>(c, jobs, idx, tag_bits, params, s, outs);
+            if (rc) {
+                for (size_t i = 0; i < n_jobs; i++) turtle_result_free(&outs[i]);
+                return rc;
+            }
+        }
+    }
+    return TURTLE_OK;
 }
 
 int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_result *out) {

@@ -127,6 +127,21 @@ __device__ __forceinline__ uint32_t key_part(K key, int k, int part_bits) {
     return (uint32_t)((v * ((1ull << 32) - v)) >> (62 - part_bits));
 }
 
+// ---------------------------------------------------------------- library tags (batched form)
+// A batch of libraries is one position range per library; a window's key carries its library
+// index in the bits just above the 2k key bits, so libraries never mix in any later step.
+__device__ __forceinline__ uint64_t add_tag(uint64_t key, uint32_t lib, int shift) {
+    return key | ((uint64_t)lib << shift);
+}
+__device__ __forceinline__ Key128 add_tag(Key128 key, uint32_t lib, int shift) {
+    if (shift >= 64) key.hi |= (uint64_t)lib << (shift - 64);
+    else {
+        key.lo |= (uint64_t)lib << shift;
+        if (shift > 0) key.hi |= (uint64_t)lib >> (64 - shift);
+    }
+    return key;
+}
+
 // ---------------------------------------------------------------- key loads/stores
 __device__ __forceinline__ uint64_t load_stream(const uint64_t *p) { return __ldcs(p); }  // read once
 __device__ __forceinline__ Key128 load_stream(const Key128 *p) {

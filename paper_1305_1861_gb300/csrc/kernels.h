@@ -58,11 +58,25 @@ struct FilterGeom {
 // first_cap) from the top, so firsts may be the candidate buffer itself (cand + first_cap == end).
 // hist (non-null): += the 256-bin digit counts of the candidates for radix passes 0..hist_passes-1.
 // part_bits > 0: only windows whose key lies in key-range parts [part_lo, part_hi) of 2^part_bits take part.
+// n_libs > 0 (batched form, <= 64): positions [lib_starts[l], lib_starts[l+1]) belong to library l, whose
+// index is added to every key above its 2k bits.
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
-                  int part_bits, uint32_t part_lo, uint32_t part_hi, uint32_t *err);
+                  int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
+                  uint32_t *err);
+// Valid windows of each library of a batch (counts: n_libs zeroed counters).
+void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,
+                        int n_libs, unsigned long long *counts);
+// Batch offsets: library l's offsets (n_reads_l + 1 entries each, concatenated in src) become positions
+// in the concatenated bases: dst[first_l + r] = src[first_l + l + r] - src[first_l + l] + lib_starts[l].
+void launch_batch_offsets(const LaunchCfg &c, const uint64_t *src, const uint64_t *entry_starts,
+                          const uint64_t *lib_starts, int n_libs, uint64_t *dst, uint64_t n_entries);
+// Batched output sorted by library tag: starts[l] <- first entry of library l (starts pre-set to
+// UINT64_MAX; libraries without entries keep it), and the tag bits (at bit `shift` and up) are cleared.
+template <class K>
+void launch_split_tags(const LaunchCfg &c, K *keys, uint64_t n, int shift, uint64_t *starts);
 // Valid windows per key-range part (counts: 2^part_bits zeroed counters).
 template <class K>
 void launch_part_count(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,

@@ -128,6 +128,78 @@ __global__ void __launch_bounds__(256) k_extract(const uint64_t *__restrict__ P,
     }
 }
 
+// Per-library valid-window counts: each 64-position word is split among the libraries it touches.
+__global__ void k_lib_windows(const uint64_t *__restrict__ V, uint64_t n_words, const uint64_t *__restrict__ lib_starts,
+                              int n_libs, unsigned long long *counts) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_words;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = V[i];
+        if (!v) continue;
+        const uint64_t p0 = i * 64, p1 = p0 + 64;
+        int lo = 0, hi = n_libs;  // library holding p0
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (lib_starts[mid] <= p0) lo = mid;
+            else hi = mid;
+        }
+        for (int l = lo; l < n_libs && lib_starts[l] < p1; l++) {
+            const uint64_t a = lib_starts[l] > p0 ? lib_starts[l] - p0 : 0;
+            const uint64_t b = lib_starts[l + 1] < p1 ? lib_starts[l + 1] - p0 : 64;
+            if (b <= a) continue;
+            const uint64_t m = (b - a == 64) ? ~0ull : (((1ull << (b - a)) - 1) << a);
+            const int c = __popcll(v & m);
+            if (c) atomicAdd(&counts[l], (unsigned long long)c);
+        }
+    }
+}
+
+// Concatenated per-library offsets -> offsets into the concatenated bases (one thread per output entry).
+__global__ void k_batch_offsets(const uint64_t *__restrict__ src, const uint64_t *__restrict__ entry_starts,
+                                const uint64_t *__restrict__ lib_starts, int n_libs, uint64_t *__restrict__ dst,
+                                uint64_t n_entries) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n_entries;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        if (j + 1 == n_entries) {  // the end of the last read
+            dst[j] = lib_starts[n_libs];
+            continue;
+        }
+        int lo = 0, hi = n_libs;  // library whose reads contain output entry j
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (entry_starts[mid] <= j) lo = mid;
+            else hi = mid;
+        }
+        const uint64_t r = j - entry_starts[lo];
+        const uint64_t *o = src + entry_starts[lo] + lo;  // library lo's own offsets
+        dst[j] = o[r] - o[0] + lib_starts[lo];
+    }
+}
+
+// Batched output sorted by library tag. First pass: the first index of each library's run
+// (starts[] holds UINT64_MAX on entry). Second pass (a separate launch, so no thread reads a
+// neighbour whose tag is already cleared): clear the tag bits in place.
+template <class K>
+__device__ __forceinline__ uint32_t tag_of(const K &key, int shift) {
+    if constexpr (sizeof(K) == 8) return (uint32_t)(key >> shift);  // shift < 64 whenever a tag is present
+    else return (uint32_t)(key.hi >> (shift - 64));                // tags of 128-bit runs sit in hi (2k >= 66)
+}
+
+template <class K>
+__global__ void k_tag_starts(const K *keys, uint64_t n, int shift, uint64_t *starts) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = tag_of(keys[i], shift);
+        if (i == 0 || tag_of(keys[i - 1], shift) != t) starts[t] = i;
+    }
+}
+
+template <class K>
+__global__ void k_clear_tags(K *keys, uint64_t n, int shift) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(K) == 8) keys[i] &= (1ull << shift) - 1;
+        else keys[i].hi &= (1ull << (shift - 64)) - 1;
+    }
+}
+
 static int grid_for(uint64_t items, int block, int sms, int per_sm) {
     uint64_t need = (items + block - 1) / block;
     uint64_t cap = (uint64_t)sms * per_sm;
@@ -159,6 +231,27 @@ void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   unsigned long long *n_windows) {
     const uint64_t n_words = L.v_words - 2;
     k_valid<<<grid_for(n_words, 256, c.sms, 8), 256, 0, c.stream>>>(B, S, n_words, k, V, n_windows);
+}
+
+void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,
+                        int n_libs, unsigned long long *counts) {
+    const uint64_t n_words = L.v_words - 2;
+    k_lib_windows<<<grid_for(n_words, 256, c.sms, 8), 256, 0, c.stream>>>(V, n_words, lib_starts, n_libs, counts);
+}
+
+template <class K>
+void launch_split_tags(const LaunchCfg &c, K *keys, uint64_t n, int shift, uint64_t *starts) {
+    if (!n) return;
+    k_tag_starts<K><<<grid_for(n, 256, c.sms, 8), 256, 0, c.stream>>>(keys, n, shift, starts);
+    k_clear_tags<K><<<grid_for(n, 256, c.sms, 8), 256, 0, c.stream>>>(keys, n, shift);
+}
+template void launch_split_tags<uint64_t>(const LaunchCfg &, uint64_t *, uint64_t, int, uint64_t *);
+template void launch_split_tags<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, uint64_t *);
+
+void launch_batch_offsets(const LaunchCfg &c, const uint64_t *src, const uint64_t *entry_starts,
+                          const uint64_t *lib_starts, int n_libs, uint64_t *dst, uint64_t n_entries) {
+    k_batch_offsets<<<grid_for(n_entries, 256, c.sms, 8), 256, 0, c.stream>>>(src, entry_starts, lib_starts, n_libs,
+                                                                            dst, n_entries);
 }
 
 void launch_extract(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
