@@ -83,7 +83,9 @@ typedef struct {
                                       MiB through two pinned buffers, packing each chunk as it lands (the
                                       ASCII is never resident whole); 0 = chunks of 1 GiB when the reads
                                       exceed a quarter of the free device memory, else one copy */
-    uint32_t reserved[2];
+    uint32_t sort_tile;            /* onesweep tile shape (256 threads): 0 = 32 keys/thread (16 for 128-bit
+                                      keys), 2 CTAs/SM (default); 1 = 16 (8), 3 CTAs/SM; 2 = 24 (12), 2/SM */
+    uint32_t reserved[1];
 } turtle_params;
 
 /* Fill *p with the defaults above. */

@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
     _fields_ = [("struct_size", u32), ("filter_bits_per_window", ctypes.c_float), ("pattern_bits", u32),
                 ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("l2_fetch_bytes", u32),
                 ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
-                ("stream_chunk_mib", u32), ("reserved", u32 * 2)]
+                ("stream_chunk_mib", u32), ("sort_tile", u32),
+                ("reserved", u32 * 1)]
 
     @classmethod
     def default(cls, **kw) -> "Params":

@@ -11,13 +11,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
 
-#include "../../include/turtle.h"
+#include "turtle.h"
 #include "common.cuh"
 #include "host.h"
 #include "kernels.h"
@@ -134,12 +135,13 @@ void ctx_begin(turtle_ctx *c, cudaStream_t s) {
     ck(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * C_N, s));
 }
 
-// Free this call's scratch. The pool keeps freed memory for the next call, but never more
-// than a quarter of the device: giant calls (key-range super-partitions) give the rest back.
+// Free this call's scratch. The pool keeps freed memory for the next call (re-growing a
+// pool from the driver is slow); only when the device runs short of free memory (below a
+// quarter) does it give back everything above a quarter of the device.
 void ctx_end(turtle_ctx *c, cudaStream_t s) {
     free_list(c->scratch, s);
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b < total_b / 4) {
         uint64_t reserved = 0;
         if (cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
             reserved > total_b / 4) {
@@ -183,7 +185,7 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
 bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
-           p.filter_bits_per_window <= 1024.f;
+           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 2;
 }
 
 turtle_params resolve(const turtle_params *p) {
@@ -262,9 +264,12 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS);
     tm.stop(TURTLE_STAGE_VALID);
     st.stage_launches[TURTLE_STAGE_VALID] = 1;
+    std::vector<unsigned long long> lib_w;
     if (tag) {
         ck(cudaMemsetAsync(tag->lib_windows, 0, 8 * tag->n_libs, s));
         launch_lib_windows(lc, L, V, tag->lib_starts, tag->n_libs, tag->lib_windows);
+        lib_w.resize(tag->n_libs);
+        ck(cudaMemcpyAsync(lib_w.data(), tag->lib_windows, 8 * tag->n_libs, cudaMemcpyDeviceToHost, s));
     }
     read_back(c, s);
     const uint64_t W = c->h_ctr[C_WINDOWS];
@@ -279,7 +284,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     }
 
     const bool use_filter = min_count >= 2;
-    const bool firsts_mode = use_filter && !prm.recount_windows;
+    const bool firsts_mode = use_filter && (!prm.recount_windows || tag);  // batches recount from first sightings
     const int key_bits = 2 * k + (tag ? tag->tag_bits : 0);
     const int passes = sort_passes_for(key_bits);
     const uint64_t *patterns = use_filter ? ctx_patterns(c, prm, s) : nullptr;
@@ -340,10 +345,26 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
         // pass 1: candidates (and first sightings)
         FilterGeom fg{};
+        uint64_t *lib_filter = nullptr;
         if (use_filter) {
-            const double bits = (double)Wg * prm.filter_bits_per_window;
-            fg.n_sectors = pow2_at_least((uint64_t)(bits / 256.0) + 1);
-            fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+            if (tag) {  // one region per library, each sized for that library's windows
+                std::vector<uint64_t> lf(2 * tag->n_libs);
+                uint64_t at = 0;
+                for (int l = 0; l < tag->n_libs; l++) {
+                    const uint64_t sec = pow2_at_least((uint64_t)(lib_w[l] * prm.filter_bits_per_window / 256.0) + 1);
+                    lf[2 * l] = at;
+                    lf[2 * l + 1] = (uint64_t)(64 - log2_exact(sec));
+                    at += sec;
+                }
+                fg.n_sectors = at;
+                lib_filter = (uint64_t *)ctx_alloc(c, 8 * lf.size(), s);
+                ck(cudaMemcpyAsync(lib_filter, lf.data(), 8 * lf.size(), cudaMemcpyHostToDevice, s));
+                fg.sector_shift = 64;
+            } else {
+                const double bits = (double)Wg * prm.filter_bits_per_window;
+                fg.n_sectors = pow2_at_least((uint64_t)(bits / 256.0) + 1);
+                fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+            }
             fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
             ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
             fg.patterns = patterns;
@@ -357,7 +378,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         tm.start(TURTLE_STAGE_FILTER);
         launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wg, firsts, ctr + C_FIRST, Wg, hist,
                         passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
-                        tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, err);
+                        tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err);
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;
         ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
@@ -381,7 +402,8 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
         tm.start(TURTLE_STAGE_SORT);
         int passes_run = 0;
-        K *sorted = launch_radix_sort<K>(lc, cand, n_cand, key_bits, ss, err, true, skip, &passes_run);
+        K *sorted = launch_radix_sort<K>(lc, cand, n_cand, key_bits, ss, err, true, skip, &passes_run,
+                                         (int)prm.sort_tile);
         tm.stop(TURTLE_STAGE_SORT);
         st.sort_passes = (uint32_t)passes_run;
         st.stage_launches[TURTLE_STAGE_SORT] += n_cand > 1 ? passes_run + 1 : 0;
@@ -424,8 +446,29 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             const uint64_t nu = c->h_ctr[C_UNIQUE];
             st.n_unique += nu;
             // load factor <= 0.4: a line overflows into the next one rarely
-            const uint64_t lines = pow2_at_least((uint64_t)(nu / (0.4 * slots_per_line(KW))) + 1);
-            const uint64_t mask = lines - 1;
+            uint64_t lines = pow2_at_least((uint64_t)(nu / (0.4 * slots_per_line(KW))) + 1);
+            TableGeom tg{lines - 1, nullptr, 0, 0};
+            if (tag) {  // one region per library (distinct candidates per library from the sorted tags)
+                std::vector<uint64_t> us(tag->n_libs + 1, ~0ull), lr(2 * tag->n_libs);
+                uint64_t *d_us = (uint64_t *)ctx_alloc(c, 8 * tag->n_libs, s);
+                ck(cudaMemsetAsync(d_us, 0xff, 8 * tag->n_libs, s));
+                launch_tag_starts<K>(lc, unique, nu, key_bits - tag->tag_bits, d_us);
+                ck(cudaMemcpyAsync(us.data(), d_us, 8 * tag->n_libs, cudaMemcpyDeviceToHost, s));
+                read_back(c, s);
+                us[tag->n_libs] = nu;
+                for (int l = tag->n_libs - 1; l >= 0; l--)
+                    if (us[l] == ~0ull) us[l] = us[l + 1];
+                lines = 0;
+                for (int l = 0; l < tag->n_libs; l++) {
+                    const uint64_t nl = pow2_at_least((uint64_t)((us[l + 1] - us[l]) / (0.4 * slots_per_line(KW))) + 1);
+                    lr[2 * l] = lines;
+                    lr[2 * l + 1] = nl - 1;
+                    lines += nl;
+                }
+                uint64_t *d_lr = (uint64_t *)ctx_alloc(c, 8 * lr.size(), s);
+                ck(cudaMemcpyAsync(d_lr, lr.data(), 8 * lr.size(), cudaMemcpyHostToDevice, s));
+                tg = TableGeom{0, d_lr, key_bits - tag->tag_bits, tag->n_libs};
+            }
             void *table = ctx_alloc(c, 128 * lines, s);
             st.table_bytes = 128 * lines > st.table_bytes ? 128 * lines : st.table_bytes;
             uint64_t member_words = 0;
@@ -437,21 +480,21 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             }
             tm.start(TURTLE_STAGE_TABLE);
             launch_table_clear<K>(lc, table, lines);
-            launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, mask, member, member_words, err);
+            launch_table_insert<K>(lc, unique, run, ctr + C_UNIQUE, nu, table, tg, member, member_words, err);
             tm.stop(TURTLE_STAGE_TABLE);
             st.stage_launches[TURTLE_STAGE_TABLE] += 1;
             tm.start(TURTLE_STAGE_RECOUNT);
             if (firsts_mode)
-                launch_add_firsts<K>(lc, first_keys, n_first, table, mask, member, member_words, W >= 0xfffffffeull,
+                launch_add_firsts<K>(lc, first_keys, n_first, table, tg, member, member_words, W >= 0xfffffffeull,
                                      err);
             else
-                launch_pass2<K>(lc, L, k, P, V, table, mask, W >= 0xfffffffeull, err);
+                launch_pass2<K>(lc, L, k, P, V, table, tg, W >= 0xfffffffeull, err);
             tm.stop(TURTLE_STAGE_RECOUNT);
             st.stage_launches[TURTLE_STAGE_RECOUNT] += (!firsts_mode || n_first) ? 1 : 0;
             K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s, !parted);
             uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nu ? nu : 1), s, !parted);
             tm.start(TURTLE_STAGE_THRESHOLD);
-            launch_threshold<K>(lc, unique, nu, table, mask, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
+            launch_threshold<K>(lc, unique, nu, table, tg, min_count, okeys, ocounts, ctr + C_OUT, ss.lookback,
                                 ss.tile_ctr + 21, err);
             tm.stop(TURTLE_STAGE_THRESHOLD);
             st.stage_launches[TURTLE_STAGE_THRESHOLD] += nu ? 1 : 0;
@@ -568,7 +611,7 @@ int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, con
 
 // memcpy with several host threads (pageable source -> pinned staging buffer).
 void par_memcpy(void *dst, const void *src, size_t n) {
-    const int T = n >= (64u << 20) ? 8 : 1;
+    const int T = n >= ((size_t)32 << 20) ? 8 : n >= ((size_t)4 << 20) ? 4 : 1;
     if (T == 1) {
         memcpy(dst, src, n);
         return;
@@ -579,6 +622,67 @@ void par_memcpy(void *dst, const void *src, size_t n) {
         th.emplace_back([=]() { memcpy((char *)dst + a, (const char *)src + a, b - a); });
     }
     for (auto &x : th) x.join();
+}
+
+// The context's two pinned staging buffers, at least `bytes` each.
+void ensure_pinned(turtle_ctx *c, size_t bytes) {
+    if (c->pinned_bytes >= bytes) return;
+    for (auto &pb : c->pinned)
+        if (pb) {
+            cudaFreeHost(pb);
+            pb = nullptr;
+        }
+    c->pinned_bytes = 0;
+    for (auto &pb : c->pinned) ck(cudaMallocHost(&pb, bytes));
+    c->pinned_bytes = bytes;
+}
+
+constexpr size_t STAGE_CHUNK = (size_t)64 << 20;
+
+// Device -> pageable host through the pinned buffers: the DMA of chunk i overlaps the
+// multi-threaded host copy of chunk i-1. Synchronises s.
+void copy_to_host(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (!bytes) return;
+    if (bytes < ((size_t)1 << 20)) {  // small: one plain copy
+        ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        return;
+    }
+    ensure_pinned(c, STAGE_CHUNK);
+    const size_t n = (bytes + STAGE_CHUNK - 1) / STAGE_CHUNK;
+    for (size_t i = 0; i <= n; i++) {
+        if (i < n) {
+            const size_t len = std::min(STAGE_CHUNK, bytes - i * STAGE_CHUNK);
+            ck(cudaMemcpyAsync(c->pinned[i & 1], (const char *)src + i * STAGE_CHUNK, len, cudaMemcpyDeviceToHost, s));
+            ck(cudaEventRecord(c->ev_h2d[i & 1], s));
+        }
+        if (i > 0) {
+            const size_t j = i - 1, len = std::min(STAGE_CHUNK, bytes - j * STAGE_CHUNK);
+            ck(cudaEventSynchronize(c->ev_h2d[j & 1]));
+            par_memcpy((char *)dst + j * STAGE_CHUNK, c->pinned[j & 1], len);
+        }
+    }
+}
+
+// Pageable host -> device through the pinned buffers (host copy of chunk i+1 overlaps the DMA of chunk i).
+void copy_to_device(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (!bytes) return;
+    if (bytes < ((size_t)1 << 20)) {
+        ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return;
+    }
+    ensure_pinned(c, STAGE_CHUNK);
+    ck(cudaStreamSynchronize(s));  // both pinned buffers are free
+    const size_t n = (bytes + STAGE_CHUNK - 1) / STAGE_CHUNK;
+    for (size_t i = 0; i < n; i++) {
+        const int b = (int)(i & 1);
+        const size_t len = std::min(STAGE_CHUNK, bytes - i * STAGE_CHUNK);
+        if (i >= 2) ck(cudaEventSynchronize(c->ev_h2d[b]));  // its previous copy has left the buffer
+        par_memcpy(c->pinned[b], (const char *)src + i * STAGE_CHUNK, len);
+        ck(cudaMemcpyAsync((char *)dst + i * STAGE_CHUNK, c->pinned[b], len, cudaMemcpyHostToDevice, s));
+        ck(cudaEventRecord(c->ev_h2d[b], s));
+    }
+    ck(cudaStreamSynchronize(s));
 }
 
 // Stream host reads to the device in chunks through two pinned buffers: while chunk i is
@@ -592,16 +696,7 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
     pp.S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
     ck(cudaMemsetAsync(pp.S, 0, 8 * L.b_words, s));
     chunk = (chunk + 63) & ~(size_t)63;  // chunk starts fall on 64-position boundaries (whole bitmap words)
-    if (c->pinned_bytes < chunk) {
-        for (auto &pb : c->pinned)
-            if (pb) {
-                cudaFreeHost(pb);
-                pb = nullptr;
-            }
-        c->pinned_bytes = 0;
-        for (auto &pb : c->pinned) ck(cudaMallocHost(&pb, chunk));
-        c->pinned_bytes = chunk;
-    }
+    ensure_pinned(c, chunk);
     uint8_t *stage[2];
     for (auto &st : stage) st = (uint8_t *)ctx_alloc(c, chunk, s);
     for (int i = 0; i < 2; i++) ck(cudaEventRecord(c->ev_packed[i], s));  // both staging buffers start free
@@ -679,8 +774,8 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         for (int l = 0; l < n_libs; l++) {  // one copy per library straight into place
             const turtle_job &j = jobs[idx[l]];
             const uint64_t nb = lib_starts[l + 1] - lib_starts[l];
-            if (nb) ck(cudaMemcpyAsync(d_bases + lib_starts[l], j.bases + j.offsets[0], nb, cudaMemcpyHostToDevice, s));
-            ck(cudaMemcpyAsync(d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), cudaMemcpyHostToDevice, s));
+            copy_to_device(c, d_bases + lib_starts[l], j.bases + j.offsets[0], nb, s);
+            copy_to_device(c, d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), s);
         }
         ck(cudaMemcpyAsync(d_tab, lib_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
         ck(cudaMemcpyAsync(d_tab + n_libs + 1, entry_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
@@ -713,8 +808,8 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
             r.counts = (uint32_t *)malloc(4 * (r.n ? r.n : 1));
             if (!r.keys || !r.counts) throw Fail{TURTLE_E_NOMEM};
             if (r.n) {
-                ck(cudaMemcpyAsync(r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, cudaMemcpyDeviceToHost, s));
-                ck(cudaMemcpyAsync(r.counts, o.counts + starts[l], 4 * r.n, cudaMemcpyDeviceToHost, s));
+                copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, s);
+                copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, s);
             }
         }
         ck(cudaStreamSynchronize(s));
@@ -903,8 +998,9 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     const uint64_t n_bases = reads->offsets[reads->n_reads];
     const turtle_params prm = resolve(params);
     size_t chunk = (size_t)prm.stream_chunk_mib << 20;
-    if (!chunk) {  // stream when the ASCII would take more than a quarter of the free device memory
+    if (!chunk && n_bases >= ((uint64_t)64 << 20)) {  // large inputs stream through the pinned buffers
         size_t free_b = 0, total_b = 0;
+        chunk = (size_t)256 << 20;
         if (cudaSetDevice(c->device) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
             n_bases > free_b / 4)
             chunk = (size_t)1 << 30;
@@ -918,7 +1014,7 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         if (!streamed) ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
         ck(cudaMallocFromPoolAsync((void **)&d_off, 8 * (reads->n_reads + 1), c->pool, s));
         if (n_bases && !streamed) ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
-        ck(cudaMemcpyAsync(d_off, reads->offsets, 8 * (reads->n_reads + 1), cudaMemcpyHostToDevice, s));
+        copy_to_device(c, d_off, reads->offsets, 8 * (reads->n_reads + 1), s);
     } catch (Fail f) {
         if (d_bases) cudaFreeAsync(d_bases, s);
         if (d_off) cudaFreeAsync(d_off, s);
@@ -937,12 +1033,13 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         turtle_result_free(out);
         return TURTLE_E_NOMEM;
     }
-    if (cudaMemcpyAsync(out->keys, o.keys, 8 * kw * o.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(out->counts, o.counts, 4 * o.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
+    try {
+        copy_to_host(c, out->keys, o.keys, 8 * kw * o.n, s);
+        copy_to_host(c, out->counts, o.counts, 4 * o.n, s);
+    } catch (Fail f) {
         cudaGetLastError();
         turtle_result_free(out);
-        return TURTLE_E_CUDA;
+        return f.code;
     }
     out->k = k;
     out->n = o.n;

@@ -142,6 +142,12 @@ __device__ __forceinline__ Key128 add_tag(Key128 key, uint32_t lib, int shift) {
     return key;
 }
 
+template <class K>
+__device__ __forceinline__ uint32_t tag_of(const K &key, int shift) {
+    if constexpr (sizeof(K) == 8) return (uint32_t)(key >> shift);  // shift < 64 whenever a tag is present
+    else return (uint32_t)(key.hi >> (shift - 64));                // tags of 128-bit runs sit in hi (2k >= 66)
+}
+
 // ---------------------------------------------------------------- key loads/stores
 __device__ __forceinline__ uint64_t load_stream(const uint64_t *p) { return __ldcs(p); }  // read once
 __device__ __forceinline__ Key128 load_stream(const Key128 *p) {

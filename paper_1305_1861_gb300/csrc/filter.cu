@@ -90,15 +90,19 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     K *firsts, unsigned long long *first_count, uint64_t first_cap,
                                                     uint64_t *hist, int hist_passes, int part_bits, uint32_t part_lo,
                                                     uint32_t part_hi, const uint64_t *__restrict__ lib_starts,
-                                                    int n_libs, uint32_t *err) {
+                                                    int n_libs, const uint64_t *__restrict__ lib_filter,
+                                                    uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
     K *s_buf = reinterpret_cast<K *>(smem);
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
     uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + 256 * hist_passes);
     __shared__ uint64_t s_lib[65];
+    __shared__ uint64_t s_lf[128];  // per-library filter region: first sector, shift of the hash
     if (n_libs)
         for (int i = threadIdx.x; i <= n_libs; i += P1_BLOCK) s_lib[i] = lib_starts[i];
+    if (n_libs && lib_filter)
+        for (int i = threadIdx.x; i < 2 * n_libs; i += P1_BLOCK) s_lf[i] = lib_filter[i];
     if (USE_FILTER)
         for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
     for (int i = threadIdx.x; i < 256 * hist_passes; i += P1_BLOCK) s_hist[i] = 0;
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
         K key[P1_ILP];
         uint64_t *addr[P1_ILP];
         uint64_t mask[P1_ILP];
+        uint32_t libi[P1_ILP];
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
             const int r = lane + WARP * i;
@@ -132,6 +137,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                         else hi = mid;
                     }
                     key[i] = add_tag(key[i], (uint32_t)lo, 2 * k);
+                    libi[i] = (uint32_t)lo;
                 }
                 if (part_bits) {  // keys of other key ranges wait for their own super-partition
                     const uint32_t pt = key_part(key[i], k, part_bits);
@@ -141,7 +147,13 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             if (ok[i]) {
                 if (USE_FILTER) {
                     const uint64_t h = key_hash(key[i]);
-                    const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
+                    uint64_t sector;
+                    if (n_libs && lib_filter) {  // batched: each library has its own region, hot in L2 while its
+                        const uint64_t sh = s_lf[2 * libi[i] + 1];  // windows are being processed
+                        sector = s_lf[2 * libi[i]] + (sh < 64 ? (h >> sh) : 0);
+                    } else {
+                        sector = sector_shift < 64 ? (h >> sector_shift) : 0;
+                    }
                     addr[i] = filter + sector * 4 + ((h >> 16) & 3);
                     mask[i] = s_pat[h & pat_mask];
                 }
@@ -243,7 +255,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
-                  uint32_t *err) {
+                  const uint64_t *lib_filter, uint32_t *err) {
     const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     const bool emit_firsts = use_filter && firsts != nullptr;
     if (!hist) hist_passes = 0;
@@ -259,7 +271,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     int grid = (int)(need < cap ? (need ? need : 1) : cap);
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
                                              cand, cand_count, cand_cap, firsts, first_count, first_cap, hist,
-                                             hist_passes, part_bits, part_lo, part_hi, lib_starts, n_libs, err);
+                                             hist_passes, part_bits, part_lo, part_hi, lib_starts, n_libs,
+                                             lib_filter, err);
 }
 
 template <class K>
@@ -273,11 +286,11 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
                                      unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, const uint64_t *, int,
-                                     uint32_t *);
+                                     const uint64_t *, uint32_t *);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
                                    unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
-                                   const uint64_t *, int, uint32_t *);
+                                   const uint64_t *, int, const uint64_t *, uint32_t *);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

@@ -2,7 +2,7 @@
 #pragma once
 #include <cstdint>
 
-#include "../../include/turtle.h"
+#include "turtle.h"
 
 // Host-memory form of turtle_count on a given context (copies or streams the reads in).
 int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,

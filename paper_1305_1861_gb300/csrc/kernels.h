@@ -59,13 +59,14 @@ struct FilterGeom {
 // hist (non-null): += the 256-bin digit counts of the candidates for radix passes 0..hist_passes-1.
 // part_bits > 0: only windows whose key lies in key-range parts [part_lo, part_hi) of 2^part_bits take part.
 // n_libs > 0 (batched form, <= 64): positions [lib_starts[l], lib_starts[l+1]) belong to library l, whose
-// index is added to every key above its 2k bits.
+// index is added to every key above its 2k bits; lib_filter (optional, 2 * n_libs entries: first
+// sector, hash shift) gives each library its own filter region.
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
-                  uint32_t *err);
+                  const uint64_t *lib_filter, uint32_t *err);
 // Valid windows of each library of a batch (counts: n_libs zeroed counters).
 void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,
                         int n_libs, unsigned long long *counts);
@@ -77,6 +78,9 @@ void launch_batch_offsets(const LaunchCfg &c, const uint64_t *src, const uint64_
 // UINT64_MAX; libraries without entries keep it), and the tag bits (at bit `shift` and up) are cleared.
 template <class K>
 void launch_split_tags(const LaunchCfg &c, K *keys, uint64_t n, int shift, uint64_t *starts);
+// Only the library starts (tags kept).
+template <class K>
+void launch_tag_starts(const LaunchCfg &c, const K *keys, uint64_t n, int shift, uint64_t *starts);
 // Valid windows per key-range part (counts: 2^part_bits zeroed counters).
 template <class K>
 void launch_part_count(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
@@ -100,7 +104,7 @@ uint64_t sort_lookback_words(uint64_t n, int key_words);
 // bit p of skip_mask skips digit pass p (only valid when every key has the same digit p).
 template <class K>
 K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err,
-                     bool hist_ready = false, uint32_t skip_mask = 0, int *passes_run = nullptr);
+                     bool hist_ready = false, uint32_t skip_mask = 0, int *passes_run = nullptr, int variant = 0);
 // unique/starts from sorted keys; *n_unique (device) receives the distinct count.
 template <class K>
 void launch_rle(const LaunchCfg &c, const K *sorted, uint64_t n, K *unique, uint64_t *starts,
@@ -109,8 +113,15 @@ void launch_rle(const LaunchCfg &c, const K *sorted, uint64_t n, K *unique, uint
 void launch_run_counts(const LaunchCfg &c, const uint64_t *starts, const unsigned long long *n_unique, uint64_t n,
                        uint64_t cap, uint32_t *counts, uint32_t *err);
 
-// a5: recount table: lines of 128 bytes (8 slots of 16 B for 64-bit keys, 4 of 32 B for 128-bit);
-// `mask` arguments below are line masks (number of lines - 1, a power of two minus one).
+// a5: recount table: lines of 128 bytes (8 slots of 16 B for 64-bit keys, 4 of 32 B for 128-bit).
+// One region (lines [0, mask]) or, for a batch, one region per library: lib_regions[2l] = first line,
+// lib_regions[2l+1] = line mask, the library taken from the key's tag at bit tag_shift.
+struct TableGeom {
+    uint64_t mask;
+    const uint64_t *lib_regions;  // device, 2 * n_libs (batched form) or nullptr
+    int tag_shift;
+    int n_libs;
+};
 template <class K> struct Slot;
 size_t slot_bytes(int key_words);
 int slots_per_line(int key_words);
@@ -120,18 +131,18 @@ void launch_table_clear(const LaunchCfg &c, void *table, uint64_t lines);
 // member_words a power of two, zeroed) receives the membership bitmap of the inserted keys.
 template <class K>
 void launch_table_insert(const LaunchCfg &c, const K *unique, const uint32_t *counts,
-                         const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask,
+                         const unsigned long long *n_unique, uint64_t cap, void *table, const TableGeom &tg,
                          uint64_t *member, uint64_t member_words, uint32_t *err);
 // a5 (first-sighting form): +1 on the slot of every key of firsts[0 .. n) that is in the table.
 template <class K>
-void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask,
+void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, const TableGeom &tg,
                        const uint64_t *member, uint64_t member_words, bool check_overflow, uint32_t *err);
 template <class K>
 void launch_pass2(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
-                  void *table, uint64_t mask, bool check_overflow, uint32_t *err);
+                  void *table, const TableGeom &tg, bool check_overflow, uint32_t *err);
 // a6: keep count >= min_count in key order.
 template <class K>
-void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, const void *table, uint64_t mask,
+void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, const void *table, const TableGeom &tg,
                       uint32_t min_count, K *out_keys, uint32_t *out_counts, unsigned long long *n_out,
                       uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err);
 

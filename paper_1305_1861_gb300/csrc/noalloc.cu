@@ -17,7 +17,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/turtle.h"
+#include "turtle.h"
 #include "common.cuh"
 #include "kernels.h"
 

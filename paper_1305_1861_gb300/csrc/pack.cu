@@ -179,12 +179,6 @@ __global__ void k_batch_offsets(const uint64_t *__restrict__ src, const uint64_t
 // (starts[] holds UINT64_MAX on entry). Second pass (a separate launch, so no thread reads a
 // neighbour whose tag is already cleared): clear the tag bits in place.
 template <class K>
-__device__ __forceinline__ uint32_t tag_of(const K &key, int shift) {
-    if constexpr (sizeof(K) == 8) return (uint32_t)(key >> shift);  // shift < 64 whenever a tag is present
-    else return (uint32_t)(key.hi >> (shift - 64));                // tags of 128-bit runs sit in hi (2k >= 66)
-}
-
-template <class K>
 __global__ void k_tag_starts(const K *keys, uint64_t n, int shift, uint64_t *starts) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t t = tag_of(keys[i], shift);
@@ -238,6 +232,14 @@ void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t 
     const uint64_t n_words = L.v_words - 2;
     k_lib_windows<<<grid_for(n_words, 256, c.sms, 8), 256, 0, c.stream>>>(V, n_words, lib_starts, n_libs, counts);
 }
+
+template <class K>
+void launch_tag_starts(const LaunchCfg &c, const K *keys, uint64_t n, int shift, uint64_t *starts) {
+    if (!n) return;
+    k_tag_starts<K><<<grid_for(n, 256, c.sms, 8), 256, 0, c.stream>>>(keys, n, shift, starts);
+}
+template void launch_tag_starts<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, int, uint64_t *);
+template void launch_tag_starts<Key128>(const LaunchCfg &, const Key128 *, uint64_t, int, uint64_t *);
 
 template <class K>
 void launch_split_tags(const LaunchCfg &c, K *keys, uint64_t n, int shift, uint64_t *starts) {

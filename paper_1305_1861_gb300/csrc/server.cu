@@ -17,7 +17,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/turtle.h"
+#include "turtle.h"
 #include "host.h"
 
 namespace {

@@ -21,14 +21,24 @@ constexpr int S_WARPS = S_BLOCK / WARP;
 constexpr int BINS = 256;
 constexpr int MAX_PASSES = 16;
 
+// Onesweep tile shapes (keys per thread, CTAs per SM), selected at run time (params.sort_tile).
+// Variant 0 is the default; the others trade tile size against occupancy.
 template <class K> struct SortCfg;
-template <> struct SortCfg<uint64_t> { static constexpr int ITEMS = 16; };  // 4096 keys (32 KB) per tile
-template <> struct SortCfg<Key128> { static constexpr int ITEMS = 8; };     // 2048 keys (32 KB) per tile
+template <> struct SortCfg<uint64_t> {
+    static constexpr int V_ITEMS[3] = {32, 16, 24};  // default: 8192 keys (64 KB) per tile, 2 CTAs/SM
+    static constexpr int V_MINB[3] = {2, 3, 2};
+    static constexpr int MIN_TILE = 256 * 16;
+};
+template <> struct SortCfg<Key128> {
+    static constexpr int V_ITEMS[3] = {16, 8, 12};   // default: 4096 keys (64 KB) per tile
+    static constexpr int V_MINB[3] = {2, 3, 2};
+    static constexpr int MIN_TILE = 256 * 8;
+};
 
 int sort_passes_for(int key_bits) { return (key_bits + 7) / 8; }
 
-uint64_t sort_lookback_words(uint64_t n, int key_words) {
-    const uint64_t tile = (uint64_t)S_BLOCK * (key_words == 1 ? SortCfg<uint64_t>::ITEMS : SortCfg<Key128>::ITEMS);
+uint64_t sort_lookback_words(uint64_t n, int key_words) {  // sized for the smallest tile of any variant
+    const uint64_t tile = key_words == 1 ? SortCfg<uint64_t>::MIN_TILE : SortCfg<Key128>::MIN_TILE;
     return ((n + tile - 1) / tile + 1) * BINS;
 }
 
@@ -65,14 +75,14 @@ __global__ void k_scan_bins(uint64_t *hist) {
     h[threadIdx.x] = s[threadIdx.x];
 }
 
-template <class K>
-__global__ void __launch_bounds__(S_BLOCK, 3) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
-                                                         int shift, const uint64_t *__restrict__ bin_base,
-                                                         uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
-                                                         uint32_t *err) {
-    constexpr int ITEMS = SortCfg<K>::ITEMS;
+template <class K, int ITEMS, int MINB>
+__global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
+                                                            int shift, const uint64_t *__restrict__ bin_base,
+                                                            uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
+                                                            uint32_t *err) {
     constexpr int TILE = S_BLOCK * ITEMS;
-    __shared__ K skeys[TILE];
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    K *skeys = reinterpret_cast<K *>(os_smem);  // TILE keys (dynamic: up to 64 KB)
     __shared__ uint32_t whist[S_WARPS][BINS];
     __shared__ uint32_t s_texcl[BINS];
     __shared__ uint64_t s_glob[BINS];
@@ -88,16 +98,29 @@ __global__ void __launch_bounds__(S_BLOCK, 3) k_onesweep(const K *__restrict__ i
     const uint64_t wstart = start + (uint64_t)warp * ITEMS * WARP;  // warp w owns a contiguous run of the tile
     const uint32_t lt = lanemask_lt();
 
+    // A full tile (every tile but the last) needs no bounds checks.
+    const bool full = start + TILE <= n;
+    const uint32_t n_in_warp = full ? (uint32_t)(ITEMS * WARP)
+                                    : (uint32_t)(wstart >= n ? 0 : (n - wstart < (uint64_t)ITEMS * WARP ? n - wstart
+                                                                                                       : ITEMS * WARP));
     K key[ITEMS];
+    uint32_t dig[(ITEMS + 3) / 4];  // digits packed four to a register, computed once
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        const uint64_t idx = wstart + i * WARP + lane;
-        if (idx < n) key[i] = in[idx];
+        const uint32_t r = (uint32_t)(i * WARP + lane);
+        if (full || r < n_in_warp) key[i] = in[wstart + r];
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        const uint32_t r = (uint32_t)(i * WARP + lane);
+        const uint32_t d = (full || r < n_in_warp) ? KeyT<K>::digit(key[i], shift) : 0u;
+        if ((i & 3) == 0) dig[i >> 2] = d;
+        else dig[i >> 2] |= d << (8 * (i & 3));
     }
     // 1. early counts: per-warp digit counts (order-free shared atomics)
 #pragma unroll
     for (int i = 0; i < ITEMS; i++)
-        if (wstart + i * WARP + lane < n) atomicAdd(&whist[warp][KeyT<K>::digit(key[i], shift)], 1u);
+        if (full || (uint32_t)(i * WARP + lane) < n_in_warp) atomicAdd(&whist[warp][(dig[i >> 2] >> (8 * (i & 3))) & 0xffu], 1u);
     __syncthreads();
     // 2. thread tid owns digit tid: tile count, publish it, tile-local start, per-warp starts
     uint32_t tcount = 0;
@@ -121,8 +144,8 @@ __global__ void __launch_bounds__(S_BLOCK, 3) k_onesweep(const K *__restrict__ i
     //    a warp's shared-memory atomics complete in issue order, so rows cannot overtake each other.
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        const bool valid = wstart + i * WARP + lane < n;
-        const uint32_t d = valid ? KeyT<K>::digit(key[i], shift) : (BINS + lane);
+        const bool valid = full || (uint32_t)(i * WARP + lane) < n_in_warp;
+        const uint32_t d = valid ? ((dig[i >> 2] >> (8 * (i & 3))) & 0xffu) : (BINS + lane);
         const uint32_t peers = __match_any_sync(FULL, d);
         const int leader = 31 - __clz(peers);
         uint32_t pos = 0;
@@ -134,20 +157,40 @@ __global__ void __launch_bounds__(S_BLOCK, 3) k_onesweep(const K *__restrict__ i
     const uint64_t excl = lookback_prefix(lookback + tid, BINS, tile, tcount, epoch, err);
     s_glob[tid] = bin_base[tid] + excl - texcl;
     __syncthreads();
-    const uint32_t tile_n = (uint32_t)(n - start < (uint64_t)TILE ? n - start : TILE);
-    for (uint32_t p = tid; p < tile_n; p += S_BLOCK) {
-        const K kk = skeys[p];
-        out[s_glob[KeyT<K>::digit(kk, shift)] + p] = kk;
+    if (full) {
+#pragma unroll 4
+        for (uint32_t p = tid; p < (uint32_t)TILE; p += S_BLOCK) {
+            const K kk = skeys[p];
+            out[s_glob[KeyT<K>::digit(kk, shift)] + p] = kk;
+        }
+    } else {
+        const uint32_t tile_n = (uint32_t)(n - start);
+        for (uint32_t p = tid; p < tile_n; p += S_BLOCK) {
+            const K kk = skeys[p];
+            out[s_glob[KeyT<K>::digit(kk, shift)] + p] = kk;
+        }
     }
+}
+
+template <class K, int V>
+static void onesweep_pass(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
+                          uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+    constexpr int ITEMS = SortCfg<K>::V_ITEMS[V], MINB = SortCfg<K>::V_MINB[V];
+    const uint64_t tiles = (n + S_BLOCK * ITEMS - 1) / (S_BLOCK * ITEMS);
+    const size_t smem = sizeof(K) * S_BLOCK * ITEMS;
+    cudaFuncSetAttribute(k_onesweep<K, ITEMS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_onesweep<K, ITEMS, MINB><<<(int)tiles, S_BLOCK, smem, c.stream>>>(src, dst, n, shift, bin_base, lookback,
+                                                                       tile_ctr, epoch, err);
 }
 
 template <class K>
 K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, const SortScratch &s, uint32_t *err,
-                     bool hist_ready, uint32_t skip_mask, int *passes_run) {
+                     bool hist_ready, uint32_t skip_mask, int *passes_run, int variant) {
     const int passes = sort_passes_for(key_bits);
     if (passes_run) *passes_run = 0;
     if (n <= 1 || passes == 0) return keys;
-    constexpr int TILE = S_BLOCK * SortCfg<K>::ITEMS;
+    if (variant < 0 || variant > 2) variant = 0;
+    const uint64_t TILE = (uint64_t)S_BLOCK * SortCfg<K>::V_ITEMS[variant];
     const uint64_t tiles = (n + TILE - 1) / TILE;
     cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
     cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
@@ -161,8 +204,8 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
     K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
     for (int p = 0; p < passes; p++) {
         if ((skip_mask >> p) & 1u) continue;  // every key has the same digit here: the pass would be a copy
-        k_onesweep<K><<<(int)tiles, S_BLOCK, 0, c.stream>>>(src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS,
-                                                           s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err);
+        auto pass = variant == 0 ? onesweep_pass<K, 0> : (variant == 1 ? onesweep_pass<K, 1> : onesweep_pass<K, 2>);
+        pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err);
         if (passes_run) (*passes_run)++;
         K *t = src;
         src = dst;
@@ -273,9 +316,9 @@ void launch_run_counts(const LaunchCfg &c, const uint64_t *starts, const unsigne
 }
 
 template uint64_t *launch_radix_sort<uint64_t>(const LaunchCfg &, uint64_t *, uint64_t, int, const SortScratch &,
-                                               uint32_t *, bool, uint32_t, int *);
+                                               uint32_t *, bool, uint32_t, int *, int);
 template Key128 *launch_radix_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, const SortScratch &, uint32_t *,
-                                           bool, uint32_t, int *);
+                                           bool, uint32_t, int *, int);
 template void launch_rle<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, uint64_t *, uint64_t *,
                                    unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
 template void launch_rle<Key128>(const LaunchCfg &, const Key128 *, uint64_t, Key128 *, uint64_t *,

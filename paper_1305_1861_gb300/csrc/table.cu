@@ -55,11 +55,22 @@ template <class K> struct TableLine {
     static constexpr int S = 128 / (int)sizeof(Slot<K>);  // slots per 128-byte line (8 or 4)
 };
 template <class K>
-__device__ __forceinline__ uint64_t probe_slot(uint64_t h, uint64_t j, uint64_t line_mask) {
+__device__ __forceinline__ uint64_t probe_slot(uint64_t h, uint64_t j, uint64_t line_mask, uint64_t line_base = 0) {
     constexpr int S = TableLine<K>::S;
     const uint64_t g = h ^ (h >> 29);
-    const uint64_t line = ((g >> 3) + j / S) & line_mask;
+    const uint64_t line = line_base + (((g >> 3) + j / S) & line_mask);
     return line * S + (uint64_t)((g + j) & (S - 1));
+}
+
+// The key's region: the whole table, or its library's lines (batched form).
+struct Region {
+    uint64_t base, mask;
+};
+template <class K>
+__device__ __forceinline__ Region region_of(const K &key, const TableGeom &tg) {
+    if (!tg.n_libs) return Region{0, tg.mask};
+    const uint32_t l = tag_of(key, tg.tag_shift);
+    return Region{__ldg(tg.lib_regions + 2 * l), __ldg(tg.lib_regions + 2 * l + 1)};
 }
 
 // Membership bitmap of the table's keys: two bits of one 64-bit word per key. It is
@@ -69,17 +80,18 @@ __device__ __forceinline__ uint64_t member_bits(uint64_t h) { return (1ull << (h
 
 template <class K>
 __global__ void k_table_insert(const K *__restrict__ unique, const uint32_t *__restrict__ counts,
-                               const unsigned long long *n_unique, Slot<K> *table, uint64_t mask,
+                               const unsigned long long *n_unique, Slot<K> *table, TableGeom tg,
                                uint64_t *member, uint64_t member_mask, uint32_t *err) {
     const uint64_t nu = *n_unique;
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nu; j += (uint64_t)gridDim.x * blockDim.x) {
         const K key = unique[j];
         const uint32_t c0 = counts ? counts[j] : 0u;
         const uint64_t h = key_hash(key);
-        const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
+        const Region rg = region_of(key, tg);
+        const uint64_t n_slots = (rg.mask + 1) * TableLine<K>::S;
         bool done = false;
         for (uint64_t probe = 0; probe < n_slots; probe++) {
-            const uint64_t s = probe_slot<K>(h, probe, mask);
+            const uint64_t s = probe_slot<K>(h, probe, rg.mask, rg.base);
             if (atomicCAS(&table[s].count, EMPTY_COUNT, c0) == EMPTY_COUNT) {  // distinct keys: claim any free slot
                 slot_put(&table[s], key);
                 done = true;
@@ -99,8 +111,9 @@ constexpr int P2_TILE = WARP * P2_ILP;
 
 template <class K>
 __global__ void __launch_bounds__(P2_BLOCK) k_pass2(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
-                                                    uint64_t n_pos, int k, Slot<K> *table, uint64_t mask,
+                                                    uint64_t n_pos, int k, Slot<K> *table, TableGeom tg,
                                                     int check_overflow, uint32_t *err) {
+    const uint64_t mask = tg.mask;  // the windows form runs on one region
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t tiles = (n_pos + P2_TILE - 1) / P2_TILE;
     for (uint64_t t = (uint64_t)blockIdx.x * P2_WARPS + warp; t < tiles; t += (uint64_t)gridDim.x * P2_WARPS) {
@@ -152,11 +165,10 @@ __global__ void __launch_bounds__(P2_BLOCK) k_pass2(const uint64_t *__restrict__
 constexpr int F_ILP = 4;
 
 template <class K>
-__global__ void __launch_bounds__(256, 6) k_add_firsts(const K *__restrict__ firsts, uint64_t n, Slot<K> *table,
-                                                    uint64_t mask, const uint64_t *__restrict__ member,
+__global__ void __launch_bounds__(256, 4) k_add_firsts(const K *__restrict__ firsts, uint64_t n, Slot<K> *table,
+                                                    TableGeom tg, const uint64_t *__restrict__ member,
                                                     uint64_t member_mask, int check_overflow, uint32_t *err) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
     for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; base < n; base += stride * F_ILP) {
         K key[F_ILP];
         uint64_t h[F_ILP], mw[F_ILP];
@@ -176,15 +188,20 @@ __global__ void __launch_bounds__(256, 6) k_add_firsts(const K *__restrict__ fir
         for (int i = 0; i < F_ILP; i++) {  // first probes of every possible member, issued together
             const uint64_t mb = member_bits(h[i]);
             ok[i] = ok[i] && (!member || (mw[i] & mb) == mb);  // else certainly not a candidate key
-            if (ok[i]) sl[i] = slot_load(table + probe_slot<K>(h[i], 0, mask));
+            if (ok[i]) {
+                const Region rg = region_of(key[i], tg);
+                sl[i] = slot_load(table + probe_slot<K>(h[i], 0, rg.mask, rg.base));
+            }
         }
 #pragma unroll
         for (int i = 0; i < F_ILP; i++) {
             if (!ok[i]) continue;
+            const Region rg = region_of(key[i], tg);  // recomputed: cheaper than holding it in registers
+            const uint64_t n_slots = (rg.mask + 1) * TableLine<K>::S;
             for (uint64_t probe = 0; probe < n_slots;) {
                 if (sl[i].count == EMPTY_COUNT) break;
                 if (slot_has(sl[i], key[i])) {
-                    unsigned int *cnt = &table[probe_slot<K>(h[i], probe, mask)].count;
+                    unsigned int *cnt = &table[probe_slot<K>(h[i], probe, rg.mask, rg.base)].count;
                     if (check_overflow) {
                         if (atomicAdd(cnt, 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
                     } else {
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(256, 6) k_add_firsts(const K *__restrict__ fir
                     }
                     break;
                 }
-                if (++probe < n_slots) sl[i] = slot_load(table + probe_slot<K>(h[i], probe, mask));
+                if (++probe < n_slots) sl[i] = slot_load(table + probe_slot<K>(h[i], probe, rg.mask, rg.base));
             }
         }
     }
@@ -202,11 +219,12 @@ constexpr int T_ITEMS = 8;
 constexpr int T_TILE = P2_BLOCK * T_ITEMS;
 
 template <class K>
-__device__ __forceinline__ uint32_t table_count(const Slot<K> *table, uint64_t mask, K key) {
+__device__ __forceinline__ uint32_t table_count(const Slot<K> *table, const TableGeom &tg, K key) {
     const uint64_t h = key_hash(key);
-    const uint64_t n_slots = (mask + 1) * TableLine<K>::S;
+    const Region rg = region_of(key, tg);
+    const uint64_t n_slots = (rg.mask + 1) * TableLine<K>::S;
     for (uint64_t probe = 0; probe < n_slots; probe++) {
-        const Slot<K> sl = slot_load(table + probe_slot<K>(h, probe, mask));
+        const Slot<K> sl = slot_load(table + probe_slot<K>(h, probe, rg.mask, rg.base));
         if (sl.count == EMPTY_COUNT) return EMPTY_COUNT;
         if (slot_has(sl, key)) return sl.count;
     }
@@ -215,7 +233,7 @@ __device__ __forceinline__ uint32_t table_count(const Slot<K> *table, uint64_t m
 
 template <class K>
 __global__ void __launch_bounds__(P2_BLOCK) k_threshold(const K *__restrict__ unique, uint64_t n_unique,
-                                                        const Slot<K> *table, uint64_t mask, uint32_t min_count,
+                                                        const Slot<K> *table, TableGeom tg, uint32_t min_count,
                                                         K *__restrict__ out_keys, uint32_t *__restrict__ out_counts,
                                                         unsigned long long *n_out, uint64_t *lookback,
                                                         uint32_t *tile_ctr, uint32_t *err) {
@@ -234,7 +252,7 @@ __global__ void __launch_bounds__(P2_BLOCK) k_threshold(const K *__restrict__ un
         const uint64_t idx = start + (uint64_t)j * P2_BLOCK + tid;  // striped: coalesced key reads
         if (idx < n_unique) {
             key[j] = unique[idx];
-            cnt[j] = table_count(table, mask, key[j]);
+            cnt[j] = table_count(table, tg, key[j]);
             if (cnt[j] == EMPTY_COUNT) atomicOr(err, ERR_NOT_FOUND);
             else if (cnt[j] >= min_count) {
                 keep |= 1u << j;
@@ -282,17 +300,17 @@ void launch_table_clear(const LaunchCfg &c, void *table, uint64_t lines) {
 
 template <class K>
 void launch_table_insert(const LaunchCfg &c, const K *unique, const uint32_t *counts,
-                         const unsigned long long *n_unique, uint64_t cap, void *table, uint64_t mask,
+                         const unsigned long long *n_unique, uint64_t cap, void *table, const TableGeom &tg,
                          uint64_t *member, uint64_t member_words, uint32_t *err) {
     uint64_t need = (cap + 255) / 256;
     const uint64_t lim = (uint64_t)c.sms * 8;
     k_table_insert<K><<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(
-        unique, counts, n_unique, reinterpret_cast<Slot<K> *>(table), mask, member,
+        unique, counts, n_unique, reinterpret_cast<Slot<K> *>(table), tg, member,
         member_words ? member_words - 1 : 0, err);
 }
 
 template <class K>
-void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, uint64_t mask,
+void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *table, const TableGeom &tg,
                        const uint64_t *member, uint64_t member_words, bool check_overflow, uint32_t *err) {
     if (n == 0) return;
     int per_sm = 0;
@@ -301,13 +319,13 @@ void launch_add_firsts(const LaunchCfg &c, const K *firsts, uint64_t n, void *ta
     uint64_t need = (n + 256 * F_ILP - 1) / (256 * F_ILP);
     const uint64_t lim = (uint64_t)c.sms * per_sm;
     k_add_firsts<K><<<(int)(need < lim ? (need ? need : 1) : lim), 256, 0, c.stream>>>(
-        firsts, n, reinterpret_cast<Slot<K> *>(table), mask, member, member_words ? member_words - 1 : 0,
+        firsts, n, reinterpret_cast<Slot<K> *>(table), tg, member, member_words ? member_words - 1 : 0,
         check_overflow ? 1 : 0, err);
 }
 
 template <class K>
 void launch_pass2(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V, void *table,
-                  uint64_t mask, bool check_overflow, uint32_t *err) {
+                  const TableGeom &tg, bool check_overflow, uint32_t *err) {
     const uint64_t tiles = (L.n_bases + P2_TILE - 1) / P2_TILE;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass2<K>, P2_BLOCK, 0);
@@ -315,11 +333,11 @@ void launch_pass2(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     uint64_t need = (tiles + P2_WARPS - 1) / P2_WARPS;
     const uint64_t cap = (uint64_t)c.sms * per_sm;
     k_pass2<K><<<(int)(need < cap ? (need ? need : 1) : cap), P2_BLOCK, 0, c.stream>>>(
-        P, V, L.n_bases, k, reinterpret_cast<Slot<K> *>(table), mask, check_overflow ? 1 : 0, err);
+        P, V, L.n_bases, k, reinterpret_cast<Slot<K> *>(table), tg, check_overflow ? 1 : 0, err);
 }
 
 template <class K>
-void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, const void *table, uint64_t mask,
+void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, const void *table, const TableGeom &tg,
                       uint32_t min_count, K *out_keys, uint32_t *out_counts, unsigned long long *n_out,
                       uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err) {
     cudaMemsetAsync(n_out, 0, sizeof(unsigned long long), c.stream);
@@ -328,7 +346,7 @@ void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, co
     cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t), c.stream);
     cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * tiles, c.stream);
     k_threshold<K><<<(int)tiles, P2_BLOCK, 0, c.stream>>>(unique, n_unique, reinterpret_cast<const Slot<K> *>(table),
-                                                          mask, min_count, out_keys, out_counts, n_out, lookback,
+                                                          tg, min_count, out_keys, out_counts, n_out, lookback,
                                                           tile_ctr, err);
 }
 
@@ -338,13 +356,14 @@ int slots_per_line(int key_words) { return key_words == 1 ? TableLine<uint64_t>:
 #define INST(K)                                                                                                  \
     template void launch_table_clear<K>(const LaunchCfg &, void *, uint64_t);                                    \
     template void launch_table_insert<K>(const LaunchCfg &, const K *, const uint32_t *,                         \
-                                         const unsigned long long *, uint64_t, void *, uint64_t, uint64_t *,     \
-                                         uint64_t, uint32_t *);                                                  \
-    template void launch_add_firsts<K>(const LaunchCfg &, const K *, uint64_t, void *, uint64_t,                 \
+                                         const unsigned long long *, uint64_t, void *, const TableGeom &,        \
+                                         uint64_t *, uint64_t, uint32_t *);                                      \
+    template void launch_add_firsts<K>(const LaunchCfg &, const K *, uint64_t, void *, const TableGeom &,        \
                                        const uint64_t *, uint64_t, bool, uint32_t *);                            \
     template void launch_pass2<K>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *, \
-                                  void *, uint64_t, bool, uint32_t *);                                           \
-    template void launch_threshold<K>(const LaunchCfg &, const K *, uint64_t, const void *, uint64_t, uint32_t,  \
+                                  void *, const TableGeom &, bool, uint32_t *);                                  \
+    template void launch_threshold<K>(const LaunchCfg &, const K *, uint64_t, const void *, const TableGeom &,   \
+                                      uint32_t,                                                                  \
                                       K *, uint32_t *, unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
 INST(uint64_t)
 INST(Key128)
