@@ -81,11 +81,19 @@ typedef struct {
                                       working set exceeds it are processed in consecutive key ranges. */
     uint32_t stream_chunk_mib;     /* host-memory calls: copy the reads to the device in chunks of this many
                                       MiB through two pinned buffers, packing each chunk as it lands (the
-                                      ASCII is never resident whole); 0 = chunks of 1 GiB when the reads
-                                      exceed a quarter of the free device memory, else one copy */
+                                      ASCII is never resident whole); 0 = automatic: reads of 64 MiB or more
+                                      stream in 256 MiB chunks (1 GiB when they exceed a quarter of the
+                                      free device memory), smaller ones are copied at once. Reads already in
+                                      page-locked memory are copied from directly, without staging. */
     uint32_t sort_tile;            /* onesweep tile shape (256 threads): 0 = 32 keys/thread (16 for 128-bit
                                       keys), 2 CTAs/SM (default); 1 = 16 (8), 3 CTAs/SM; 2 = 24 (12), 2/SM */
-    uint32_t reserved[1];
+    uint32_t compact;              /* form of sort-and-compact (step a4, with a5 and a6): 0 = bucketed
+                                      (default): one MSD radix pass moves candidates and first sightings
+                                      into key-range buckets; per bucket, in shared memory, duplicates are
+                                      merged into run lengths, first sightings add one, counts below
+                                      min_count are dropped and the rest sorted. 1 = global: LSD radix sort
+                                      of all candidates, run-length compaction, recount table, threshold.
+                                      Both are exact. Batches and recount_windows = 1 use the global form. */
 } turtle_params;
 
 /* Fill *p with the defaults above. */

@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("l2_fetch_bytes", u32),
                 ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
                 ("stream_chunk_mib", u32), ("sort_tile", u32),
-                ("reserved", u32 * 1)]
+                ("compact", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":
@@ -144,6 +144,38 @@ def _shape_keys(flat: np.ndarray, n: int, k: int) -> np.ndarray:
     return flat.reshape(n, 2) if k > 32 else flat
 
 
+class _ResultOwner:
+    """Holds a library-allocated turtle_result; frees it when the last NumPy view goes away."""
+
+    def __init__(self, lib, res):
+        self._lib, self._res = lib, res
+
+    def __del__(self):
+        self._lib.turtle_result_free(ctypes.byref(self._res))
+
+
+class _View:
+    """Array interface over one buffer of a turtle_result; keeps its owner alive."""
+
+    def __init__(self, owner, ptr, n, typestr):
+        self._owner = owner
+        self.__array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def _take(lib, res, k):
+    """(keys, counts, n_windows) viewing the library's buffers without a copy; the result is freed with them."""
+    w = 2 if k > 32 else 1
+    n = int(res.n)
+    nw = int(res.n_windows)
+    if n == 0:
+        lib.turtle_result_free(ctypes.byref(res))
+        return _shape_keys(np.zeros(0, dtype=np.uint64), 0, k), np.zeros(0, np.uint32), nw
+    owner = _ResultOwner(lib, res)
+    keys = np.asarray(_View(owner, ctypes.cast(res.keys, ctypes.c_void_p).value, n * w, "<u8"))
+    counts = np.asarray(_View(owner, ctypes.cast(res.counts, ctypes.c_void_p).value, n, "<u4"))
+    return _shape_keys(keys, n, k), counts, nw
+
+
 def turtle_count(bases, offsets, k: int, min_count: int = 2, params: Params | None = None, stream=None):
     """Host-memory form: (keys, counts, n_windows) as NumPy arrays, keys uint64[n] or uint64[n, 2] (hi, lo)."""
     lib = load()
@@ -154,15 +186,7 @@ def turtle_count(bases, offsets, k: int, min_count: int = 2, params: Params | No
     rc = lib.turtle_count_ex(ctypes.byref(reads), k, min_count, ctypes.byref(params) if params else None,
                              _stream_ptr(stream), ctypes.byref(res))
     _check(rc, "turtle_count")
-    try:
-        w = 2 if k > 32 else 1
-        n = res.n
-        keys = np.ctypeslib.as_array(res.keys, shape=(max(n * w, 1),))[: n * w].copy() if n else \
-            np.zeros(0, dtype=np.uint64)
-        counts = np.ctypeslib.as_array(res.counts, shape=(max(n, 1),))[:n].copy() if n else np.zeros(0, np.uint32)
-        return _shape_keys(keys, n, k), counts, int(res.n_windows)
-    finally:
-        lib.turtle_result_free(ctypes.byref(res))
+    return _take(lib, res, k)
 
 
 def _stream_ptr(stream):
@@ -222,18 +246,10 @@ def turtle_count_batch(jobs, params: Params | None = None, stream=None):
     rc = lib.turtle_count_batch(arr, len(jobs), ctypes.byref(params) if params else None, _stream_ptr(stream), outs)
     _check(rc, "turtle_count_batch")
     res = []
-    try:
-        for i, (_, _, k, _) in enumerate(jobs):
-            r = outs[i]
-            w = 2 if k > 32 else 1
-            n = r.n
-            keys = np.ctypeslib.as_array(r.keys, shape=(max(n * w, 1),))[: n * w].copy() if n else \
-                np.zeros(0, dtype=np.uint64)
-            counts = np.ctypeslib.as_array(r.counts, shape=(max(n, 1),))[:n].copy() if n else np.zeros(0, np.uint32)
-            res.append((_shape_keys(keys, n, k), counts, int(r.n_windows)))
-    finally:
-        for i in range(len(jobs)):
-            lib.turtle_result_free(ctypes.byref(outs[i]))
+    for i, (_, _, k, _) in enumerate(jobs):
+        r = _Result()
+        ctypes.memmove(ctypes.byref(r), ctypes.byref(outs[i]), ctypes.sizeof(_Result))
+        res.append(_take(lib, r, k))
     return res
 
 
@@ -266,17 +282,11 @@ class Server:
         if rc == -5:
             raise TurtleError(rc, "turtle_poll")
         k = self._keep.pop(ticket, (None, None, 31))[2]
-        try:
-            _check(rc, "turtle_poll")
-            w = 2 if k > 32 else 1
-            n = res.n
-            keys = np.ctypeslib.as_array(res.keys, shape=(max(n * w, 1),))[: n * w].copy() if n else \
-                np.zeros(0, dtype=np.uint64)
-            counts = np.ctypeslib.as_array(res.counts, shape=(max(n, 1),))[:n].copy() if n else \
-                np.zeros(0, np.uint32)
-            return _shape_keys(keys, n, k), counts, int(res.n_windows), tm
-        finally:
+        if rc != 0:
             self._lib.turtle_result_free(ctypes.byref(res))
+            _check(rc, "turtle_poll")
+        keys, counts, nw = _take(self._lib, res, k)
+        return keys, counts, nw, tm
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -185,7 +185,7 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
 bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
-           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 2;
+           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 2 && p.compact <= 1;
 }
 
 turtle_params resolve(const turtle_params *p) {
@@ -227,6 +227,93 @@ struct DeviceOut {
     uint32_t *counts = nullptr;
     uint64_t n = 0, n_windows = 0;
 };
+
+struct PartOut {
+    void *keys;
+    uint32_t *counts;
+    uint64_t n;
+};
+
+// Bucketed sort-and-compact of one key range [part_lo, part_hi) of the 2^part_bits parts: stable
+// radix sort of the candidates and of the first sightings by bucket index, bucket bounds, then per
+// bucket merge + first-sighting recount + threshold + sort, then a dense gather.
+constexpr uint64_t BUCKET_WINDOWS = 16384;  // candidates + first sightings per bucket, about
+
+// Buckets for n_all windows of the key range [part_lo, part_hi) of 2^part_bits parts; *bits = index
+// bits (8 per sort pass). A lone 9th or 17th bit would cost a whole pass: it is dropped instead
+// (buckets twice as full).
+BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int part_bits, int k, int *bits) {
+    int b = 0;
+    while (b < 24 && (n_all >> b) > BUCKET_WINDOWS) b++;
+    if (b % 8 == 1) b--;
+    BucketGeom bg{};
+    bg.k = k;
+    bg.f_lo = (uint64_t)part_lo << (62 - part_bits);
+    const uint64_t span = (uint64_t)(part_hi - part_lo) << (62 - part_bits);
+    bg.shift = 0;
+    while (bg.shift < 62 && (span >> bg.shift) > ((uint64_t)1 << b)) bg.shift++;
+    bg.n_buckets = (uint32_t)(((span - 1) >> bg.shift) + 1);  // <= 2^b
+    *bits = b;
+    return bg;
+}
+
+template <class K>
+PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, uint32_t min_count,
+                      K *cand, uint64_t n_cand, K *first_keys, uint64_t n_first, const BucketGeom &bg, int bits,
+                      uint64_t *hist, bool result_buffers, cudaStream_t s) {
+    constexpr int KW = sizeof(K) / 8;
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+    const uint64_t n_all = n_cand + n_first;
+    const uint32_t B = bg.n_buckets;
+    unsigned long long *off_c = (unsigned long long *)ctx_alloc(c, 8 * ((uint64_t)B + 1), s);
+    unsigned long long *off_f = (unsigned long long *)ctx_alloc(c, 8 * ((uint64_t)B + 1), s);
+    unsigned long long *nrep = (unsigned long long *)ctx_alloc(c, 8 * (uint64_t)B, s);
+    unsigned long long *out_off = (unsigned long long *)ctx_alloc(c, 8 * ((uint64_t)B + 1), s);
+    uint32_t *ticket = (uint32_t *)ctx_alloc(c, 16, s);
+    K *alt = (K *)ctx_alloc(c, sizeof(K) * (n_all ? n_all : 1), s);
+    uint32_t *tmp_counts = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s);
+    const int passes_all = (bits + 7) / 8;
+    SortScratch ss{};
+    ss.lookback_words = sort_lookback_words(n_cand > n_first ? n_cand : n_first, KW);
+    ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
+    ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
+    tm.start(TURTLE_STAGE_SORT);
+    int passes = 0;
+    ss.alt = alt;
+    ss.hist = hist;  // digit histograms from pass 1: candidates, then first sightings
+    K *sc = launch_bucket_sort<K>(lc, cand, n_cand, bg, bits, ss, err, &passes, true);
+    ss.alt = alt + n_cand;
+    ss.hist = hist + 256 * passes_all;
+    K *sf = n_first ? launch_bucket_sort<K>(lc, first_keys, n_first, bg, bits, ss, err, nullptr, true) : nullptr;
+    launch_bucket_bounds<K>(lc, sc, n_cand, bg, off_c);
+    if (sf) launch_bucket_bounds<K>(lc, sf, n_first, bg, off_f);
+    tm.stop(TURTLE_STAGE_SORT);
+    // per-bucket results go to whichever buffer holds neither sorted array
+    K *tmp = sc == cand ? alt : cand;
+    tm.start(TURTLE_STAGE_RLE);
+    ck(cudaMemsetAsync(ticket, 0, 16, s));
+    // cand is free after the scatter: it receives each bucket's results at the bucket's candidate offset
+    launch_bucket_count<K>(lc, sc, off_c, sf, off_f, B, min_count, tmp, tmp_counts, nrep, ticket, ctr + C_UNIQUE,
+                           err);
+    launch_scan_u64(lc, nrep, B, out_off);
+    tm.stop(TURTLE_STAGE_RLE);
+    ck(cudaMemcpyAsync(ctr + C_OUT, out_off + B, 8, cudaMemcpyDeviceToDevice, s));
+    const int sorts = (n_cand > 1 && passes ? 1 : 0) + (n_first > 1 && passes ? 1 : 0);
+    st.stage_launches[TURTLE_STAGE_SORT] += sorts * (passes + 1) + (sf ? 2 : 1);
+    st.stage_launches[TURTLE_STAGE_RLE] += 2;
+    st.sort_passes = (uint32_t)passes;
+    read_back(c, s);
+    const uint64_t n_out = c->h_ctr[C_OUT];
+    st.n_unique += c->h_ctr[C_UNIQUE];
+    K *okeys = (K *)ctx_alloc(c, sizeof(K) * (n_out ? n_out : 1), s, result_buffers);
+    uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (n_out ? n_out : 1), s, result_buffers);
+    tm.start(TURTLE_STAGE_THRESHOLD);
+    launch_bucket_gather<K>(lc, tmp, tmp_counts, off_c, out_off, B, okeys, ocounts);
+    tm.stop(TURTLE_STAGE_THRESHOLD);
+    st.stage_launches[TURTLE_STAGE_THRESHOLD] += 1;
+    return PartOut{okeys, ocounts, n_out};
+}
 
 template <class K>
 void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
@@ -331,12 +418,9 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     }
     const bool parted = groups.size() > 1;
     st.super_partitions = (uint32_t)groups.size();
+    // the bucketed form of sort-and-compact; batches and the window-recount mode use the global form
+    const bool bucketed = !tag && prm.compact == 0 && (firsts_mode || !use_filter);
 
-    struct PartOut {
-        void *keys;
-        uint32_t *counts;
-        uint64_t n;
-    };
     std::vector<PartOut> outs;
     for (size_t g = 0; g < groups.size(); g++) {
         const uint64_t Wg = group_w[g];
@@ -374,14 +458,21 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         K *cand = (K *)ctx_alloc(c, sizeof(K) * Wg, s);
         K *firsts = firsts_mode ? cand : nullptr;  // first sightings fill the same buffer from the top
         uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
-        ck(cudaMemsetAsync(hist, 0, 8 * 256 * passes, s));
+        int bucket_bits = 0;
+        BucketGeom bg{};
+        if (bucketed)  // every window of the range becomes a candidate or a first sighting: Wg of them
+            bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
+                             PART_BITS, k, &bucket_bits);
+        const int hist_passes = bucketed ? (bucket_bits + 7) / 8 : passes;
+        ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
         tm.start(TURTLE_STAGE_FILTER);
         launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wg, firsts, ctr + C_FIRST, Wg, hist,
-                        passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
-                        tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err);
+                        hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
+                        tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
+                        bucketed ? &bg : nullptr);
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;
-        ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
+        if (!bucketed) ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
         read_back(c, s);
         const uint64_t n_cand = c->h_ctr[C_CAND];
         const uint64_t n_first = c->h_ctr[C_FIRST];
@@ -389,6 +480,11 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         st.n_candidates += n_cand;
         st.n_firsts += n_first;
 
+        PartOut po{};
+        if (bucketed) {
+            po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, const_cast<K *>(first_keys), n_first, bg,
+                                  bucket_bits, hist, !parted, s);
+        } else {
         // a4: sort + compact
         SortScratch ss{};
         ss.alt = ctx_alloc(c, sizeof(K) * (n_cand ? n_cand : 1), s);
@@ -415,7 +511,6 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         tm.stop(TURTLE_STAGE_RLE);
         st.stage_launches[TURTLE_STAGE_RLE] += n_cand ? 1 : 0;
 
-        PartOut po{};
         if (!use_filter) {
             // every window is a candidate: run lengths are the exact counts (min_count == 1)
             uint32_t *counts = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s, !parted);
@@ -501,6 +596,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             read_back(c, s);
             po = PartOut{okeys, ocounts, c->h_ctr[C_OUT]};
         }
+        }  // global form
         if (prm.timing) {  // accumulate this super-partition's stage times (events are reused per part)
             for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
                 float ms = 0.f;
@@ -639,11 +735,21 @@ void ensure_pinned(turtle_ctx *c, size_t bytes) {
 
 constexpr size_t STAGE_CHUNK = (size_t)64 << 20;
 
+// True when p lies in page-locked host memory the copy engines can read or write directly.
+bool is_pinned(const void *p) {
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 // Device -> pageable host through the pinned buffers: the DMA of chunk i overlaps the
 // multi-threaded host copy of chunk i-1. Synchronises s.
 void copy_to_host(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (!bytes) return;
-    if (bytes < ((size_t)1 << 20)) {  // small: one plain copy
+    if (bytes < ((size_t)1 << 20) || is_pinned(dst)) {  // small or already pinned: one plain copy
         ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
         ck(cudaStreamSynchronize(s));
         return;
@@ -667,7 +773,7 @@ void copy_to_host(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaS
 // Pageable host -> device through the pinned buffers (host copy of chunk i+1 overlaps the DMA of chunk i).
 void copy_to_device(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (!bytes) return;
-    if (bytes < ((size_t)1 << 20)) {
+    if (bytes < ((size_t)1 << 20) || is_pinned(src)) {
         ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
         return;
     }
@@ -696,7 +802,8 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
     pp.S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
     ck(cudaMemsetAsync(pp.S, 0, 8 * L.b_words, s));
     chunk = (chunk + 63) & ~(size_t)63;  // chunk starts fall on 64-position boundaries (whole bitmap words)
-    ensure_pinned(c, chunk);
+    const bool direct = is_pinned(reads->bases);  // caller's memory is page-locked: DMA straight from it
+    if (!direct) ensure_pinned(c, chunk);
     uint8_t *stage[2];
     for (auto &st : stage) st = (uint8_t *)ctx_alloc(c, chunk, s);
     for (int i = 0; i < 2; i++) ck(cudaEventRecord(c->ev_packed[i], s));  // both staging buffers start free
@@ -705,10 +812,14 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
     for (uint64_t i = 0; i < n_chunks; i++) {
         const int b = (int)(i & 1);
         const uint64_t c0 = i * chunk, c1 = c0 + chunk < n_bases ? c0 + chunk : n_bases;
-        ck(cudaEventSynchronize(c->ev_h2d[b]));  // the pinned buffer's previous copy has finished
-        par_memcpy(c->pinned[b], reads->bases + c0, c1 - c0);
+        const char *src = reads->bases + c0;
+        if (!direct) {
+            ck(cudaEventSynchronize(c->ev_h2d[b]));  // the pinned buffer's previous copy has finished
+            par_memcpy(c->pinned[b], src, c1 - c0);
+            src = (const char *)c->pinned[b];
+        }
         ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0));  // its staging buffer was packed
-        ck(cudaMemcpyAsync(stage[b], c->pinned[b], c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
+        ck(cudaMemcpyAsync(stage[b], src, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
         ck(cudaEventRecord(c->ev_h2d[b], c->copy_stream));
         ck(cudaStreamWaitEvent(s, c->ev_h2d[b], 0));
         const uint64_t g0 = c0 / 32, g1 = i + 1 == n_chunks ? L.pack_groups() : c1 / 32;

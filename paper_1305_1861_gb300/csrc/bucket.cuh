@@ -1,0 +1,32 @@
+// Bucket index of a key for the bucketed sort-and-compact (device side).
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace turtle {
+
+// ((f(v) - f_lo) >> shift) clamped to [0, n_buckets), v = top 31 bits of the 2k-bit key,
+// f(v) = v (2^32 - v): monotone in the key, so buckets are consecutive key ranges, and about
+// equally full for the canonical keys of random sequence.
+template <class K>
+__device__ __forceinline__ uint32_t bucket_of(K key, const BucketGeom &g) {
+    const uint64_t v = top31(key, g.k);
+    const uint64_t f = v * ((1ull << 32) - v);
+    const uint64_t b = f >= g.f_lo ? (f - g.f_lo) >> g.shift : 0;
+    return b < g.n_buckets ? (uint32_t)b : g.n_buckets - 1;
+}
+
+// Radix digit policies for the onesweep passes: a byte of the key, or a byte of its bucket index.
+template <class K>
+struct RawDigit {
+    __device__ __forceinline__ uint32_t operator()(K key, int shift) const { return KeyT<K>::digit(key, shift); }
+};
+template <class K>
+struct BucketDigit {
+    BucketGeom g;
+    __device__ __forceinline__ uint32_t operator()(K key, int shift) const {
+        return (bucket_of(key, g) >> shift) & 0xffu;
+    }
+};
+
+}  // namespace turtle

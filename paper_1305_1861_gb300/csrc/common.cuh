@@ -164,6 +164,13 @@ __device__ __forceinline__ Key128 shfl_key(Key128 k, int src) {
     r.lo = __shfl_sync(FULL, k.lo, src);
     return r;
 }
+__device__ __forceinline__ uint64_t shfl_down_key(uint64_t k, int d) { return __shfl_down_sync(FULL, k, d); }
+__device__ __forceinline__ Key128 shfl_down_key(Key128 k, int d) {
+    Key128 r;
+    r.hi = __shfl_down_sync(FULL, k.hi, d);
+    r.lo = __shfl_down_sync(FULL, k.lo, d);
+    return r;
+}
 __device__ __forceinline__ uint64_t shfl_up_key(uint64_t k) { return __shfl_up_sync(FULL, k, 1); }
 __device__ __forceinline__ Key128 shfl_up_key(Key128 k) {
     Key128 r;

@@ -15,8 +15,7 @@
 // key seen twice emits at least one candidate (no false negatives, for any
 // interleaving). A plain load that already shows every pattern bit set proves
 // "seen" without the atomic, because bits are never cleared.
-#include "common.cuh"
-#include "kernels.h"
+#include "bucket.cuh"
 
 namespace turtle {
 
@@ -69,12 +68,19 @@ __device__ __forceinline__ void flush_rest(K *wbuf, int nbuf, K *out, unsigned l
 }
 
 // Digit counts of every radix pass for the keys being flushed (fused into pass 1 so the
-// sorter does not have to read the candidates once more just to histogram them).
+// sorter does not have to read the keys once more just to histogram them): digits of the key
+// itself, or (by_bucket) of its bucket index for the bucketed sort-and-compact.
 template <class K>
-__device__ __forceinline__ void hist_keys(const K *buf, int count, uint32_t *s_hist, int passes, int lane) {
+__device__ __forceinline__ void hist_keys(const K *buf, int count, uint32_t *s_hist, int passes, int lane,
+                                          const BucketGeom &bg, bool by_bucket) {
     for (int j = lane; j < count; j += WARP) {
         const K key = buf[j];
-        for (int p = 0; p < passes; p++) atomicAdd(&s_hist[p * 256 + KeyT<K>::digit(key, 8 * p)], 1u);
+        if (by_bucket) {
+            const uint32_t b = bucket_of(key, bg);
+            for (int p = 0; p < passes; p++) atomicAdd(&s_hist[p * 256 + ((b >> (8 * p)) & 0xffu)], 1u);
+        } else {
+            for (int p = 0; p < passes; p++) atomicAdd(&s_hist[p * 256 + KeyT<K>::digit(key, 8 * p)], 1u);
+        }
     }
 }
 
@@ -91,12 +97,15 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     uint64_t *hist, int hist_passes, int part_bits, uint32_t part_lo,
                                                     uint32_t part_hi, const uint64_t *__restrict__ lib_starts,
                                                     int n_libs, const uint64_t *__restrict__ lib_filter,
-                                                    uint32_t *err) {
+                                                    BucketGeom bg, int by_bucket, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
+    // by_bucket: first sightings get their own histograms, after the candidates'
+    const int n_hist = 256 * hist_passes * (by_bucket && EMIT_FIRSTS ? 2 : 1);
     K *s_buf = reinterpret_cast<K *>(smem);
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
-    uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + 256 * hist_passes);
+    uint32_t *s_fhist = s_hist + 256 * hist_passes;
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
     __shared__ uint64_t s_lib[65];
     __shared__ uint64_t s_lf[128];  // per-library filter region: first sector, shift of the hash
     if (n_libs)
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
         for (int i = threadIdx.x; i < 2 * n_libs; i += P1_BLOCK) s_lf[i] = lib_filter[i];
     if (USE_FILTER)
         for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
-    for (int i = threadIdx.x; i < 256 * hist_passes; i += P1_BLOCK) s_hist[i] = 0;
+    for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK) s_hist[i] = 0;
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             nbuf += __popc(b);
             if (nbuf >= P1_STAGE) {
                 __syncwarp();
-                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane);
+                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane, bg, by_bucket);
                 flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
             }
             if (EMIT_FIRSTS) {
@@ -191,16 +200,25 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                 const uint32_t bf = __ballot_sync(FULL, f);
                 if (f) fbuf[nfirst + __popc(bf & lt)] = key[i];
                 nfirst += __popc(bf);
-                if (nfirst >= P1_STAGE) flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+                if (nfirst >= P1_STAGE) {
+                    if (by_bucket) {
+                        __syncwarp();
+                        hist_keys(fbuf, P1_STAGE, s_fhist, hist_passes, lane, bg, true);
+                    }
+                    flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+                }
             }
         }
     }
     __syncwarp();
-    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane);
+    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane, bg, by_bucket);
     flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
-    if (EMIT_FIRSTS) flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+    if (EMIT_FIRSTS) {
+        if (by_bucket) hist_keys(fbuf, nfirst, s_fhist, hist_passes, lane, bg, true);
+        flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < 256 * hist_passes; i += P1_BLOCK)
+    for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK)
         if (s_hist[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)s_hist[i]);
 }
 
@@ -255,11 +273,14 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
-                  const uint64_t *lib_filter, uint32_t *err) {
+                  const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket) {
     const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     const bool emit_firsts = use_filter && firsts != nullptr;
     if (!hist) hist_passes = 0;
-    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) + 4 * 256 * hist_passes +
+    const BucketGeom bg = bucket ? *bucket : BucketGeom{};
+    const int by_bucket = bucket != nullptr;
+    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
+                        4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) +
                         (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
     auto kern = emit_firsts ? k_pass1<K, true, true> : (use_filter ? k_pass1<K, true, false> : k_pass1<K, false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -272,7 +293,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
                                              cand, cand_count, cand_cap, firsts, first_count, first_cap, hist,
                                              hist_passes, part_bits, part_lo, part_hi, lib_starts, n_libs,
-                                             lib_filter, err);
+                                             lib_filter, bg, by_bucket, err);
 }
 
 template <class K>
@@ -286,11 +307,11 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
                                      unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, const uint64_t *, int,
-                                     const uint64_t *, uint32_t *);
+                                     const uint64_t *, uint32_t *, const BucketGeom *);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
                                    unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
-                                   const uint64_t *, int, const uint64_t *, uint32_t *);
+                                   const uint64_t *, int, const uint64_t *, uint32_t *, const BucketGeom *);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

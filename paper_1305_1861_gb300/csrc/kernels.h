@@ -24,6 +24,16 @@ struct PackLayout {
     uint64_t pack_groups() const { return 2 * b_words; }  // groups of 32 positions, padding included
 };
 
+// Bucket of a key (bucketed sort-and-compact): ((f(top31(key)) - f_lo) >> shift), clamped to
+// [0, n_buckets), with the monotone map f(v) = v (2^32 - v) of the key-range parts: buckets are
+// consecutive key ranges.
+struct BucketGeom {
+    uint64_t f_lo;
+    int shift;
+    uint32_t n_buckets;
+    int k;
+};
+
 struct LaunchCfg {
     int sms;            // multiprocessors on the device
     cudaStream_t stream;
@@ -66,7 +76,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
-                  const uint64_t *lib_filter, uint32_t *err);
+                  const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr);
 // Valid windows of each library of a batch (counts: n_libs zeroed counters).
 void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,
                         int n_libs, unsigned long long *counts);
@@ -145,5 +155,29 @@ template <class K>
 void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, const void *table, const TableGeom &tg,
                       uint32_t min_count, K *out_keys, uint32_t *out_counts, unsigned long long *n_out,
                       uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err);
+
+// ---------------------------------------------------------------- bucketed sort-and-compact (bucket.cu)
+// Stable sort of keys[0 .. n) by bucket index (8 bits per onesweep pass); returns keys or s.alt.
+template <class K>
+K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom &g, int bits, const SortScratch &s,
+                      uint32_t *err, int *passes_run, bool hist_ready);
+// off[b] <- first position of bucket b in bucket-sorted keys, b = 0 .. n_buckets (off[n_buckets] = n).
+template <class K>
+void launch_bucket_bounds(const LaunchCfg &c, const K *keys, uint64_t n, const BucketGeom &g,
+                          unsigned long long *off);
+// out[0 .. n] <- exclusive scan of in[0 .. n), out[n] = total (one CTA).
+void launch_scan_u64(const LaunchCfg &c, const unsigned long long *in, uint64_t n, unsigned long long *out);
+// Per bucket: merge candidates, add first sightings (first may be null), keep count >= min_count,
+// sort; results at tmp_*[off_c[b] ..], their number at n_rep[b]. ticket must be zero on entry.
+template <class K>
+void launch_bucket_count(const LaunchCfg &c, const K *cand, const unsigned long long *off_c, const K *first,
+                         const unsigned long long *off_f, uint32_t B, uint32_t min_count, K *tmp_keys,
+                         uint32_t *tmp_counts, unsigned long long *n_rep, uint32_t *ticket,
+                         unsigned long long *n_distinct, uint32_t *err);
+// Dense output: bucket b's n_rep entries from tmp_*[off[b] ..] to out[out_off[b] ..].
+template <class K>
+void launch_bucket_gather(const LaunchCfg &c, const K *tmp_keys, const uint32_t *tmp_counts,
+                          const unsigned long long *off, const unsigned long long *out_off, uint32_t B, K *okeys,
+                          uint32_t *ocounts);
 
 }  // namespace turtle

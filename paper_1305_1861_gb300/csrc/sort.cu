@@ -11,8 +11,7 @@
 // digits is written contiguously. Each pass reads and writes every key once.
 // Run-length compaction then keeps the first key of each run (flag = key differs
 // from its predecessor) with an order-preserving single-pass scan.
-#include "common.cuh"
-#include "kernels.h"
+#include "bucket.cuh"
 
 namespace turtle {
 
@@ -42,15 +41,15 @@ uint64_t sort_lookback_words(uint64_t n, int key_words) {  // sized for the smal
     return ((n + tile - 1) / tile + 1) * BINS;
 }
 
-template <class K>
+template <class K, class D>
 __global__ void __launch_bounds__(S_BLOCK) k_hist(const K *__restrict__ keys, uint64_t n, int passes,
-                                                  uint64_t *__restrict__ hist) {
+                                                  uint64_t *__restrict__ hist, D dig) {
     __shared__ uint32_t sh[MAX_PASSES * BINS];
     for (int i = threadIdx.x; i < passes * BINS; i += S_BLOCK) sh[i] = 0;
     __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)S_BLOCK + threadIdx.x; i < n; i += (uint64_t)gridDim.x * S_BLOCK) {
         const K key = keys[i];
-        for (int p = 0; p < passes; p++) atomicAdd(&sh[p * BINS + KeyT<K>::digit(key, 8 * p)], 1u);
+        for (int p = 0; p < passes; p++) atomicAdd(&sh[p * BINS + dig(key, 8 * p)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * BINS; i += S_BLOCK)
@@ -75,14 +74,15 @@ __global__ void k_scan_bins(uint64_t *hist) {
     h[threadIdx.x] = s[threadIdx.x];
 }
 
-template <class K, int ITEMS, int MINB>
+template <class K, int ITEMS, int MINB, class D>
 __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
                                                             int shift, const uint64_t *__restrict__ bin_base,
                                                             uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
-                                                            uint32_t *err) {
+                                                            uint32_t *err, D digit) {
     constexpr int TILE = S_BLOCK * ITEMS;
     extern __shared__ __align__(16) unsigned char os_smem[];
     K *skeys = reinterpret_cast<K *>(os_smem);  // TILE keys (dynamic: up to 64 KB)
+    __shared__ uint8_t sdig[TILE];  // digit of each staged key: the scatter does not recompute it
     __shared__ uint32_t whist[S_WARPS][BINS];
     __shared__ uint32_t s_texcl[BINS];
     __shared__ uint64_t s_glob[BINS];
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
         const uint32_t r = (uint32_t)(i * WARP + lane);
-        const uint32_t d = (full || r < n_in_warp) ? KeyT<K>::digit(key[i], shift) : 0u;
+        const uint32_t d = (full || r < n_in_warp) ? digit(key[i], shift) : 0u;
         if ((i & 3) == 0) dig[i >> 2] = d;
         else dig[i >> 2] |= d << (8 * (i & 3));
     }
@@ -151,7 +151,10 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
         uint32_t pos = 0;
         if (valid && lane == leader) pos = atomicAdd(&whist[warp][d], (uint32_t)__popc(peers));
         pos = __shfl_sync(FULL, pos, leader);
-        if (valid) skeys[pos + __popc(peers & lt)] = key[i];
+        if (valid) {
+            skeys[pos + __popc(peers & lt)] = key[i];
+            sdig[pos + __popc(peers & lt)] = (uint8_t)d;
+        }
     }
     // 4. global offsets of this tile's digits (predecessors have usually published by now)
     const uint64_t excl = lookback_prefix(lookback + tid, BINS, tile, tcount, epoch, err);
@@ -160,27 +163,25 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     if (full) {
 #pragma unroll 4
         for (uint32_t p = tid; p < (uint32_t)TILE; p += S_BLOCK) {
-            const K kk = skeys[p];
-            out[s_glob[KeyT<K>::digit(kk, shift)] + p] = kk;
+            out[s_glob[sdig[p]] + p] = skeys[p];
         }
     } else {
         const uint32_t tile_n = (uint32_t)(n - start);
         for (uint32_t p = tid; p < tile_n; p += S_BLOCK) {
-            const K kk = skeys[p];
-            out[s_glob[KeyT<K>::digit(kk, shift)] + p] = kk;
+            out[s_glob[sdig[p]] + p] = skeys[p];
         }
     }
 }
 
-template <class K, int V>
+template <class K, int V, class D = RawDigit<K>>
 static void onesweep_pass(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
-                          uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+                          uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err, D digit = D{}) {
     constexpr int ITEMS = SortCfg<K>::V_ITEMS[V], MINB = SortCfg<K>::V_MINB[V];
     const uint64_t tiles = (n + S_BLOCK * ITEMS - 1) / (S_BLOCK * ITEMS);
     const size_t smem = sizeof(K) * S_BLOCK * ITEMS;
-    cudaFuncSetAttribute(k_onesweep<K, ITEMS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_onesweep<K, ITEMS, MINB><<<(int)tiles, S_BLOCK, smem, c.stream>>>(src, dst, n, shift, bin_base, lookback,
-                                                                       tile_ctr, epoch, err);
+    cudaFuncSetAttribute(k_onesweep<K, ITEMS, MINB, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_onesweep<K, ITEMS, MINB, D><<<(int)tiles, S_BLOCK, smem, c.stream>>>(src, dst, n, shift, bin_base, lookback,
+                                                                          tile_ctr, epoch, err, digit);
 }
 
 template <class K>
@@ -198,14 +199,47 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
         cudaMemsetAsync(s.hist, 0, sizeof(uint64_t) * passes * BINS, c.stream);
         uint64_t need = (n + S_BLOCK - 1) / S_BLOCK;
         const uint64_t cap = (uint64_t)c.sms * 4;
-        k_hist<K><<<(int)(need < cap ? need : cap), S_BLOCK, 0, c.stream>>>(keys, n, passes, s.hist);
+        k_hist<K><<<(int)(need < cap ? need : cap), S_BLOCK, 0, c.stream>>>(keys, n, passes, s.hist, RawDigit<K>{});
     }
     k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
     K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
     for (int p = 0; p < passes; p++) {
         if ((skip_mask >> p) & 1u) continue;  // every key has the same digit here: the pass would be a copy
         auto pass = variant == 0 ? onesweep_pass<K, 0> : (variant == 1 ? onesweep_pass<K, 1> : onesweep_pass<K, 2>);
-        pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err);
+        pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err,
+             RawDigit<K>{});
+        if (passes_run) (*passes_run)++;
+        K *t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// Stable LSD sort by bucket index (bits bits, 8 per pass); keys keep their input order inside a
+// bucket. Returns the buffer holding the result (keys or s.alt).
+template <class K>
+K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom &g, int bits, const SortScratch &s,
+                      uint32_t *err, int *passes_run, bool hist_ready) {
+    const int passes = (bits + 7) / 8;
+    if (passes_run) *passes_run = 0;
+    if (n <= 1 || passes == 0) return keys;
+    const BucketDigit<K> dig{g};
+    const uint64_t TILE = (uint64_t)S_BLOCK * SortCfg<K>::V_ITEMS[0];
+    const uint64_t tiles = (n + TILE - 1) / TILE;
+    cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
+    cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
+    if (!hist_ready) {
+        cudaMemsetAsync(s.hist, 0, sizeof(uint64_t) * passes * BINS, c.stream);
+        const uint64_t need = (n + S_BLOCK - 1) / S_BLOCK, cap = (uint64_t)c.sms * 4;
+        k_hist<K, BucketDigit<K>><<<(int)(need < cap ? need : cap), S_BLOCK, 0, c.stream>>>(keys, n, passes, s.hist,
+                                                                                         dig);
+    }
+    k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
+    K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
+    for (int p = 0; p < passes; p++) {
+        onesweep_pass<K, 0, BucketDigit<K>>(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback,
+                                            s.tile_ctr + p, (uint32_t)(p + 1), err, dig);
         if (passes_run) (*passes_run)++;
         K *t = src;
         src = dst;
@@ -319,6 +353,10 @@ template uint64_t *launch_radix_sort<uint64_t>(const LaunchCfg &, uint64_t *, ui
                                                uint32_t *, bool, uint32_t, int *, int);
 template Key128 *launch_radix_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, const SortScratch &, uint32_t *,
                                            bool, uint32_t, int *, int);
+template uint64_t *launch_bucket_sort<uint64_t>(const LaunchCfg &, uint64_t *, uint64_t, const BucketGeom &, int,
+                                                const SortScratch &, uint32_t *, int *, bool);
+template Key128 *launch_bucket_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, const BucketGeom &, int,
+                                            const SortScratch &, uint32_t *, int *, bool);
 template void launch_rle<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, uint64_t *, uint64_t *,
                                    unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
 template void launch_rle<Key128>(const LaunchCfg &, const Key128 *, uint64_t, Key128 *, uint64_t *,

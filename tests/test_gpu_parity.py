@@ -183,9 +183,15 @@ def _check_count(ctx, bases, offs, k, min_count, params=None):
 
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("min_count", [1, 2, 3])
-def test_count_small_library_all_k(ctx, k, min_count):
+@pytest.mark.parametrize("compact", [0, 1])
+def test_count_small_library_all_k(ctx, k, min_count, compact):
+    """Both forms of sort-and-compact: bucketed (default) and global."""
+    import paper_1305_1861_gb300 as pkg
+
     lib = synth.small(seed=k, scale=0.02)  # 20 kbp genome, 4000 reads: many tiles, ragged tails
-    _check_count(ctx, lib.bases, lib.offsets, k, min_count)
+    st = _check_count(ctx, lib.bases, lib.offsets, k, min_count, pkg.Params.default(compact=compact))
+    if compact == 0:
+        assert st["sort_passes"] == 1 and st["stage_launches"]["table"] == 0
 
 
 @pytest.mark.parametrize("k", [5, 31, 32, 33, 64])
