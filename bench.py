@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1 = default)")
     ap.add_argument("--recount-windows", action="store_true", help="recount by re-extracting every window")
     ap.add_argument("--member-filter", action="store_true", help="screen first sightings with a membership bitmap")
-    ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..2 (-1 = default)")
+    ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..3 (-1 = default)")
+    ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
+    ap.add_argument("--compact", type=int, default=-1, help="0 = bucketed, 1 = global sort-and-compact")
     ap.add_argument("--micro", action="store_true",
                     help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()
@@ -202,6 +204,10 @@ def run_ours(args, rank, world):
         prm.member_filter = 1
     if args.sort_tile >= 0:
         prm.sort_tile = args.sort_tile
+    if args.bucket_slots:
+        prm.bucket_slots = args.bucket_slots
+    if args.compact >= 0:
+        prm.compact = args.compact
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)

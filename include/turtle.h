@@ -85,15 +85,21 @@ typedef struct {
                                       stream in 256 MiB chunks (1 GiB when they exceed a quarter of the
                                       free device memory), smaller ones are copied at once. Reads already in
                                       page-locked memory are copied from directly, without staging. */
-    uint32_t sort_tile;            /* onesweep tile shape (256 threads): 0 = 32 keys/thread (16 for 128-bit
-                                      keys), 2 CTAs/SM (default); 1 = 16 (8), 3 CTAs/SM; 2 = 24 (12), 2/SM */
+    uint32_t sort_tile;            /* onesweep tile shape (256 threads): 0 = default (global sort: 32 keys per
+                                      thread, 16 for 128-bit keys, 2 CTAs/SM; bucket sort: 16 (8), 3 CTAs/SM);
+                                      1 = 16 (8), 3 CTAs/SM; 2 = 24 (12), 2/SM; 3 = 32 (16), 2/SM */
     uint32_t compact;              /* form of sort-and-compact (step a4, with a5 and a6): 0 = bucketed
                                       (default): one MSD radix pass moves candidates and first sightings
                                       into key-range buckets; per bucket, in shared memory, duplicates are
                                       merged into run lengths, first sightings add one, counts below
                                       min_count are dropped and the rest sorted. 1 = global: LSD radix sort
                                       of all candidates, run-length compaction, recount table, threshold.
-                                      Both are exact. Batches and recount_windows = 1 use the global form. */
+                                      Both are exact. recount_windows = 1 uses the global form. */
+    uint32_t bucket_slots;         /* bucketed form: shared-memory table of one bucket CTA, 0 = 4096 slots
+                                      (512 threads, two CTAs per SM; default), 8192 = 8192 slots (1024
+                                      threads, one CTA per SM: twice the distinct keys per bucket before a
+                                      bucket is split) */
+    uint32_t reserved;
 } turtle_params;
 
 /* Fill *p with the defaults above. */

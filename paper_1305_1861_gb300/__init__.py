@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("l2_fetch_bytes", u32),
                 ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
                 ("stream_chunk_mib", u32), ("sort_tile", u32),
-                ("compact", u32)]
+                ("compact", u32), ("bucket_slots", u32), ("reserved", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":

@@ -185,7 +185,8 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
 bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
-           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 2 && p.compact <= 1;
+           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 1 &&
+           (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192);
 }
 
 turtle_params resolve(const turtle_params *p) {
@@ -260,7 +261,7 @@ BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int p
 template <class K>
 PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, uint32_t min_count,
                       K *cand, uint64_t n_cand, K *first_keys, uint64_t n_first, const BucketGeom &bg, int bits,
-                      uint64_t *hist, bool result_buffers, cudaStream_t s) {
+                      uint64_t *hist, bool result_buffers, int variant, bool large_table, cudaStream_t s) {
     constexpr int KW = sizeof(K) / 8;
     uint32_t *err = c->d_err;
     unsigned long long *ctr = c->d_ctr;
@@ -282,10 +283,11 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     int passes = 0;
     ss.alt = alt;
     ss.hist = hist;  // digit histograms from pass 1: candidates, then first sightings
-    K *sc = launch_bucket_sort<K>(lc, cand, n_cand, bg, bits, ss, err, &passes, true);
+    K *sc = launch_bucket_sort<K>(lc, cand, n_cand, bg, bits, ss, err, &passes, true, variant);
     ss.alt = alt + n_cand;
     ss.hist = hist + 256 * passes_all;
-    K *sf = n_first ? launch_bucket_sort<K>(lc, first_keys, n_first, bg, bits, ss, err, nullptr, true) : nullptr;
+    K *sf = n_first ? launch_bucket_sort<K>(lc, first_keys, n_first, bg, bits, ss, err, nullptr, true, variant)
+                    : nullptr;
     launch_bucket_bounds<K>(lc, sc, n_cand, bg, off_c);
     if (sf) launch_bucket_bounds<K>(lc, sf, n_first, bg, off_f);
     tm.stop(TURTLE_STAGE_SORT);
@@ -295,7 +297,7 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     ck(cudaMemsetAsync(ticket, 0, 16, s));
     // cand is free after the scatter: it receives each bucket's results at the bucket's candidate offset
     launch_bucket_count<K>(lc, sc, off_c, sf, off_f, B, min_count, tmp, tmp_counts, nrep, ticket, ctr + C_UNIQUE,
-                           err);
+                           err, large_table ? 1 : 0);
     launch_scan_u64(lc, nrep, B, out_off);
     tm.stop(TURTLE_STAGE_RLE);
     ck(cudaMemcpyAsync(ctr + C_OUT, out_off + B, 8, cudaMemcpyDeviceToDevice, s));
@@ -418,8 +420,8 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     }
     const bool parted = groups.size() > 1;
     st.super_partitions = (uint32_t)groups.size();
-    // the bucketed form of sort-and-compact; batches and the window-recount mode use the global form
-    const bool bucketed = !tag && prm.compact == 0 && (firsts_mode || !use_filter);
+    // the bucketed form of sort-and-compact; the window-recount mode uses the global form
+    const bool bucketed = prm.compact == 0 && (firsts_mode || !use_filter);
 
     std::vector<PartOut> outs;
     for (size_t g = 0; g < groups.size(); g++) {
@@ -460,9 +462,26 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
         int bucket_bits = 0;
         BucketGeom bg{};
-        if (bucketed)  // every window of the range becomes a candidate or a first sighting: Wg of them
+        if (bucketed && tag) {  // batch: each library its own range of buckets, sized by its windows
+            std::vector<uint4> lg(tag->n_libs);
+            uint32_t at = 0;
+            for (int l = 0; l < tag->n_libs; l++) {
+                int b = 0;
+                while (b < 20 && (lib_w[l] >> b) > BUCKET_WINDOWS) b++;
+                lg[l] = make_uint4(at, 1u << b, (uint32_t)(62 - b), 0u);
+                at += 1u << b;
+            }
+            uint4 *d_lg = (uint4 *)ctx_alloc(c, sizeof(uint4) * lg.size(), s);
+            ck(cudaMemcpyAsync(d_lg, lg.data(), sizeof(uint4) * lg.size(), cudaMemcpyHostToDevice, s));
+            bg.k = k;
+            bg.n_buckets = at;
+            bg.tag_shift = 2 * k;
+            bg.lib = d_lg;
+            while (bucket_bits < 24 && ((uint64_t)1 << bucket_bits) < at) bucket_bits++;
+        } else if (bucketed) {  // every window of the range becomes a candidate or a first sighting: Wg of them
             bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
                              PART_BITS, k, &bucket_bits);
+        }
         const int hist_passes = bucketed ? (bucket_bits + 7) / 8 : passes;
         ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
         tm.start(TURTLE_STAGE_FILTER);
@@ -483,7 +502,9 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         PartOut po{};
         if (bucketed) {
             po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, const_cast<K *>(first_keys), n_first, bg,
-                                  bucket_bits, hist, !parted, s);
+                                  bucket_bits, hist, !parted,
+                                  prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
+                                  prm.bucket_slots == 8192, s);
         } else {
         // a4: sort + compact
         SortScratch ss{};
@@ -499,7 +520,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         tm.start(TURTLE_STAGE_SORT);
         int passes_run = 0;
         K *sorted = launch_radix_sort<K>(lc, cand, n_cand, key_bits, ss, err, true, skip, &passes_run,
-                                         (int)prm.sort_tile);
+                                         prm.sort_tile == 3 ? 0 : (int)prm.sort_tile);
         tm.stop(TURTLE_STAGE_SORT);
         st.sort_passes = (uint32_t)passes_run;
         st.stage_launches[TURTLE_STAGE_SORT] += n_cand > 1 ? passes_run + 1 : 0;

@@ -23,18 +23,21 @@ namespace turtle {
 
 namespace {
 
-constexpr uint32_t BT_THREADS = 512;              // threads of one bucket CTA
-constexpr uint32_t BT_SLOTS = 4096;                // shared-memory table slots
-constexpr uint32_t BT_LOG2 = 12;
-constexpr uint32_t BT_LIMIT = 3072;                // distinct keys per attempt before a split (load 0.75)
-constexpr uint32_t BT_ITEMS = BT_LIMIT / BT_THREADS;  // table entries a thread extracts
-constexpr int BT_STACK = 136;                      // pending key ranges (2 per split level, 128-bit ranges)
+// Bucket CTA shapes: threads, shared-memory table slots, CTAs per SM. A table attempt holds at most
+// LIMIT distinct keys (load 0.75); every thread extracts ITEMS table entries.
+template <uint32_t THREADS_, uint32_t LOG2_, int MINB_>
+struct BtCfg {
+    static constexpr uint32_t THREADS = THREADS_, LOG2 = LOG2_, SLOTS = 1u << LOG2_;
+    static constexpr uint32_t LIMIT = SLOTS / 4 * 3, ITEMS = LIMIT / THREADS;
+    static constexpr int MINB = MINB_;
+    static_assert(LIMIT + THREADS < SLOTS, "an empty slot must always remain");
+    static_assert(LIMIT % THREADS == 0, "extraction items per thread");
+};
+using BtSmall = BtCfg<512, 12, 2>;   // 4096 slots, two CTAs per SM
+using BtLarge = BtCfg<1024, 13, 1>;  // 8192 slots, one CTA per SM
+constexpr int BT_STACK = 136;        // pending key ranges (2 per split level, 128-bit ranges)
 constexpr uint32_t BT_LOG2_NSUB = 10, BT_NSUB = 1u << BT_LOG2_NSUB;  // sub-buckets of the kept keys
-constexpr uint32_t BT_SUB_SORT = 32;               // largest sub-bucket sorted by insertion
-static_assert(2 * BT_NSUB * 4 <= BT_SLOTS * 2, "sub-bucket counters fit in the claim list");
-static_assert(BT_NSUB % BT_THREADS == 0, "sub-bucket scan");
-static_assert(BT_LIMIT + BT_THREADS < BT_SLOTS, "an empty slot must always remain");
-static_assert(BT_LIMIT % BT_THREADS == 0, "extraction items per thread");
+constexpr uint32_t BT_SUB_SORT = 32;  // largest sub-bucket sorted by insertion
 
 typedef unsigned __int128 u128;
 
@@ -46,11 +49,13 @@ template <> __device__ __forceinline__ uint64_t empty_key<uint64_t>() { return ~
 template <> __device__ __forceinline__ Key128 empty_key<Key128>() { return Key128{~0ull, ~0ull}; }
 // A canonical key is never all ones: min(x, rc(x)) of the all-T string is the all-A string.
 
+template <uint32_t LOG2>
 __device__ __forceinline__ uint32_t slot_hash(uint64_t k) {
-    return (uint32_t)((k * 0x9e3779b97f4a7c15ull) >> (64 - BT_LOG2));
+    return (uint32_t)((k * 0x9e3779b97f4a7c15ull) >> (64 - LOG2));
 }
+template <uint32_t LOG2>
 __device__ __forceinline__ uint32_t slot_hash(Key128 k) {
-    return (uint32_t)(((k.hi * 0xc2b2ae3d27d4eb4full) ^ k.lo) * 0x9e3779b97f4a7c15ull >> (64 - BT_LOG2));
+    return (uint32_t)(((k.hi * 0xc2b2ae3d27d4eb4full) ^ k.lo) * 0x9e3779b97f4a7c15ull >> (64 - LOG2));
 }
 
 // Shared-memory compare-and-swap of a whole key; returns the previous value.
@@ -140,31 +145,31 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan_u64(const unsigned long l
     if (threadIdx.x == 0) out[n] = s_carry;
 }
 
-template <class K>
+template <class K, class C>
 struct BucketSmem {
-    K key[BT_SLOTS];
-    uint32_t count[BT_SLOTS];
-    uint16_t list[BT_SLOTS];  // claimed slots in claim order
+    K key[C::SLOTS];
+    uint32_t count[C::SLOTS];
+    uint16_t list[C::SLOTS];  // claimed slots in claim order
     u128 lo[BT_STACK], hi[BT_STACK];
-    uint32_t warp_sums[BT_THREADS / 32];
-    K wmin[BT_THREADS / 32], wmax[BT_THREADS / 32];
+    uint32_t warp_sums[C::THREADS / 32];
+    K wmin[C::THREADS / 32], wmax[C::THREADS / 32];
     uint32_t distinct, overflow, top, bucket, n_rep, sub_max;
     unsigned long long out_at, n_distinct;
 };
 
 // Insert one candidate: claim its slot or add to the slot that holds it. Gives up (returns) once
 // the table has been declared over its limit for this attempt.
-template <class K>
-__device__ __forceinline__ void bt_insert(BucketSmem<K> &sm, K key, uint32_t *err) {
+template <class K, class C>
+__device__ __forceinline__ void bt_insert(BucketSmem<K, C> &sm, K key, uint32_t *err) {
     const K E = empty_key<K>();
-    uint32_t h = slot_hash(key);
-    for (uint32_t probe = 0; probe < BT_SLOTS; probe++) {
+    uint32_t h = slot_hash<C::LOG2>(key);
+    for (uint32_t probe = 0; probe < C::SLOTS; probe++) {
         if (*(volatile uint32_t *)&sm.overflow) return;
         const K old = cas_key(&sm.key[h], E, key);
         if (KeyT<K>::eq(old, E)) {  // claimed a new slot
             const uint32_t d = atomicAdd(&sm.distinct, 1u);
-            sm.list[d] = (uint16_t)h;  // d < BT_LIMIT + BT_THREADS < BT_SLOTS
-            if (d + 1 >= BT_LIMIT) sm.overflow = 1;
+            sm.list[d] = (uint16_t)h;  // d < C::LIMIT + C::THREADS < C::SLOTS
+            if (d + 1 >= C::LIMIT) sm.overflow = 1;
             atomicAdd(&sm.count[h], 1u);
             return;
         }
@@ -172,15 +177,15 @@ __device__ __forceinline__ void bt_insert(BucketSmem<K> &sm, K key, uint32_t *er
             if (atomicAdd(&sm.count[h], 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
             return;
         }
-        h = (h + 1) & (BT_SLOTS - 1);
+        h = (h + 1) & (C::SLOTS - 1);
     }
 }
 
 // One CTA at a time per bucket, taken in ticket order. Bucket b's candidates are
 // cand[off_c[b] .. off_c[b+1]), its first sightings first[off_f[b] .. off_f[b+1]). Output: the
 // bucket's kept keys, ascending, with counts, at tmp_* + off_c[b]; their number at n_rep[b].
-template <class K>
-__global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restrict__ cand,
+template <class K, class C>
+__global__ __launch_bounds__(C::THREADS, C::MINB) void k_bucket_count(const K *__restrict__ cand,
                                                                  const unsigned long long *__restrict__ off_c,
                                                                  const K *__restrict__ first,
                                                                  const unsigned long long *__restrict__ off_f,
@@ -190,8 +195,10 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                                                                  unsigned long long *__restrict__ n_rep,
                                                                  uint32_t *ticket, unsigned long long *n_distinct,
                                                                  uint32_t *err) {
+    static_assert(BT_NSUB % C::THREADS == 0, "sub-bucket scan");
+    static_assert(2 * BT_NSUB * 4 <= C::SLOTS * 2, "sub-bucket counters fit in the claim list");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    BucketSmem<K> &sm = *reinterpret_cast<BucketSmem<K> *>(smem_raw);
+    BucketSmem<K, C> &sm = *reinterpret_cast<BucketSmem<K, C> *>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const K E = empty_key<K>();
     if (tid == 0) sm.n_distinct = 0;
@@ -213,7 +220,7 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
         while (sm.top > 0) {  // uniform: every thread reads top after the same barrier
             const u128 lo = sm.lo[sm.top - 1], hi = sm.hi[sm.top - 1];
             __syncthreads();
-            for (uint32_t i = tid; i < BT_SLOTS; i += BT_THREADS) {
+            for (uint32_t i = tid; i < C::SLOTS; i += C::THREADS) {
                 sm.key[i] = E;
                 sm.count[i] = 0;
             }
@@ -225,10 +232,10 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
             }
             __syncthreads();
             // candidates of this key range -> table
-            for (uint64_t i = c0 + tid; i < c1; i += 4 * BT_THREADS) {
+            for (uint64_t i = c0 + tid; i < c1; i += 4 * C::THREADS) {
                 K kk[4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) kk[j] = i + j * BT_THREADS < c1 ? cand[i + j * BT_THREADS] : E;
+                for (int j = 0; j < 4; j++) kk[j] = i + j * C::THREADS < c1 ? cand[i + j * C::THREADS] : E;
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const u128 v = as_u128(kk[j]);
@@ -242,7 +249,7 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 if (!narrowed) {  // first split: shrink to the bucket's own key span
                     K mn = E, mx = K{};
                     bool any = false;
-                    for (uint64_t i = c0 + tid; i < c1; i += BT_THREADS) {
+                    for (uint64_t i = c0 + tid; i < c1; i += C::THREADS) {
                         const K x = cand[i];
                         if (!any || KeyT<K>::lt(x, mn)) mn = x;
                         if (!any || KeyT<K>::lt(mx, x)) mx = x;
@@ -263,7 +270,7 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                     }
                     __syncthreads();
                     if (tid == 0) {
-                        for (uint32_t w = 1; w < BT_THREADS / 32; w++) {
+                        for (uint32_t w = 1; w < C::THREADS / 32; w++) {
                             if (KeyT<K>::lt(sm.wmin[w], sm.wmin[0])) sm.wmin[0] = sm.wmin[w];
                             if (KeyT<K>::lt(sm.wmax[0], sm.wmax[w])) sm.wmax[0] = sm.wmax[w];
                         }
@@ -291,29 +298,29 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 continue;
             }
             // first sightings of this key range: +1 for keys that are candidates too
-            for (uint64_t i = f0 + tid; i < f1; i += BT_THREADS) {
+            for (uint64_t i = f0 + tid; i < f1; i += C::THREADS) {
                 const K x = first[i];
                 const u128 v = as_u128(x);
                 if (v < lo || v > hi) continue;
-                uint32_t h = slot_hash(x);
-                for (uint32_t probe = 0; probe < BT_SLOTS; probe++) {
+                uint32_t h = slot_hash<C::LOG2>(x);
+                for (uint32_t probe = 0; probe < C::SLOTS; probe++) {
                     const K y = sm.key[h];
                     if (KeyT<K>::eq(y, x)) {
                         if (atomicAdd(&sm.count[h], 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
                         break;
                     }
                     if (KeyT<K>::eq(y, E)) break;
-                    h = (h + 1) & (BT_SLOTS - 1);
+                    h = (h + 1) & (C::SLOTS - 1);
                 }
             }
             __syncthreads();
             // keep count >= min_count: gather to registers, then rewrite the arrays as a dense list
             const uint32_t nd = sm.distinct;
-            K ik[BT_ITEMS];
-            uint32_t ic[BT_ITEMS], kept = 0;
+            K ik[C::ITEMS];
+            uint32_t ic[C::ITEMS], kept = 0;
 #pragma unroll
-            for (uint32_t j = 0; j < BT_ITEMS; j++) {
-                const uint32_t e = tid + j * BT_THREADS;
+            for (uint32_t j = 0; j < C::ITEMS; j++) {
+                const uint32_t e = tid + j * C::THREADS;
                 ic[j] = 0;
                 if (e < nd) {
                     const uint32_t h = sm.list[e];
@@ -324,7 +331,7 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 }
             }
             uint32_t total;
-            uint32_t pos = block_exclusive_scan<BT_THREADS>(kept, sm.warp_sums, &total);
+            uint32_t pos = block_exclusive_scan<C::THREADS>(kept, sm.warp_sums, &total);
             // Sort the kept keys. Common case: sub-buckets by the leading bits of (key - min) (counting
             // sort), then an insertion sort inside each (a few keys). Skewed keys: bitonic sort.
             uint32_t *sub_cnt = reinterpret_cast<uint32_t *>(sm.list);  // the claim list is no longer needed
@@ -332,7 +339,7 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
             {
                 K mn = E, mx = K{};
 #pragma unroll
-                for (uint32_t j = 0; j < BT_ITEMS; j++)
+                for (uint32_t j = 0; j < C::ITEMS; j++)
                     if (ic[j]) {
                         if (KeyT<K>::lt(ik[j], mn)) mn = ik[j];
                         if (KeyT<K>::lt(mx, ik[j])) mx = ik[j];
@@ -346,11 +353,11 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                     sm.wmin[warp] = mn;
                     sm.wmax[warp] = mx;
                 }
-                for (uint32_t d = tid; d < BT_NSUB; d += BT_THREADS) sub_cnt[d] = 0;
+                for (uint32_t d = tid; d < BT_NSUB; d += C::THREADS) sub_cnt[d] = 0;
                 if (tid == 0) sm.sub_max = 0;
                 __syncthreads();
                 if (tid == 0) {
-                    for (uint32_t w = 1; w < BT_THREADS / 32; w++) {
+                    for (uint32_t w = 1; w < C::THREADS / 32; w++) {
                         if (KeyT<K>::lt(sm.wmin[w], sm.wmin[0])) sm.wmin[0] = sm.wmin[w];
                         if (KeyT<K>::lt(sm.wmax[0], sm.wmax[w])) sm.wmax[0] = sm.wmax[w];
                     }
@@ -362,9 +369,9 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
             const int span_bits = (uint64_t)(span >> 64) ? 128 - __clzll((long long)(uint64_t)(span >> 64))
                                                           : 64 - __clzll((long long)(uint64_t)span);
             const int sub_shift = span_bits > BT_LOG2_NSUB ? span_bits - BT_LOG2_NSUB : 0;
-            uint32_t packed[BT_ITEMS];  // sub-bucket | rank inside it << BT_LOG2_NSUB
+            uint32_t packed[C::ITEMS];  // sub-bucket | rank inside it << BT_LOG2_NSUB
 #pragma unroll
-            for (uint32_t j = 0; j < BT_ITEMS; j++)
+            for (uint32_t j = 0; j < C::ITEMS; j++)
                 if (ic[j]) {
                     const uint32_t d = (uint32_t)((as_u128(ik[j]) - kmin) >> sub_shift);
                     const uint32_t r = atomicAdd(&sub_cnt[d], 1u);
@@ -373,14 +380,14 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 }
             __syncthreads();
             if (sm.sub_max == 0) {
-                constexpr uint32_t PER = BT_NSUB / BT_THREADS;
+                constexpr uint32_t PER = BT_NSUB / C::THREADS;
                 uint32_t v[PER], sum = 0;
 #pragma unroll
                 for (uint32_t q = 0; q < PER; q++) {
                     v[q] = sub_cnt[tid * PER + q];
                     sum += v[q];
                 }
-                uint32_t run = block_exclusive_scan<BT_THREADS>(sum, sm.warp_sums, nullptr);
+                uint32_t run = block_exclusive_scan<C::THREADS>(sum, sm.warp_sums, nullptr);
 #pragma unroll
                 for (uint32_t q = 0; q < PER; q++) {
                     sub_off[tid * PER + q] = run;
@@ -388,14 +395,14 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 }
                 __syncthreads();
 #pragma unroll
-                for (uint32_t j = 0; j < BT_ITEMS; j++)
+                for (uint32_t j = 0; j < C::ITEMS; j++)
                     if (ic[j]) {
                         const uint32_t d = packed[j] & (BT_NSUB - 1), dst = sub_off[d] + (packed[j] >> BT_LOG2_NSUB);
                         sm.key[dst] = ik[j];
                         sm.count[dst] = ic[j];
                     }
                 __syncthreads();
-                for (uint32_t d = tid; d < BT_NSUB; d += BT_THREADS) {
+                for (uint32_t d = tid; d < BT_NSUB; d += C::THREADS) {
                     const uint32_t a = sub_off[d], m = sub_cnt[d];
                     for (uint32_t x = 1; x < m; x++) {
                         const K key = sm.key[a + x];
@@ -415,21 +422,21 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 uint32_t N = 1;
                 while (N < total) N <<= 1;
 #pragma unroll
-                for (uint32_t j = 0; j < BT_ITEMS; j++)
+                for (uint32_t j = 0; j < C::ITEMS; j++)
                     if (ic[j]) {
                         sm.key[pos] = ik[j];
                         sm.count[pos] = ic[j];
                         pos++;
                     }
-                for (uint32_t i = total + tid; i < N; i += BT_THREADS) {
+                for (uint32_t i = total + tid; i < N; i += C::THREADS) {
                     sm.key[i] = E;
                     sm.count[i] = 0;
                 }
                 __syncthreads();
-                // bitonic sort of the kept keys (N <= BT_SLOTS)
+                // bitonic sort of the kept keys (N <= C::SLOTS)
                 for (uint32_t size = 2; size <= N; size <<= 1) {
                     for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-                        for (uint32_t t = tid; t < N / 2; t += BT_THREADS) {
+                        for (uint32_t t = tid; t < N / 2; t += C::THREADS) {
                             const uint32_t i = 2 * t - (t & (stride - 1)), j = i + stride;
                             const bool up = (i & size) == 0;
                             const K a = sm.key[i], c = sm.key[j];
@@ -446,7 +453,7 @@ __global__ __launch_bounds__(BT_THREADS, 2) void k_bucket_count(const K *__restr
                 }
             }
             const uint64_t at = c0 + sm.out_at;
-            for (uint32_t i = tid; i < total; i += BT_THREADS) {
+            for (uint32_t i = tid; i < total; i += C::THREADS) {
                 tmp_keys[at + i] = sm.key[i];
                 tmp_counts[at + i] = sm.count[i];
             }
@@ -490,17 +497,30 @@ void launch_scan_u64(const LaunchCfg &c, const unsigned long long *in, uint64_t 
     k_scan_u64<<<1, SCAN_THREADS, 0, c.stream>>>(in, n, out);
 }
 
+template <class K, class C>
+static void bucket_count_cfg(const LaunchCfg &c, const K *cand, const unsigned long long *off_c, const K *first,
+                             const unsigned long long *off_f, uint32_t B, uint32_t min_count, K *tmp_keys,
+                             uint32_t *tmp_counts, unsigned long long *n_rep, uint32_t *ticket,
+                             unsigned long long *n_distinct, uint32_t *err) {
+    const size_t smem = sizeof(BucketSmem<K, C>);  // above the 48 KB default: opt in (per device, cheap)
+    cudaFuncSetAttribute(k_bucket_count<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned grid = (unsigned)std::min<uint64_t>(B, (uint64_t)c.sms * C::MINB);
+    k_bucket_count<K, C><<<grid, C::THREADS, smem, c.stream>>>(cand, off_c, first, off_f, B, min_count, tmp_keys,
+                                                                 tmp_counts, n_rep, ticket, n_distinct, err);
+}
+
 template <class K>
 void launch_bucket_count(const LaunchCfg &c, const K *cand, const unsigned long long *off_c, const K *first,
                          const unsigned long long *off_f, uint32_t B, uint32_t min_count, K *tmp_keys,
                          uint32_t *tmp_counts, unsigned long long *n_rep, uint32_t *ticket,
-                         unsigned long long *n_distinct, uint32_t *err) {
+                         unsigned long long *n_distinct, uint32_t *err, int large) {
     if (!B) return;
-    const size_t smem = sizeof(BucketSmem<K>);  // above the 48 KB default: opt in (per device, cheap)
-    cudaFuncSetAttribute(k_bucket_count<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const unsigned grid = (unsigned)std::min<uint64_t>(B, (uint64_t)c.sms * 2);
-    k_bucket_count<K><<<grid, BT_THREADS, smem, c.stream>>>(cand, off_c, first, off_f, B, min_count, tmp_keys,
-                                                             tmp_counts, n_rep, ticket, n_distinct, err);
+    if (large)
+        bucket_count_cfg<K, BtLarge>(c, cand, off_c, first, off_f, B, min_count, tmp_keys, tmp_counts, n_rep, ticket,
+                                     n_distinct, err);
+    else
+        bucket_count_cfg<K, BtSmall>(c, cand, off_c, first, off_f, B, min_count, tmp_keys, tmp_counts, n_rep, ticket,
+                                     n_distinct, err);
 }
 
 template <class K>
@@ -517,7 +537,7 @@ void launch_bucket_gather(const LaunchCfg &c, const K *tmp_keys, const uint32_t 
                                           unsigned long long *);                                                   \
     template void launch_bucket_count<K>(const LaunchCfg &, const K *, const unsigned long long *, const K *,      \
                                          const unsigned long long *, uint32_t, uint32_t, K *, uint32_t *,          \
-                                         unsigned long long *, uint32_t *, unsigned long long *, uint32_t *);      \
+                                         unsigned long long *, uint32_t *, unsigned long long *, uint32_t *, int); \
     template void launch_bucket_gather<K>(const LaunchCfg &, const K *, const uint32_t *,                          \
                                           const unsigned long long *, const unsigned long long *, uint32_t, K *,   \
                                           uint32_t *);

@@ -7,11 +7,17 @@ namespace turtle {
 
 // ((f(v) - f_lo) >> shift) clamped to [0, n_buckets), v = top 31 bits of the 2k-bit key,
 // f(v) = v (2^32 - v): monotone in the key, so buckets are consecutive key ranges, and about
-// equally full for the canonical keys of random sequence.
+// equally full for the canonical keys of random sequence. Tagged keys (batches) first select
+// their library's range of buckets; tags are the most significant key bits, so the order holds.
 template <class K>
 __device__ __forceinline__ uint32_t bucket_of(K key, const BucketGeom &g) {
     const uint64_t v = top31(key, g.k);
     const uint64_t f = v * ((1ull << 32) - v);
+    if (g.lib) {
+        const uint4 e = __ldg(g.lib + tag_of(key, g.tag_shift));
+        const uint64_t b = f >> e.z;
+        return e.x + (b < e.y ? (uint32_t)b : e.y - 1);
+    }
     const uint64_t b = f >= g.f_lo ? (f - g.f_lo) >> g.shift : 0;
     return b < g.n_buckets ? (uint32_t)b : g.n_buckets - 1;
 }

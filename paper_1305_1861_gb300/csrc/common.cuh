@@ -110,15 +110,16 @@ template <> __device__ __forceinline__ Key128 canonical<Key128>(const uint64_t *
 // u(2 - u) equals f(v) / 2^62: equal slices of f hold about equal numbers of keys.
 // Part p of 2^bits takes the keys with f(v) >> (62 - bits) == p; since f is
 // monotone, parts are ordered key ranges.
+// (Bits above the 2k key bits, i.e. a batch's library tag, are masked off.)
 __device__ __forceinline__ uint64_t top31(uint64_t key, int k) {
     const int b = 2 * k;
-    return b >= 31 ? key >> (b - 31) : key << (31 - b);
+    return (b >= 31 ? key >> (b - 31) : key << (31 - b)) & 0x7fffffffull;
 }
 __device__ __forceinline__ uint64_t top31(Key128 key, int k) {
     const int b = 2 * k;  // 66..128 bits: the top 31 start inside hi or straddle hi/lo
     const int sh = b - 31;
-    if (sh >= 64) return key.hi >> (sh - 64);
-    return (key.hi << (64 - sh)) | (key.lo >> sh);
+    if (sh >= 64) return (key.hi >> (sh - 64)) & 0x7fffffffull;
+    return ((key.hi << (64 - sh)) | (key.lo >> sh)) & 0x7fffffffull;
 }
 template <class K>
 __device__ __forceinline__ uint32_t key_part(K key, int k, int part_bits) {

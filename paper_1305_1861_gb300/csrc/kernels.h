@@ -26,12 +26,15 @@ struct PackLayout {
 
 // Bucket of a key (bucketed sort-and-compact): ((f(top31(key)) - f_lo) >> shift), clamped to
 // [0, n_buckets), with the monotone map f(v) = v (2^32 - v) of the key-range parts: buckets are
-// consecutive key ranges.
+// consecutive key ranges. Batches (lib != null): library l = the key's tag owns the buckets
+// [lib[l].x, lib[l].x + lib[l].y), indexed by f >> lib[l].z.
 struct BucketGeom {
     uint64_t f_lo;
     int shift;
     uint32_t n_buckets;
     int k;
+    int tag_shift;
+    const uint4 *lib;
 };
 
 struct LaunchCfg {
@@ -160,7 +163,7 @@ void launch_threshold(const LaunchCfg &c, const K *unique, uint64_t n_unique, co
 // Stable sort of keys[0 .. n) by bucket index (8 bits per onesweep pass); returns keys or s.alt.
 template <class K>
 K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom &g, int bits, const SortScratch &s,
-                      uint32_t *err, int *passes_run, bool hist_ready);
+                      uint32_t *err, int *passes_run, bool hist_ready, int variant = 0);
 // off[b] <- first position of bucket b in bucket-sorted keys, b = 0 .. n_buckets (off[n_buckets] = n).
 template <class K>
 void launch_bucket_bounds(const LaunchCfg &c, const K *keys, uint64_t n, const BucketGeom &g,
@@ -173,7 +176,7 @@ template <class K>
 void launch_bucket_count(const LaunchCfg &c, const K *cand, const unsigned long long *off_c, const K *first,
                          const unsigned long long *off_f, uint32_t B, uint32_t min_count, K *tmp_keys,
                          uint32_t *tmp_counts, unsigned long long *n_rep, uint32_t *ticket,
-                         unsigned long long *n_distinct, uint32_t *err);
+                         unsigned long long *n_distinct, uint32_t *err, int large = 0);
 // Dense output: bucket b's n_rep entries from tmp_*[off[b] ..] to out[out_off[b] ..].
 template <class K>
 void launch_bucket_gather(const LaunchCfg &c, const K *tmp_keys, const uint32_t *tmp_counts,

@@ -220,12 +220,13 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
 // bucket. Returns the buffer holding the result (keys or s.alt).
 template <class K>
 K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom &g, int bits, const SortScratch &s,
-                      uint32_t *err, int *passes_run, bool hist_ready) {
+                      uint32_t *err, int *passes_run, bool hist_ready, int variant) {
     const int passes = (bits + 7) / 8;
     if (passes_run) *passes_run = 0;
     if (n <= 1 || passes == 0) return keys;
+    if (variant < 0 || variant > 2) variant = 0;
     const BucketDigit<K> dig{g};
-    const uint64_t TILE = (uint64_t)S_BLOCK * SortCfg<K>::V_ITEMS[0];
+    const uint64_t TILE = (uint64_t)S_BLOCK * SortCfg<K>::V_ITEMS[variant];
     const uint64_t tiles = (n + TILE - 1) / TILE;
     cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
     cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
@@ -238,8 +239,10 @@ K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom 
     k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
     K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
     for (int p = 0; p < passes; p++) {
-        onesweep_pass<K, 0, BucketDigit<K>>(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback,
-                                            s.tile_ctr + p, (uint32_t)(p + 1), err, dig);
+        auto pass = variant == 0 ? onesweep_pass<K, 0, BucketDigit<K>>
+                                 : (variant == 1 ? onesweep_pass<K, 1, BucketDigit<K>> : onesweep_pass<K, 2, BucketDigit<K>>);
+        pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err,
+             dig);
         if (passes_run) (*passes_run)++;
         K *t = src;
         src = dst;
@@ -354,9 +357,9 @@ template uint64_t *launch_radix_sort<uint64_t>(const LaunchCfg &, uint64_t *, ui
 template Key128 *launch_radix_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, int, const SortScratch &, uint32_t *,
                                            bool, uint32_t, int *, int);
 template uint64_t *launch_bucket_sort<uint64_t>(const LaunchCfg &, uint64_t *, uint64_t, const BucketGeom &, int,
-                                                const SortScratch &, uint32_t *, int *, bool);
+                                                const SortScratch &, uint32_t *, int *, bool, int);
 template Key128 *launch_bucket_sort<Key128>(const LaunchCfg &, Key128 *, uint64_t, const BucketGeom &, int,
-                                            const SortScratch &, uint32_t *, int *, bool);
+                                            const SortScratch &, uint32_t *, int *, bool, int);
 template void launch_rle<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, uint64_t *, uint64_t *,
                                    unsigned long long *, uint64_t *, uint32_t *, uint32_t *);
 template void launch_rle<Key128>(const LaunchCfg &, const Key128 *, uint64_t, Key128 *, uint64_t *,

@@ -16,7 +16,9 @@ def _lib(seed, G, cov, R, k, m, err=0.01):
     return (b, o, k, m)
 
 
-def test_batch_matches_oracle_per_library(have_gpu):
+@pytest.mark.parametrize("compact", [0, 1])
+def test_batch_matches_oracle_per_library(have_gpu, compact):
+    """Both forms of sort-and-compact (bucketed: per-library bucket ranges; global: recount table)."""
     import paper_1305_1861_gb300 as pkg
 
     jobs = []
@@ -31,7 +33,7 @@ def test_batch_matches_oracle_per_library(have_gpu):
     jobs.append((np.zeros(0, np.uint8), np.zeros(1, np.uint64), 21, 2))  # empty library
     b, o = brute.pack(["ACGT" * 30, "NNACGTACGTAAAATTTT" * 5])
     jobs.append((np.concatenate([np.frombuffer(b"TTT", np.uint8), b]), o + 3, 21, 2))  # offsets start past 0
-    got = pkg.turtle_count_batch(jobs)
+    got = pkg.turtle_count_batch(jobs, pkg.Params.default(compact=compact))
     assert len(got) == len(jobs)
     for (b, o, k, m), (keys, counts, nw) in zip(jobs, got):
         ok, oc, onw = oracle.count(b, o, k, m)

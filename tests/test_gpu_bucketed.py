@@ -25,23 +25,29 @@ def ctx(have_gpu):
     c.close()
 
 
-def _run(ctx, bases, offs, k, min_count, compact):
+# (compact, bucket_slots, sort_tile): bucketed with both table sizes and two tile shapes, and global
+FORMS = [(0, 0, 0), (0, 8192, 3), (1, 0, 0)]
+
+
+def _run(ctx, bases, offs, k, min_count, form):
     import torch
     import paper_1305_1861_gb300 as pkg
 
+    compact, slots, tile = form
     b = torch.from_numpy(np.ascontiguousarray(bases)).cuda()
     o = torch.from_numpy(np.ascontiguousarray(offs).astype(np.int64)).cuda()
-    keys, counts, nw = ctx.turtle_count_device(b, o, k, min_count, pkg.Params.default(compact=compact))
+    p = pkg.Params.default(compact=compact, bucket_slots=slots, sort_tile=tile)
+    keys, counts, nw = ctx.turtle_count_device(b, o, k, min_count, p)
     return keys.cpu().numpy().astype(np.uint64), counts.cpu().numpy().astype(np.uint64), nw, ctx.stats()
 
 
 def _check(ctx, bases, offs, k, min_count):
     ok, oc, onw = oracle.count(bases, offs, k, min_count)
-    for compact in (0, 1):
-        gk, gc, nw, st = _run(ctx, bases, offs, k, min_count, compact)
+    for form in FORMS:
+        gk, gc, nw, st = _run(ctx, bases, offs, k, min_count, form)
         assert nw == onw
-        assert gk.shape == ok.shape and np.array_equal(gk, ok), compact
-        assert np.array_equal(gc, oc), compact
+        assert gk.shape == ok.shape and np.array_equal(gk, ok), form
+        assert np.array_equal(gc, oc), form
     return ok, oc
 
 
