@@ -61,7 +61,9 @@ extern "C" {
 typedef struct {
     uint32_t struct_size;          /* sizeof(turtle_params); set by turtle_params_default */
     float filter_bits_per_window;  /* Bloom filter bits per valid window (rounded up to a power of two
-                                      number of 32-byte sectors); default 4 */
+                                      number of 32-byte sectors); default 1: a small filter stays partly
+                                      in L2, and the few extra false-positive candidates cost less
+                                      than the DRAM lines a larger filter's probes would move */
     uint32_t pattern_bits;         /* bits per precomputed pattern (1..64); default 4 */
     uint32_t n_patterns;           /* pattern-table entries, power of two, 1..4096; default 1024 */
     uint64_t pattern_seed;         /* SplitMix64 seed of the pattern table */
@@ -95,10 +97,10 @@ typedef struct {
                                       min_count are dropped and the rest sorted. 1 = global: LSD radix sort
                                       of all candidates, run-length compaction, recount table, threshold.
                                       Both are exact. recount_windows = 1 uses the global form. */
-    uint32_t bucket_slots;         /* bucketed form: shared-memory table of one bucket CTA, 0 = 4096 slots
-                                      (512 threads, two CTAs per SM; default), 8192 = 8192 slots (1024
-                                      threads, one CTA per SM: twice the distinct keys per bucket before a
-                                      bucket is split) */
+    uint32_t bucket_slots;         /* bucketed form: shared-memory table of one bucket CTA: 0 or 8192 =
+                                      8192 slots (1024 threads, one CTA per SM; default), 4096 = 4096 slots
+                                      (512 threads, two CTAs per SM; half the distinct keys per bucket
+                                      before a bucket is split) */
     uint32_t reserved;
 } turtle_params;
 

@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <unistd.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -89,10 +91,8 @@ struct turtle_ctx {
     cudaEvent_t ev[2 * TURTLE_STAGE_COUNT] = {};
     turtle_stats stats{};
     uint64_t scratch_bytes = 0;
-    // streamed input: two pinned host buffers, a copy stream and their events
+    // streamed input: a copy stream and the events that order it with the packing stream
     cudaStream_t copy_stream = nullptr;
-    void *pinned[2] = {nullptr, nullptr};
-    size_t pinned_bytes = 0;
     cudaEvent_t ev_h2d[2] = {}, ev_packed[2] = {};
 };
 
@@ -240,13 +240,19 @@ struct PartOut {
 // bucket merge + first-sighting recount + threshold + sort, then a dense gather.
 constexpr uint64_t BUCKET_WINDOWS = 16384;  // candidates + first sightings per bucket, about
 
-// Buckets for n_all windows of the key range [part_lo, part_hi) of 2^part_bits parts; *bits = index
-// bits (8 per sort pass). A lone 9th or 17th bit would cost a whole pass: it is dropped instead
-// (buckets twice as full).
+// Bucket-index bits actually used, given the bits wanted: 8 per sort pass, and one or two bits
+// beyond a multiple of 8 are dropped rather than paid for with a whole extra pass (buckets up to
+// four times fuller).
+int bucket_bits_for(int want) {
+    if (want > 8 && (want % 8 == 1 || want % 8 == 2)) return want - want % 8;
+    return want < 24 ? want : 24;
+}
+
+// Buckets for n_all windows of the key range [part_lo, part_hi) of 2^part_bits parts; *bits = index bits.
 BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int part_bits, int k, int *bits) {
     int b = 0;
     while (b < 24 && (n_all >> b) > BUCKET_WINDOWS) b++;
-    if (b % 8 == 1) b--;
+    b = bucket_bits_for(b);
     BucketGeom bg{};
     bg.k = k;
     bg.f_lo = (uint64_t)part_lo << (62 - part_bits);
@@ -256,6 +262,30 @@ BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int p
     bg.n_buckets = (uint32_t)(((span - 1) >> bg.shift) + 1);  // <= 2^b
     *bits = b;
     return bg;
+}
+
+// Batch: library l gets 2^b[l] buckets for its lib_w[l] windows; the total is capped the same way
+// (the largest libraries give up bits first). Returns the index bits of the total.
+int batch_bucket_bits(const std::vector<unsigned long long> &lib_w, std::vector<int> &b) {
+    const size_t n = lib_w.size();
+    b.assign(n, 0);
+    uint64_t total = 0;
+    for (size_t l = 0; l < n; l++) {
+        while (b[l] < 20 && (lib_w[l] >> b[l]) > BUCKET_WINDOWS) b[l]++;
+        total += (uint64_t)1 << b[l];
+    }
+    int want = 0;
+    while (((uint64_t)1 << want) < total) want++;
+    const int bits = bucket_bits_for(want);
+    while (total > ((uint64_t)1 << bits)) {
+        size_t big = 0;
+        for (size_t l = 1; l < n; l++)
+            if (b[l] > b[big]) big = l;
+        if (b[big] == 0) break;  // cannot happen: n libraries <= 2^bits
+        total -= (uint64_t)1 << (b[big] - 1);
+        b[big]--;
+    }
+    return bits;
 }
 
 template <class K>
@@ -381,11 +411,23 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     // Super-partitions (key routing, Sec. 2.1.5): when the post-filter working set of all windows does
     // not fit in free device memory, split the key space into consecutive key ranges and run the rest
     // of the path once per range; outputs are appended in key order.
-    // candidates + first sightings share one buffer; sort buffer; run starts and lengths; filter; table
-    const double bytes_per_window = 2.0 * sizeof(K) + 12.0 + (use_filter ? prm.filter_bits_per_window / 8.0 : 0.0) +
-                                    8.0;
+    // Working set per window of a range. Bucketed: candidates + first sightings share one buffer, the
+    // bucket sort's second buffer, per-candidate result counts, filter, a share of the output.
+    // Global: the same two buffers, run starts and lengths, recount table, filter.
+    // the bucketed form of sort-and-compact; the window-recount mode uses the global form
+    const bool bucketed = prm.compact == 0 && (firsts_mode || !use_filter);
+    const double filter_bpw = use_filter ? prm.filter_bits_per_window / 8.0 : 0.0;
+    const double bytes_per_window = bucketed ? 2.0 * sizeof(K) + 8.0 + filter_bpw
+                                                  : 2.0 * sizeof(K) + 20.0 + filter_bpw;
+    // free device memory, plus what this context's pool holds unused from earlier calls
     size_t free_b = 0, total_b = 0;
     ck(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t pool_reserved = 0, pool_used = 0;
+    if (cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &pool_reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &pool_used) == cudaSuccess &&
+        pool_reserved > pool_used)
+        free_b += pool_reserved - pool_used;
+    cudaGetLastError();
     const double budget = prm.budget_mib ? (double)prm.budget_mib * (1 << 20) : 0.8 * (double)free_b;
     constexpr int PART_BITS = 6;
     std::vector<std::pair<uint32_t, uint32_t>> groups;  // [part_lo, part_hi) of each super-partition
@@ -420,8 +462,6 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     }
     const bool parted = groups.size() > 1;
     st.super_partitions = (uint32_t)groups.size();
-    // the bucketed form of sort-and-compact; the window-recount mode uses the global form
-    const bool bucketed = prm.compact == 0 && (firsts_mode || !use_filter);
 
     std::vector<PartOut> outs;
     for (size_t g = 0; g < groups.size(); g++) {
@@ -463,13 +503,13 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         int bucket_bits = 0;
         BucketGeom bg{};
         if (bucketed && tag) {  // batch: each library its own range of buckets, sized by its windows
+            std::vector<int> lb;
+            bucket_bits = batch_bucket_bits(lib_w, lb);
             std::vector<uint4> lg(tag->n_libs);
             uint32_t at = 0;
             for (int l = 0; l < tag->n_libs; l++) {
-                int b = 0;
-                while (b < 20 && (lib_w[l] >> b) > BUCKET_WINDOWS) b++;
-                lg[l] = make_uint4(at, 1u << b, (uint32_t)(62 - b), 0u);
-                at += 1u << b;
+                lg[l] = make_uint4(at, 1u << lb[l], (uint32_t)(62 - lb[l]), 0u);
+                at += 1u << lb[l];
             }
             uint4 *d_lg = (uint4 *)ctx_alloc(c, sizeof(uint4) * lg.size(), s);
             ck(cudaMemcpyAsync(d_lg, lg.data(), sizeof(uint4) * lg.size(), cudaMemcpyHostToDevice, s));
@@ -477,7 +517,6 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             bg.n_buckets = at;
             bg.tag_shift = 2 * k;
             bg.lib = d_lg;
-            while (bucket_bits < 24 && ((uint64_t)1 << bucket_bits) < at) bucket_bits++;
         } else if (bucketed) {  // every window of the range becomes a candidate or a first sighting: Wg of them
             bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
                              PART_BITS, k, &bucket_bits);
@@ -504,7 +543,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, const_cast<K *>(first_keys), n_first, bg,
                                   bucket_bits, hist, !parted,
                                   prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
-                                  prm.bucket_slots == 8192, s);
+                                  prm.bucket_slots != 4096, s);
         } else {
         // a4: sort + compact
         SortScratch ss{};
@@ -726,95 +765,45 @@ int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, con
     }
 }
 
-// memcpy with several host threads (pageable source -> pinned staging buffer).
-void par_memcpy(void *dst, const void *src, size_t n) {
-    const int T = n >= ((size_t)32 << 20) ? 8 : n >= ((size_t)4 << 20) ? 4 : 1;
+// Host <-> device copies go straight from and to host memory, pageable or not: on a Grace-based
+// GPU the copy engines reach pageable memory through the CPU's page tables at about the rate of
+// page-locked memory (~200 GB/s over NVLink-C2C), faster than staging through a page-locked
+// buffer with host copies. Host pages that do not exist yet are the exception: the copy engine
+// would fault each one in, an order of magnitude slower, so a result buffer is first touched
+// page by page from several host threads.
+void copy_to_device(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+}
+
+void first_touch(void *p, size_t bytes) {
+    const size_t page = (size_t)sysconf(_SC_PAGESIZE);
+    const size_t pages = (bytes + page - 1) / page;
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = bytes < ((size_t)4 << 20) ? 1 : (int)std::min(16u, hw ? hw : 1u);
+    auto touch = [=](size_t a, size_t b) {
+        for (size_t i = a; i < b; i++) static_cast<volatile char *>(p)[i * page] = 0;
+    };
     if (T == 1) {
-        memcpy(dst, src, n);
+        touch(0, pages);
         return;
     }
     std::vector<std::thread> th;
-    for (int t = 0; t < T; t++) {
-        const size_t a = n * t / T, b = n * (t + 1) / T;
-        th.emplace_back([=]() { memcpy((char *)dst + a, (const char *)src + a, b - a); });
-    }
+    for (int t = 0; t < T; t++) th.emplace_back(touch, pages * t / T, pages * (t + 1) / T);
     for (auto &x : th) x.join();
 }
 
-// The context's two pinned staging buffers, at least `bytes` each.
-void ensure_pinned(turtle_ctx *c, size_t bytes) {
-    if (c->pinned_bytes >= bytes) return;
-    for (auto &pb : c->pinned)
-        if (pb) {
-            cudaFreeHost(pb);
-            pb = nullptr;
-        }
-    c->pinned_bytes = 0;
-    for (auto &pb : c->pinned) ck(cudaMallocHost(&pb, bytes));
-    c->pinned_bytes = bytes;
-}
-
-constexpr size_t STAGE_CHUNK = (size_t)64 << 20;
-
-// True when p lies in page-locked host memory the copy engines can read or write directly.
-bool is_pinned(const void *p) {
-    cudaPointerAttributes a{};
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeHost;
-}
-
-// Device -> pageable host through the pinned buffers: the DMA of chunk i overlaps the
-// multi-threaded host copy of chunk i-1. Synchronises s.
-void copy_to_host(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
-    if (!bytes) return;
-    if (bytes < ((size_t)1 << 20) || is_pinned(dst)) {  // small or already pinned: one plain copy
+// Into a freshly allocated host buffer. Synchronises s.
+void copy_to_host(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes) {
+        first_touch(dst, bytes);
         ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
-        ck(cudaStreamSynchronize(s));
-        return;
-    }
-    ensure_pinned(c, STAGE_CHUNK);
-    const size_t n = (bytes + STAGE_CHUNK - 1) / STAGE_CHUNK;
-    for (size_t i = 0; i <= n; i++) {
-        if (i < n) {
-            const size_t len = std::min(STAGE_CHUNK, bytes - i * STAGE_CHUNK);
-            ck(cudaMemcpyAsync(c->pinned[i & 1], (const char *)src + i * STAGE_CHUNK, len, cudaMemcpyDeviceToHost, s));
-            ck(cudaEventRecord(c->ev_h2d[i & 1], s));
-        }
-        if (i > 0) {
-            const size_t j = i - 1, len = std::min(STAGE_CHUNK, bytes - j * STAGE_CHUNK);
-            ck(cudaEventSynchronize(c->ev_h2d[j & 1]));
-            par_memcpy((char *)dst + j * STAGE_CHUNK, c->pinned[j & 1], len);
-        }
-    }
-}
-
-// Pageable host -> device through the pinned buffers (host copy of chunk i+1 overlaps the DMA of chunk i).
-void copy_to_device(turtle_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s) {
-    if (!bytes) return;
-    if (bytes < ((size_t)1 << 20) || is_pinned(src)) {
-        ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
-        return;
-    }
-    ensure_pinned(c, STAGE_CHUNK);
-    ck(cudaStreamSynchronize(s));  // both pinned buffers are free
-    const size_t n = (bytes + STAGE_CHUNK - 1) / STAGE_CHUNK;
-    for (size_t i = 0; i < n; i++) {
-        const int b = (int)(i & 1);
-        const size_t len = std::min(STAGE_CHUNK, bytes - i * STAGE_CHUNK);
-        if (i >= 2) ck(cudaEventSynchronize(c->ev_h2d[b]));  // its previous copy has left the buffer
-        par_memcpy(c->pinned[b], (const char *)src + i * STAGE_CHUNK, len);
-        ck(cudaMemcpyAsync((char *)dst + i * STAGE_CHUNK, c->pinned[b], len, cudaMemcpyHostToDevice, s));
-        ck(cudaEventRecord(c->ev_h2d[b], s));
     }
     ck(cudaStreamSynchronize(s));
 }
 
-// Stream host reads to the device in chunks through two pinned buffers: while chunk i is
-// copied host->device on the copy stream and packed on `s`, chunk i+1 is staged by the host.
-// Only the 2-bit codes and bitmaps stay on the device; the ASCII is never resident as a whole.
+// Stream host reads to the device in chunks: chunk i is copied host->device on the copy stream
+// while chunk i-1 is packed on `s` (two device staging buffers). Only the 2-bit codes and bitmaps
+// stay on the device; the ASCII is never resident as a whole.
 void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off,
                    size_t chunk, cudaStream_t s, PrePacked &pp, const LaunchCfg &lc) {
     const PackLayout L = PackLayout::of(n_bases);
@@ -823,24 +812,15 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
     pp.S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
     ck(cudaMemsetAsync(pp.S, 0, 8 * L.b_words, s));
     chunk = (chunk + 63) & ~(size_t)63;  // chunk starts fall on 64-position boundaries (whole bitmap words)
-    const bool direct = is_pinned(reads->bases);  // caller's memory is page-locked: DMA straight from it
-    if (!direct) ensure_pinned(c, chunk);
     uint8_t *stage[2];
     for (auto &st : stage) st = (uint8_t *)ctx_alloc(c, chunk, s);
     for (int i = 0; i < 2; i++) ck(cudaEventRecord(c->ev_packed[i], s));  // both staging buffers start free
-    for (int i = 0; i < 2; i++) ck(cudaEventRecord(c->ev_h2d[i], c->copy_stream));
     const uint64_t n_chunks = n_bases ? (n_bases + chunk - 1) / chunk : 0;
     for (uint64_t i = 0; i < n_chunks; i++) {
         const int b = (int)(i & 1);
         const uint64_t c0 = i * chunk, c1 = c0 + chunk < n_bases ? c0 + chunk : n_bases;
-        const char *src = reads->bases + c0;
-        if (!direct) {
-            ck(cudaEventSynchronize(c->ev_h2d[b]));  // the pinned buffer's previous copy has finished
-            par_memcpy(c->pinned[b], src, c1 - c0);
-            src = (const char *)c->pinned[b];
-        }
         ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0));  // its staging buffer was packed
-        ck(cudaMemcpyAsync(stage[b], src, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
+        ck(cudaMemcpyAsync(stage[b], reads->bases + c0, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
         ck(cudaEventRecord(c->ev_h2d[b], c->copy_stream));
         ck(cudaStreamWaitEvent(s, c->ev_h2d[b], 0));
         const uint64_t g0 = c0 / 32, g1 = i + 1 == n_chunks ? L.pack_groups() : c1 / 32;
@@ -851,7 +831,7 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
     launch_mark_starts(lc, d_off, reads->n_reads, L, pp.S, c->d_err);
 }
 
-// Host-memory input streamed through pinned double buffers, then the path on the packed reads.
+// Host-memory input streamed through two device staging buffers, then the path on the packed reads.
 int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off, int k,
                         uint32_t min_count, const turtle_params *params, size_t chunk, cudaStream_t s,
                         DeviceOut &o) {
@@ -876,11 +856,29 @@ int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bas
     }
 }
 
+// Copy-out of finished runs on host threads, overlapping the next runs on the GPU.
+struct BatchOutput {
+    cudaStream_t stream = nullptr;  // device -> host copies of every run
+    std::vector<std::thread> threads;
+    std::mutex mu;
+    int rc = TURTLE_OK;
+    void fail(int code) {
+        std::lock_guard<std::mutex> g(mu);
+        if (rc == TURTLE_OK) rc = code;
+    }
+    int join() {
+        for (auto &t : threads) t.join();
+        threads.clear();
+        return rc;
+    }
+};
+
 // One batched run: libraries `idx` (same k and min_count) concatenated on the device, counted by
-// one pipeline with library-tagged keys, results split back per library into outs[].
+// one pipeline with library-tagged keys, results split back per library into outs[] by a host
+// thread of bo, which also frees the run's device results.
 template <class K>
 int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, int tag_bits,
-              const turtle_params *params, cudaStream_t s, turtle_result *outs) {
+              const turtle_params *params, cudaStream_t s, turtle_result *outs, BatchOutput &bo) {
     const int k = jobs[idx[0]].k;
     const uint32_t min_count = jobs[idx[0]].min_count;
     const int n_libs = (int)idx.size();
@@ -930,25 +928,45 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         starts[n_libs] = o.n;
         for (int l = n_libs - 1; l >= 0; l--)
             if (starts[l] == ~0ull) starts[l] = starts[l + 1];  // no entries: an empty range
-        const int kw = sizeof(K) / 8;
-        for (int l = 0; l < n_libs; l++) {
-            turtle_result &r = outs[idx[l]];
-            r.k = k;
-            r.n = starts[l + 1] - starts[l];
-            r.n_windows = lib_windows[l];
-            r.keys = (uint64_t *)malloc(8 * kw * (r.n ? r.n : 1));
-            r.counts = (uint32_t *)malloc(4 * (r.n ? r.n : 1));
-            if (!r.keys || !r.counts) throw Fail{TURTLE_E_NOMEM};
-            if (r.n) {
-                copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, s);
-                copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, s);
-            }
-        }
-        ck(cudaStreamSynchronize(s));
+        // the device results now belong to the copy-out thread (the next run must not free them)
+        for (auto it = c->result.begin(); it != c->result.end();)
+            it = (*it == o.keys || *it == (void *)o.counts) ? c->result.erase(it) : it + 1;
         ctx_end(c, s);
+        std::vector<size_t> lib_idx = idx;
+        const int dev = c->device;
+        cudaStream_t os = bo.stream;
+        bo.threads.emplace_back([=, &bo]() {
+            const int kw = sizeof(K) / 8;
+            int rc = TURTLE_OK;
+            if (cudaSetDevice(dev) != cudaSuccess) rc = TURTLE_E_CUDA;
+            for (int l = 0; l < n_libs && rc == TURTLE_OK; l++) {
+                turtle_result &r = outs[lib_idx[l]];
+                r.k = k;
+                r.n = starts[l + 1] - starts[l];
+                r.n_windows = lib_windows[l];
+                r.keys = (uint64_t *)malloc(8 * kw * (r.n ? r.n : 1));
+                r.counts = (uint32_t *)malloc(4 * (r.n ? r.n : 1));
+                if (!r.keys || !r.counts) {
+                    rc = TURTLE_E_NOMEM;
+                    break;
+                }
+                if (r.n) {
+                    try {
+                        copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os);
+                        copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, os);
+                    } catch (Fail f) {
+                        rc = f.code;
+                    }
+                }
+            }
+            cudaFreeAsync(o.keys, os);
+            cudaFreeAsync(o.counts, os);
+            cudaGetLastError();
+            if (rc) bo.fail(rc);
+        });
     } catch (Fail f) {
         return fail_code(s, c, f.code);
-    } catch (std::bad_alloc &) {
+    } catch (std::exception &) {  // bad_alloc, or no thread for the copy-out
         return fail_code(s, c, TURTLE_E_NOMEM);
     }
     return TURTLE_OK;
@@ -965,7 +983,7 @@ void turtle_params_default(turtle_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
     p->struct_size = sizeof(turtle_params);
-    p->filter_bits_per_window = 4.0f;
+    p->filter_bits_per_window = 1.0f;
     p->pattern_bits = 4;
     p->n_patterns = 1024;
     p->pattern_seed = 0x7475727469ull;
@@ -1055,8 +1073,6 @@ void turtle_ctx_destroy(turtle_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->ev_packed)
         if (e) cudaEventDestroy(e);
-    for (auto &pb : c->pinned)
-        if (pb) cudaFreeHost(pb);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
@@ -1130,9 +1146,8 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     const uint64_t n_bases = reads->offsets[reads->n_reads];
     const turtle_params prm = resolve(params);
     size_t chunk = (size_t)prm.stream_chunk_mib << 20;
-    if (!chunk && n_bases >= ((uint64_t)64 << 20)) {  // large inputs stream through the pinned buffers
+    if (!chunk) {  // stream when the ASCII would take more than a quarter of the free device memory
         size_t free_b = 0, total_b = 0;
-        chunk = (size_t)256 << 20;
         if (cudaSetDevice(c->device) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
             n_bases > free_b / 4)
             chunk = (size_t)1 << 30;
@@ -1210,6 +1225,11 @@ int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_param
     turtle_ctx *c = default_ctx(&rc);
     if (!c) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    BatchOutput bo;
+    if (cudaStreamCreateWithFlags(&bo.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return TURTLE_E_CUDA;
+    }
     // group by (k, min_count); a run holds as many libraries as the spare key bits can tag (<= 64)
     std::map<std::pair<int, uint32_t>, std::vector<size_t>> groups;
     for (size_t i = 0; i < n_jobs; i++) groups[{jobs[i].k, jobs[i].min_count}].push_back(i);
@@ -1222,15 +1242,21 @@ int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_param
             std::vector<size_t> idx(all.begin() + a, all.begin() + std::min(all.size(), a + per_run));
             int tag_bits = 0;
             while (((size_t)1 << tag_bits) < idx.size()) tag_bits++;
-            rc = 2 * k + tag_bits <= 64 ? batch_run<uint64_t>(c, jobs, idx, tag_bits, params, s, outs)
-                                        : batch_run<Key128>(c, jobs, idx, tag_bits, params, s, outs);
+            rc = 2 * k + tag_bits <= 64 ? batch_run<uint64_t>(c, jobs, idx, tag_bits, params, s, outs, bo)
+                                        : batch_run<Key128>(c, jobs, idx, tag_bits, params, s, outs, bo);
             if (rc) {
+                bo.join();
+                cudaStreamDestroy(bo.stream);
                 for (size_t i = 0; i < n_jobs; i++) turtle_result_free(&outs[i]);
                 return rc;
             }
         }
     }
-    return TURTLE_OK;
+    rc = bo.join();
+    cudaStreamDestroy(bo.stream);
+    if (rc)
+        for (size_t i = 0; i < n_jobs; i++) turtle_result_free(&outs[i]);
+    return rc;
 }
 
 int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_result *out) {
