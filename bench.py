@@ -32,9 +32,10 @@ import synth  # noqa: E402
 
 METRIC = "canonical k-mers/s"
 HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/served vs plain"
-# DRAM bytes (read + write) per unit measured by ncu on the 1/10-scale fly-shaped case (64-bit keys),
-# see profiles/: scaled to a full launch by the units that launch processes.
-NCU_BYTES_PER_UNIT = {"sort": 16.14, "filter": 131.23, "recount": 204.65}
+# DRAM bytes (read + write) per unit of each kernel, from ncu captures of the current kernels on the
+# fly-shaped library at 1/10 scale (profiles/); scaled to a full launch by the units it processes.
+# A kernel is left out (traffic null) until it has been captured again after a change.
+NCU_BYTES_PER_UNIT = {"k_pass1": 99.39, "k_onesweep": 16.16, "k_bucket_count": 8.67}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -162,23 +163,45 @@ def cpu_baseline(lib, sample_reads: int):
             "sample": "first %d reads (%d windows) of the same library, %.1f s" % (n, nw, dt)}
 
 
-def alg_bytes(stage: str, st: dict, lib) -> float:
-    """Algorithmic HBM bytes of one launch of the stage's kernel (byte model, one unit = one window)."""
+# The kernel behind each timed stage (bucketed form / global form of sort-and-compact).
+STAGE_KERNEL = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_bucket_count", "recount": "k_add_firsts"}
+STAGE_KERNEL_GLOBAL = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_rle", "recount": "k_add_firsts"}
+
+
+def stage_bytes(stage: str, st: dict, lib, bucketed: bool):
+    """(algorithmic HBM bytes of the stage's main kernel over one step, its launches per step, its units
+    per step: windows for filter and rle, key-passes for sort, first sightings for recount).
+
+    Byte model (one unit = one valid window; kw = key bytes; parts = key-range super-partitions):
+      filter  k_pass1: every part re-reads the packed reads (2-bit codes + validity bits), each window
+              probes one 32-byte filter sector in its own part, a first sighting writes its sector
+              back, every probed window leaves as one key (candidate or first sighting)
+      sort    k_onesweep: every key read and written once per digit pass (bucketed: candidates and
+              first sightings, two sorts per part; global: candidates)
+      rle     k_bucket_count: candidates and first sightings read once, kept keys and counts written
+              (global form k_rle: candidates read, distinct keys and run starts written)
+      recount k_add_firsts (global form): first sightings streamed, one table sector each
+    """
     W = st["n_windows"]
     kw = 8 if lib.k <= 32 else 16
+    parts = max(st["super_partitions"], 1)
     R = float(np.diff(lib.offsets[:2].astype(np.int64))[0]) if lib.n_reads else 100.0
-    packed = (R / 4.0) / max(R - lib.k + 1, 1)  # 2-bit packed read bytes per window, one pass
-    firsts = W - st["n_candidates"]
-    if stage == "filter":  # packed input, one filter sector per window, write-back on first sightings, outputs
-        out = kw * W if st.get("n_firsts") else kw * st["n_candidates"]
-        return W * (packed + 32.0) + 32.0 * firsts + out
+    packed = (R / 4.0 + R / 8.0) / max(R - lib.k + 1, 1)
+    nc, nf, nu, no = st["n_candidates"], st["n_firsts"], st["n_unique"], st["n_out"]
+    passes = max(st["sort_passes"], 1)
+    if stage == "filter":
+        return parts * W * packed + W * 32.0 + 32.0 * (nf if nf else W - nc) + kw * (nc + nf), parts, W
+    if stage == "sort":
+        if bucketed:
+            return passes * 2.0 * kw * (nc + nf), passes * parts * ((nc > 1) + (nf > 1)), passes * (nc + nf)
+        return passes * 2.0 * kw * nc, passes * parts, passes * nc
+    if stage == "rle":
+        if bucketed:
+            return kw * (nc + nf) + (kw + 4.0) * no, parts, nc + nf
+        return kw * nc + (kw + 8.0) * nu, parts, nc
     if stage == "recount":
-        if st.get("n_firsts"):  # stream the firsts once, one table sector each, write-back when found
-            return st["n_firsts"] * (kw + 32.0) + 32.0 * st["n_unique"]
-        return W * (packed + 32.0) + 32.0 * st["n_candidates"]
-    if stage == "sort":  # one onesweep digit pass: every candidate read and written once
-        return 2.0 * kw * st["n_candidates"]
-    return 0.0
+        return nf * (kw + 32.0) + 32.0 * nu, parts, nf
+    return 0.0, 1, 0
 
 
 def run_ours(args, rank, world):
@@ -276,18 +299,19 @@ def run_ours(args, rank, world):
 
     # roofline of the dominant kernel, from the live per-stage CUDA events of the timed steps
     avg = {s: float(np.mean(v)) for s, v in stage_ms.items()}
-    per_launch = {}
-    for s in ("filter", "sort", "recount"):
-        n_l = st["stage_launches"][s] if s != "sort" else max(st["sort_passes"], 1)
-        per_launch[s] = avg[s] / max(n_l, 1)
-    dom = max(("filter", "recount", "sort"), key=lambda s: avg[s])
+    bucketed = prm.compact == 0 and not prm.recount_windows
+    dom = max(("filter", "sort", "rle", "recount"), key=lambda s: avg[s])
     hbm, src = peaks()
-    ach = alg_bytes(dom, st, lib) / (per_launch[dom] / 1e3) / 1e9
-    units = {"sort": st["n_candidates"], "filter": W, "recount": st["n_firsts"]}[dom]
-    traffic = NCU_BYTES_PER_UNIT[dom] * units if lib.k <= 32 and units else None
-    roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
+    total_bytes, n_launch, units = stage_bytes(dom, st, lib, bucketed)
+    ach = total_bytes / (avg[dom] / 1e3) / 1e9  # = bytes per launch / average launch time
+    kern = (STAGE_KERNEL if bucketed else STAGE_KERNEL_GLOBAL)[dom]
+    per_unit = NCU_BYTES_PER_UNIT.get(kern) if lib.k <= 32 and bucketed else None
+    traffic = per_unit * units / n_launch if per_unit else None
+    roof = {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
-            "traffic_note": "ncu dram bytes per unit on the 1/10-scale case x units per launch" if traffic else None,
+            "bytes_per_launch": total_bytes / n_launch, "launches_per_step": n_launch,
+            "traffic_note": ("ncu dram bytes per unit of this kernel (profiles/) x units per launch"
+                             if traffic else None),
             "stage_ms": {s: round(v, 3) for s, v in avg.items()}}
 
     out = {"metric": HEADLINE, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
