@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk", "served", "batched"])
     ap.add_argument("--jobs", type=int, default=1000, help="served: number of jobs (Poisson arrivals, 50/s)")
-    ap.add_argument("--workers", type=int, default=8, help="served: concurrent jobs on the device")
+    ap.add_argument("--workers", type=int, default=64, help="served: most queued jobs batched into one run")
     ap.add_argument("--saturate-jobs", type=int, default=300,
                     help="served: also submit this many jobs at once (no arrival gaps) to compare capacity")
     ap.add_argument("--scale", type=float, default=1.0)
@@ -410,8 +410,9 @@ def micro():
 def run_served(args):
     """Served form: Poisson arrivals (50 jobs/s) of 1-50 Mbase libraries, k in {25,31,63}, min_count in {2,3}.
 
-    The same arrival stream is driven through the server twice: with `--workers` concurrent jobs
-    (continuous batching) and with one worker (the plain per-library form behind a FIFO queue).
+    The same arrival stream is driven through the server twice: with up to `--workers` queued jobs
+    batched into one run (continuous batching) and with every job run alone (the plain per-library
+    form behind a FIFO queue).
     """
     import queue
 
@@ -424,7 +425,7 @@ def run_served(args):
         jobs.append((lib.bases, lib.offsets, sp["k"], sp["min_count"], sp["t"]))
 
     def drive(workers, jobs=jobs, paced=True):
-        srv = pkg.Server(0, hbm_budget_bytes=0, max_concurrent=workers)
+        srv = pkg.Server(0, hbm_budget_bytes=0, max_batch=workers)
         for b, o, k, m, _ in jobs[:4]:  # warm every worker's context
             srv.poll(srv.submit(b, o, k, m))
         pending = queue.Queue()
@@ -469,7 +470,7 @@ def run_served(args):
             "config": {"workload": "served: %d jobs, Poisson arrivals 50/s, read bases log-uniform %.1f-%.0f Mbase, "
                                    "100 bp, 1%% substitutions, k in {25,31,63}, min_count in {2,3}"
                                    % (len(jobs), 1.0 * args.scale, 50.0 * args.scale),
-                       "workers": args.workers},
+                       "max_batch": args.workers},
             "served": served, "plain_fifo_1_worker": plain,
             "p99_speedup_vs_plain": plain["p99_ms"] / served["p99_ms"],
             "saturated": {"jobs": len(burst), "served": sat_served, "plain_fifo_1_worker": sat_plain,

@@ -239,11 +239,13 @@ int turtle_sort_compact(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int k
                         uint64_t *unique, uint32_t *counts, uint64_t *n_unique, void *stream);
 
 /* ------------------------------------------------------------------ served form
- * A request loop for many counting jobs (continuous batching). Jobs are admitted in
- * arrival order as soon as a worker is idle and the job's device-memory footprint
- * estimate fits in what is left of the HBM budget; admitted jobs run concurrently on
- * separate streams and overlap on the device. Each result equals turtle_count on the
- * same reads. Reads stay in caller-owned host memory until the job's poll returns.
+ * A request loop for many counting jobs (continuous batching). Jobs queue in arrival order;
+ * whenever the device is free, the oldest job is admitted together with every queued job of
+ * the same k and min_count whose device-memory footprint estimate still fits the HBM budget
+ * (at most max_batch of them, and at most as many as turtle_count_batch puts in one run), and
+ * they run as one batched pipeline. Device work runs one batch at a time; a finished batch's
+ * results are copied to the host while the next batch runs. Each result equals turtle_count on
+ * the same reads. Reads stay in caller-owned host memory until the job's poll returns.
  */
 typedef struct turtle_server turtle_server;
 
@@ -277,11 +279,13 @@ typedef struct {
 typedef struct {
     uint64_t budget_bytes, admitted_bytes, peak_admitted_bytes;
     uint64_t submitted, completed, failed, queued, running, peak_running, peak_queued;
+    uint64_t batches, largest_batch;  /* batched runs started; most jobs in one run */
 } turtle_server_stats;
 
-/* Start a server on `device` with `max_concurrent` workers (1..64), each owning a context and
- * a stream. hbm_budget_bytes = 0 takes half of the free device memory. params may be NULL. */
-int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_concurrent, const turtle_params *params,
+/* Start a server on `device`; up to max_batch jobs (1..64) share one run (1 = every job alone,
+ * in arrival order). The server owns one context, a stream and two host threads (executor and
+ * copy-out). hbm_budget_bytes = 0 takes half of the free device memory. params may be NULL. */
+int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_batch, const turtle_params *params,
                          turtle_server **server);
 /* Queue a job; *ticket identifies it. TURTLE_E_BUSY: its footprint estimate exceeds the whole
  * budget, so it could never be admitted. */

@@ -229,7 +229,8 @@ class JobTimes(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, u64) for n in ("budget_bytes", "admitted_bytes", "peak_admitted_bytes", "submitted", "completed",
-                                   "failed", "queued", "running", "peak_running", "peak_queued")]
+                                   "failed", "queued", "running", "peak_running", "peak_queued", "batches",
+                                   "largest_batch")]
 
 
 def turtle_count_batch(jobs, params: Params | None = None, stream=None):
@@ -254,14 +255,17 @@ def turtle_count_batch(jobs, params: Params | None = None, stream=None):
 
 
 class Server:
-    """Served form: continuous batching of counting jobs admitted by device-memory footprint."""
+    """Served form: continuous batching of counting jobs admitted by device-memory footprint.
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_concurrent: int = 4,
+    Up to max_batch queued jobs with the same k and min_count share one batched run.
+    """
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_batch: int = 64,
                  params: Params | None = None):
         self._lib = load()
         self._h = _p()
         self._keep = {}
-        _check(self._lib.turtle_server_create(device, hbm_budget_bytes, max_concurrent,
+        _check(self._lib.turtle_server_create(device, hbm_budget_bytes, max_batch,
                                               ctypes.byref(params) if params else None, ctypes.byref(self._h)),
                "turtle_server_create")
 

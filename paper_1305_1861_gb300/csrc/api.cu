@@ -856,29 +856,13 @@ int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bas
     }
 }
 
-// Copy-out of finished runs on host threads, overlapping the next runs on the GPU.
-struct BatchOutput {
-    cudaStream_t stream = nullptr;  // device -> host copies of every run
-    std::vector<std::thread> threads;
-    std::mutex mu;
-    int rc = TURTLE_OK;
-    void fail(int code) {
-        std::lock_guard<std::mutex> g(mu);
-        if (rc == TURTLE_OK) rc = code;
-    }
-    int join() {
-        for (auto &t : threads) t.join();
-        threads.clear();
-        return rc;
-    }
-};
-
 // One batched run: libraries `idx` (same k and min_count) concatenated on the device, counted by
 // one pipeline with library-tagged keys, results split back per library into outs[] by a host
 // thread of bo, which also frees the run's device results.
 template <class K>
 int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, int tag_bits,
-              const turtle_params *params, cudaStream_t s, turtle_result *outs, BatchOutput &bo) {
+              const turtle_params *params, cudaStream_t s, turtle_result *outs, BatchOutput &bo,
+              std::function<void(int)> done) {
     const int k = jobs[idx[0]].k;
     const uint32_t min_count = jobs[idx[0]].min_count;
     const int n_libs = (int)idx.size();
@@ -934,8 +918,8 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         ctx_end(c, s);
         std::vector<size_t> lib_idx = idx;
         const int dev = c->device;
-        cudaStream_t os = bo.stream;
-        bo.threads.emplace_back([=, &bo]() {
+        cudaStream_t os = bo.stream();
+        bo.post([=, &bo]() {
             const int kw = sizeof(K) / 8;
             int rc = TURTLE_OK;
             if (cudaSetDevice(dev) != cudaSuccess) rc = TURTLE_E_CUDA;
@@ -963,6 +947,7 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
             cudaFreeAsync(o.counts, os);
             cudaGetLastError();
             if (rc) bo.fail(rc);
+            if (done) done(rc);
         });
     } catch (Fail f) {
         return fail_code(s, c, f.code);
@@ -976,6 +961,77 @@ std::mutex g_default_mu;
 turtle_ctx *g_default[64] = {};
 
 }  // namespace
+
+BatchOutput::BatchOutput() {
+    if (cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        stream_ = nullptr;
+    }
+    worker_ = std::thread([this] { loop(); });
+}
+
+BatchOutput::~BatchOutput() {
+    drain();
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        stop_ = true;
+    }
+    cv_.notify_all();
+    worker_.join();
+    if (stream_) cudaStreamDestroy(stream_);
+    cudaGetLastError();
+}
+
+void BatchOutput::loop() {
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+        cv_.wait(lk, [&] { return stop_ || !tasks_.empty(); });
+        if (tasks_.empty()) return;  // stop_ with nothing left
+        std::function<void()> t = std::move(tasks_.front());
+        tasks_.pop_front();
+        busy_ = true;
+        lk.unlock();
+        t();
+        lk.lock();
+        busy_ = false;
+        cv_idle_.notify_all();
+    }
+}
+
+void BatchOutput::post(std::function<void()> task) {
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        tasks_.push_back(std::move(task));
+    }
+    cv_.notify_one();
+}
+
+void BatchOutput::fail(int code) {
+    std::lock_guard<std::mutex> g(mu_);
+    if (rc_ == TURTLE_OK) rc_ = code;
+}
+
+int BatchOutput::drain() {
+    std::unique_lock<std::mutex> lk(mu_);
+    cv_idle_.wait(lk, [&] { return tasks_.empty() && !busy_; });
+    return rc_;
+}
+
+size_t batch_capacity(int k) {
+    const int room = (2 * k <= 64 ? 64 : 128) - 2 * k;  // key bits above the 2k of the key
+    return room >= 6 ? 64 : ((size_t)1 << room);
+}
+
+int batch_run_jobs(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, const turtle_params *params,
+                   cudaStream_t s, turtle_result *outs, BatchOutput &bo, std::function<void(int)> done) {
+    if (idx.empty() || idx.size() > batch_capacity(jobs[idx[0]].k) || !bo.ok()) return TURTLE_E_ARG;
+    const int k = jobs[idx[0]].k;
+    int tag_bits = 0;
+    while (((size_t)1 << tag_bits) < idx.size()) tag_bits++;
+    return 2 * k + tag_bits <= 64 ? batch_run<uint64_t>(c, jobs, idx, tag_bits, params, s, outs, bo, done)
+                                  : batch_run<Key128>(c, jobs, idx, tag_bits, params, s, outs, bo, done);
+}
+
 
 extern "C" {
 
@@ -1226,34 +1282,20 @@ int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_param
     if (!c) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     BatchOutput bo;
-    if (cudaStreamCreateWithFlags(&bo.stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        return TURTLE_E_CUDA;
-    }
+    if (!bo.ok()) return TURTLE_E_CUDA;
     // group by (k, min_count); a run holds as many libraries as the spare key bits can tag (<= 64)
     std::map<std::pair<int, uint32_t>, std::vector<size_t>> groups;
     for (size_t i = 0; i < n_jobs; i++) groups[{jobs[i].k, jobs[i].min_count}].push_back(i);
     for (auto &kv : groups) {
-        const int k = kv.first.first;
-        const int room = (2 * k <= 64 ? 64 : 128) - 2 * k;
-        const size_t per_run = room >= 6 ? 64 : ((size_t)1 << room);
+        const size_t per_run = batch_capacity(kv.first.first);
         const std::vector<size_t> &all = kv.second;
-        for (size_t a = 0; a < all.size(); a += per_run) {
+        for (size_t a = 0; a < all.size() && rc == TURTLE_OK; a += per_run) {
             std::vector<size_t> idx(all.begin() + a, all.begin() + std::min(all.size(), a + per_run));
-            int tag_bits = 0;
-            while (((size_t)1 << tag_bits) < idx.size()) tag_bits++;
-            rc = 2 * k + tag_bits <= 64 ? batch_run<uint64_t>(c, jobs, idx, tag_bits, params, s, outs, bo)
-                                        : batch_run<Key128>(c, jobs, idx, tag_bits, params, s, outs, bo);
-            if (rc) {
-                bo.join();
-                cudaStreamDestroy(bo.stream);
-                for (size_t i = 0; i < n_jobs; i++) turtle_result_free(&outs[i]);
-                return rc;
-            }
+            rc = batch_run_jobs(c, jobs, idx, params, s, outs, bo, nullptr);
         }
     }
-    rc = bo.join();
-    cudaStreamDestroy(bo.stream);
+    const int rc_out = bo.drain();
+    if (rc == TURTLE_OK) rc = rc_out;
     if (rc)
         for (size_t i = 0; i < n_jobs; i++) turtle_result_free(&outs[i]);
     return rc;

@@ -1,12 +1,14 @@
 // Served form: a request loop that admits counting jobs by device-memory footprint as they
-// arrive and runs them concurrently (continuous batching).
+// arrive and runs them with continuous batching.
 //
-// Each worker owns a context (its own memory pool, kept between jobs) and a stream. A job
-// waits in FIFO order until a worker is idle AND its footprint estimate fits in what is left of
-// the HBM budget; it then runs on that worker's stream, so jobs admitted while others are on
-// the GPU overlap with them. A job whose estimate exceeds the whole budget is refused at submit
-// time (TURTLE_E_BUSY). Results are exactly those of turtle_count on the same reads: nothing is
-// shared between jobs except the device.
+// One executor thread owns the device work, in FIFO order. Whenever the GPU is free it takes
+// the oldest queued job plus every other queued job with the same k and min_count whose
+// footprint estimate still fits the HBM budget (up to max_batch jobs, and as many as the spare
+// key bits can tag), and runs them as one batched pipeline: each stage is one launch for all of
+// them. The run's results are split and copied to the host by a second thread while the next
+// run executes, so host-side work overlaps device work. A job whose estimate exceeds the whole
+// budget is refused at submit time (TURTLE_E_BUSY). Results are exactly those of turtle_count
+// on the same reads.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -40,11 +42,13 @@ struct Ticket {
 
 struct turtle_server {
     int device = 0;
+    int max_batch = 1;
     uint64_t budget = 0, in_use = 0;
     turtle_params params{};
-    std::vector<std::thread> workers;
-    std::vector<turtle_ctx *> ctxs;
-    std::vector<cudaStream_t> streams;
+    turtle_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::unique_ptr<BatchOutput> out;
+    std::thread executor;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
@@ -54,55 +58,92 @@ struct turtle_server {
     turtle_server_stats stats{};
 };
 
-static void worker_loop(turtle_server *sv, int w) {
+// A run has finished (or failed): hand each job its result, release its footprint.
+static void finish(turtle_server *sv, const std::vector<uint64_t> &ids, const std::vector<uint64_t> &fps,
+                   turtle_result *outs, int rc) {
+    std::lock_guard<std::mutex> g(sv->mu);
+    const double t = now_ms();
+    for (size_t i = 0; i < ids.size(); i++) {
+        Ticket *tk = sv->tickets[ids[i]].get();
+        if (rc == TURTLE_OK) {
+            tk->res = outs[i];
+        } else {
+            turtle_result_free(&outs[i]);
+            memset(&tk->res, 0, sizeof(tk->res));
+        }
+        tk->rc = rc;
+        tk->t_end = t;
+        tk->done = true;
+        sv->in_use -= fps[i];
+        sv->stats.running--;
+        sv->stats.completed++;
+        if (rc) sv->stats.failed++;
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+}
+
+static void executor_loop(turtle_server *sv) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
         sv->cv_work.wait(lk, [&] {
             if (sv->stop) return true;
             if (sv->queue.empty()) return false;
-            const Ticket *t = sv->tickets[sv->queue.front()].get();
-            return sv->in_use + t->footprint <= sv->budget;  // admission by device-memory footprint
+            return sv->in_use + sv->tickets[sv->queue.front()]->footprint <= sv->budget;  // admission
         });
         if (sv->stop) return;
-        const uint64_t id = sv->queue.front();
-        sv->queue.pop_front();
-        Ticket *t = sv->tickets[id].get();
-        sv->in_use += t->footprint;
-        sv->stats.running++;
+        // continuous batching: the oldest job and the queued jobs that can share its pipeline
+        const turtle_job head = sv->tickets[sv->queue.front()]->job;
+        const size_t cap = std::min<size_t>((size_t)sv->max_batch, batch_capacity(head.k));
+        std::vector<uint64_t> ids, fps;
+        uint64_t room = sv->budget - sv->in_use;
+        for (auto it = sv->queue.begin(); it != sv->queue.end() && ids.size() < cap;) {
+            Ticket *t = sv->tickets[*it].get();
+            const bool same = t->job.k == head.k && t->job.min_count == head.min_count;
+            if ((ids.empty() || same) && t->footprint <= room) {
+                room -= t->footprint;
+                ids.push_back(*it);
+                fps.push_back(t->footprint);
+                it = sv->queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        const double t0 = now_ms();
+        std::vector<turtle_job> jobs(ids.size());
+        for (size_t i = 0; i < ids.size(); i++) {
+            Ticket *t = sv->tickets[ids[i]].get();
+            t->t_start = t0;
+            jobs[i] = t->job;
+            sv->in_use += fps[i];
+        }
+        sv->stats.running += ids.size();
+        sv->stats.batches++;
+        if (ids.size() > sv->stats.largest_batch) sv->stats.largest_batch = ids.size();
         if (sv->stats.running > sv->stats.peak_running) sv->stats.peak_running = sv->stats.running;
         if (sv->in_use > sv->stats.peak_admitted_bytes) sv->stats.peak_admitted_bytes = sv->in_use;
-        t->t_start = now_ms();
-        const turtle_job job = t->job;
-        const bool more = !sv->queue.empty();
         lk.unlock();
-        if (more) sv->cv_work.notify_one();  // the next job may fit beside this one
-        turtle_reads r{job.bases, job.offsets, job.n_reads};
-        turtle_result res{};
-        const int rc = count_host_impl(sv->ctxs[w], &r, job.k, job.min_count, &sv->params, sv->streams[w], &res);
+        std::shared_ptr<std::vector<turtle_result>> outs = std::make_shared<std::vector<turtle_result>>(ids.size());
+        std::vector<size_t> idx(ids.size());
+        for (size_t i = 0; i < idx.size(); i++) idx[i] = i;
+        const int rc = batch_run_jobs(sv->ctx, jobs.data(), idx, &sv->params, sv->stream, outs->data(), *sv->out,
+                                      [sv, ids, fps, outs](int r) { finish(sv, ids, fps, outs->data(), r); });
+        if (rc) finish(sv, ids, fps, outs->data(), rc);  // nothing was posted
         lk.lock();
-        t->res = res;
-        t->rc = rc;
-        t->t_end = now_ms();
-        t->done = true;
-        sv->in_use -= t->footprint;
-        sv->stats.running--;
-        sv->stats.completed++;
-        if (rc) sv->stats.failed++;
-        sv->cv_done.notify_all();
-        sv->cv_work.notify_all();
     }
 }
 
 extern "C" {
 
-int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_concurrent, const turtle_params *params,
+int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_batch, const turtle_params *params,
                          turtle_server **out) {
-    if (!out || max_concurrent < 1 || max_concurrent > 64) return TURTLE_E_ARG;
+    if (!out || max_batch < 1 || max_batch > 64) return TURTLE_E_ARG;
     *out = nullptr;
     turtle_server *sv = new (std::nothrow) turtle_server();
     if (!sv) return TURTLE_E_NOMEM;
     sv->device = device;
+    sv->max_batch = max_batch;
     if (params) sv->params = *params;
     else turtle_params_default(&sv->params);
     if (sv->params.struct_size != sizeof(turtle_params)) turtle_params_default(&sv->params);
@@ -119,32 +160,28 @@ int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_concurre
     }
     sv->budget = hbm_budget_bytes;
     sv->stats.budget_bytes = hbm_budget_bytes;
-    for (int w = 0; w < max_concurrent; w++) {
-        turtle_ctx *c = nullptr;
-        int rc = turtle_ctx_create(device, &c);
-        cudaStream_t st = nullptr;
-        if (!rc && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = TURTLE_E_CUDA;
-        if (rc) {
-            if (c) turtle_ctx_destroy(c);
-            cudaGetLastError();
-            sv->stop = true;
-            turtle_server_destroy(sv);
-            return rc;
-        }
-        sv->ctxs.push_back(c);
-        sv->streams.push_back(st);
+    int rc = turtle_ctx_create(device, &sv->ctx);
+    if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = TURTLE_E_CUDA;
+    if (!rc) {
+        sv->out.reset(new (std::nothrow) BatchOutput());
+        if (!sv->out || !sv->out->ok()) rc = TURTLE_E_CUDA;
     }
-    for (int w = 0; w < max_concurrent; w++) sv->workers.emplace_back(worker_loop, sv, w);
+    if (rc) {
+        cudaGetLastError();
+        turtle_server_destroy(sv);
+        return rc;
+    }
+    sv->executor = std::thread(executor_loop, sv);
     *out = sv;
     return TURTLE_OK;
 }
 
 int turtle_submit(turtle_server *sv, const turtle_job *job, uint64_t *ticket) {
     if (!sv || !job || !ticket || !job->offsets || (job->n_reads && !job->bases) || job->k < 1 || job->k > 64 ||
-        job->min_count < 1)
+        job->min_count < 1 || job->offsets[job->n_reads] < job->offsets[0])
         return TURTLE_E_ARG;
     *ticket = 0;
-    const uint64_t n_bases = job->offsets[job->n_reads];
+    const uint64_t n_bases = job->offsets[job->n_reads] - job->offsets[0];
     const uint64_t fp = footprint_estimate(n_bases, job->n_reads, job->k, job->min_count, &sv->params);
     if (fp > sv->budget) return TURTLE_E_BUSY;  // could never be admitted
     auto t = std::make_unique<Ticket>();
@@ -199,12 +236,12 @@ void turtle_server_destroy(turtle_server *sv) {
         sv->stop = true;
     }
     sv->cv_work.notify_all();
-    for (auto &th : sv->workers) th.join();  // running jobs finish first
+    if (sv->executor.joinable()) sv->executor.join();  // the running batch finishes first
+    if (sv->out) sv->out->drain();                       // and its copy-out
+    sv->out.reset();
     for (auto &kv : sv->tickets) turtle_result_free(&kv.second->res);
-    for (size_t w = 0; w < sv->ctxs.size(); w++) {
-        turtle_ctx_destroy(sv->ctxs[w]);
-        if (sv->streams[w]) cudaStreamDestroy(sv->streams[w]);
-    }
+    if (sv->ctx) turtle_ctx_destroy(sv->ctx);
+    if (sv->stream) cudaStreamDestroy(sv->stream);
     cudaGetLastError();
     delete sv;
 }

@@ -24,7 +24,7 @@ def test_results_alone_equal_results_in_the_mix(have_gpu):
 
     jobs = _jobs(24)
     alone = [pkg.turtle_count(b, o, k, m) for b, o, k, m in jobs]
-    srv = pkg.Server(0, hbm_budget_bytes=3 << 30, max_concurrent=4)
+    srv = pkg.Server(0, hbm_budget_bytes=3 << 30, max_batch=4)
     tickets = [srv.submit(b, o, k, m) for b, o, k, m in jobs]
     for t, (ak, ac, an) in zip(tickets, alone):
         keys, counts, nw, tm = srv.poll(t)
@@ -32,7 +32,7 @@ def test_results_alone_equal_results_in_the_mix(have_gpu):
         assert tm.total_ms >= tm.run_ms >= 0
     st = srv.stats()
     assert st["completed"] == 24 and st["failed"] == 0 and st["peak_admitted_bytes"] <= 3 << 30
-    assert st["peak_running"] >= 2  # jobs overlapped on the device
+    assert st["largest_batch"] >= 2 and st["batches"] < 24  # queued jobs shared runs
     srv.close()
     b, o, k, m = jobs[0]
     ok, oc, _ = oracle.count(b, o, k, m)
@@ -43,7 +43,7 @@ def test_admission_refuses_a_job_larger_than_the_budget(have_gpu):
     import paper_1305_1861_gb300 as pkg
 
     b, o, k, m = _jobs(1)[0]
-    srv = pkg.Server(0, hbm_budget_bytes=1 << 20, max_concurrent=1)
+    srv = pkg.Server(0, hbm_budget_bytes=1 << 20, max_batch=1)
     with pytest.raises(pkg.TurtleError) as e:
         srv.submit(b, o, k, m)
     assert e.value.code == -6
@@ -55,7 +55,7 @@ def test_poll_times_out_then_completes(have_gpu):
 
     big = synth.fly(seed=3, scale=0.05)  # ~150 Mbase: tens of ms on the single worker
     small = _jobs(1)[0]
-    srv = pkg.Server(0, hbm_budget_bytes=64 << 30, max_concurrent=1)
+    srv = pkg.Server(0, hbm_budget_bytes=64 << 30, max_batch=1)
     t_big = srv.submit(big.bases, big.offsets, 31, 2)
     t_small = srv.submit(*small)
     with pytest.raises(pkg.TurtleError) as e:
