@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk", "served", "batched"])
     ap.add_argument("--jobs", type=int, default=1000, help="served: number of jobs (Poisson arrivals, 50/s)")
-    ap.add_argument("--workers", type=int, default=64, help="served: most queued jobs batched into one run")
+    ap.add_argument("--max-batch", type=int, default=4, help="served: most queued jobs batched into one run")
     ap.add_argument("--saturate-jobs", type=int, default=300,
                     help="served: also submit this many jobs at once (no arrival gaps) to compare capacity")
     ap.add_argument("--scale", type=float, default=1.0)
@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..3 (-1 = default)")
     ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
     ap.add_argument("--compact", type=int, default=-1, help="0 = bucketed, 1 = global sort-and-compact")
+    ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
     ap.add_argument("--micro", action="store_true",
                     help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()
@@ -231,6 +232,8 @@ def run_ours(args, rank, world):
         prm.bucket_slots = args.bucket_slots
     if args.compact >= 0:
         prm.compact = args.compact
+    if args.budget_mib:
+        prm.budget_mib = args.budget_mib
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)
@@ -305,7 +308,9 @@ def run_ours(args, rank, world):
     total_bytes, n_launch, units = stage_bytes(dom, st, lib, bucketed)
     ach = total_bytes / (avg[dom] / 1e3) / 1e9  # = bytes per launch / average launch time
     kern = (STAGE_KERNEL if bucketed else STAGE_KERNEL_GLOBAL)[dom]
-    per_unit = NCU_BYTES_PER_UNIT.get(kern) if lib.k <= 32 and bucketed else None
+    # per-unit DRAM bytes were captured on the fly-shaped library at default parameters only
+    per_unit = (NCU_BYTES_PER_UNIT.get(kern) if args.workload == "fly" and bucketed and args.filter_bits <= 0
+                and args.scale == 1.0 else None)
     traffic = per_unit * units / n_launch if per_unit else None
     roof = {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
@@ -410,7 +415,7 @@ def micro():
 def run_served(args):
     """Served form: Poisson arrivals (50 jobs/s) of 1-50 Mbase libraries, k in {25,31,63}, min_count in {2,3}.
 
-    The same arrival stream is driven through the server twice: with up to `--workers` queued jobs
+    The same arrival stream is driven through the server twice: with up to `--max-batch` queued jobs
     batched into one run (continuous batching) and with every job run alone (the plain per-library
     form behind a FIFO queue).
     """
@@ -460,17 +465,17 @@ def run_served(args):
                 "windows": windows, "peak_running": st["peak_running"], "peak_queued": st["peak_queued"],
                 "peak_admitted_gb": st["peak_admitted_bytes"] / 1e9}
 
-    served = drive(args.workers)
+    served = drive(args.max_batch)
     plain = drive(1)
     burst = jobs[: args.saturate_jobs]
-    sat_served = drive(args.workers, burst, paced=False)
+    sat_served = drive(args.max_batch, burst, paced=False)
     sat_plain = drive(1, burst, paced=False)
     return {"metric": "served: p50/p99 job latency and aggregate canonical k-mers/s", "value": served["kmers_per_s"],
             "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "served: %d jobs, Poisson arrivals 50/s, read bases log-uniform %.1f-%.0f Mbase, "
                                    "100 bp, 1%% substitutions, k in {25,31,63}, min_count in {2,3}"
                                    % (len(jobs), 1.0 * args.scale, 50.0 * args.scale),
-                       "max_batch": args.workers},
+                       "max_batch": args.max_batch},
             "served": served, "plain_fifo_1_worker": plain,
             "p99_speedup_vs_plain": plain["p99_ms"] / served["p99_ms"],
             "saturated": {"jobs": len(burst), "served": sat_served, "plain_fifo_1_worker": sat_plain,

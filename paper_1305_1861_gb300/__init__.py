@@ -260,7 +260,7 @@ class Server:
     Up to max_batch queued jobs with the same k and min_count share one batched run.
     """
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_batch: int = 64,
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_batch: int = 4,
                  params: Params | None = None):
         self._lib = load()
         self._h = _p()

@@ -779,7 +779,8 @@ void first_touch(void *p, size_t bytes) {
     const size_t page = (size_t)sysconf(_SC_PAGESIZE);
     const size_t pages = (bytes + page - 1) / page;
     const unsigned hw = std::thread::hardware_concurrency();
-    const int T = bytes < ((size_t)4 << 20) ? 1 : (int)std::min(16u, hw ? hw : 1u);
+    // half the host's threads at most: the executor and the caller's threads keep running meanwhile
+    const int T = bytes < ((size_t)4 << 20) ? 1 : (int)std::max(1u, std::min(8u, hw / 2));
     auto touch = [=](size_t a, size_t b) {
         for (size_t i = a; i < b; i++) static_cast<volatile char *>(p)[i * page] = 0;
     };

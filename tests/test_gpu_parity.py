@@ -281,7 +281,8 @@ def test_fly_shaped_scaled_with_repeats_and_n(ctx):
     _check_count(ctx, lib.bases, lib.offsets, 31, 2)
 
 
-@pytest.mark.parametrize("k,min_count,rw", [(31, 2, 0), (31, 2, 1), (31, 1, 0), (64, 2, 0), (64, 3, 1), (17, 2, 0)])
+@pytest.mark.parametrize("k,min_count,rw", [(31, 2, 0), (31, 2, 1), (31, 1, 0), (64, 2, 0), (64, 3, 1), (17, 2, 0),
+                                            (16, 2, 0), (15, 2, 0), (33, 1, 0), (48, 2, 0)])
 def test_count_in_key_range_super_partitions(ctx, k, min_count, rw):
     """A 1 MiB budget forces the key space into many consecutive ranges; the output must not change."""
     import paper_1305_1861_gb300 as pkg
