@@ -62,6 +62,10 @@ def _load():
         lib.oracle_pbbf_free.argtypes = [_p]
         lib.oracle_pbbf_test_and_set.argtypes = [_p, _p, u64, ctypes.c_int, _p]
         lib.oracle_pbbf_test.argtypes = [_p, _p, u64, ctypes.c_int, _p]
+        lib.oracle_cturtle.argtypes = [_p, _p, u64, ctypes.c_int, u64, ctypes.c_int, ctypes.c_int, u64,
+                                       ctypes.POINTER(_Result)]
+        lib.oracle_cturtle_collision_free.argtypes = [_p, u64, ctypes.c_int, u64, ctypes.c_int, ctypes.c_int, u64, _p]
+        lib.oracle_cturtle_collision_free.restype = None
         lib.oracle_pbbf_words.argtypes = [_p]
         lib.oracle_pbbf_words.restype = ctypes.POINTER(u64)
         lib.oracle_pbbf_patterns.argtypes = [_p]
@@ -227,3 +231,29 @@ def pbbf_fp_formula(lam: float, h: int, n_patterns: int, word_bits: int = 64, im
 def standard_bloom_bits_per_item(p: float) -> float:
     """Classic sizing of an unblocked Bloom filter with optimal hash count: m/n = -ln p / (ln 2)^2."""
     return -math.log(p) / (math.log(2) ** 2)
+
+def cturtle(bases, offsets, k: int, n_sectors: int, pattern_bits: int = 4, n_patterns: int = 1024,
+            seed: int = 0x7475727469):
+    """cTurtle (Sec. 2.2): keys reported by the sequential two-stage counting filter, in report
+    order (uint64[n] or uint64[n, 2]), and the number of valid windows."""
+    bases, offsets = _prep(bases, offsets)
+    res = _Result()
+    rc = _load().oracle_cturtle(bases.ctypes.data, offsets.ctypes.data, offsets.size - 1, k, n_sectors,
+                                pattern_bits, n_patterns, seed, ctypes.byref(res))
+    if rc:
+        raise ValueError("oracle_cturtle failed (%d)" % rc)
+    keys, _, nw = _take(res)
+    return keys, nw
+
+
+def cturtle_collision_free(keys, n_sectors: int, pattern_bits: int = 4, n_patterns: int = 1024,
+                           seed: int = 0x7475727469):
+    """For distinct keys (uint64[n] or uint64[n, 2]): True where the key's cTurtle outcome cannot
+    depend on the order of the windows (see oracle_cturtle_collision_free)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    words = 2 if keys.ndim == 2 else 1
+    n = keys.shape[0]
+    out = np.zeros(max(n, 1), np.uint8)
+    _load().oracle_cturtle_collision_free(keys.ctypes.data, n, words, n_sectors, pattern_bits, n_patterns, seed,
+                                          out.ctypes.data)
+    return out[:n].astype(bool)

@@ -448,4 +448,108 @@ void oracle_pbbf_test(const oracle_pbbf *f, const uint64_t *keys, uint64_t n, in
 const uint64_t *oracle_pbbf_words(const oracle_pbbf *f) { return f->words; }
 const uint64_t *oracle_pbbf_patterns(const oracle_pbbf *f) { return f->patterns; }
 
+
+/* ---------------------------------------------------------------- cTurtle (Sec. 2.2)
+ * A counting pattern-blocked Bloom filter in two stages, over the windows in read order.
+ * Stage 1 is the filter above: the key's pattern in its block. A window whose stage-1
+ * pattern was not complete sets it (a first sighting) and is done. Otherwise the key has
+ * been seen: stage 2 looks at a second pattern in the adjacent block (the paper's
+ * [h(x)+b, h(x)+2b]): if that pattern was not complete, it is set and the key is reported
+ * as frequent; if it was, the key was reported before (or its stage-2 bits were all set by
+ * other keys: a false negative). A singleton whose stage-1 bits were all set by other keys
+ * is reported too (a false positive). No counts are kept.
+ *
+ * Stage-2 geometry (a reading): block = sector (s + 1) mod n_sectors after the stage-1
+ * sector s; word = (h >> 18) & 3; pattern index = (h >> 20) & (n_patterns - 1), from the
+ * same table.
+ */
+} /* extern "C" */
+
+static inline void cturtle_addr(const oracle_pbbf *f, uint64_t h, uint64_t *w1, uint64_t *m1, uint64_t *w2,
+                                uint64_t *m2) {
+    const uint64_t pm = (uint64_t)(f->n_patterns - 1);
+    const uint64_t s1 = f->sector_bits ? h >> (64 - f->sector_bits) : 0;
+    const uint64_t s2 = (s1 + 1) & (f->n_sectors - 1);
+    *w1 = s1 * 4 + ((h >> 16) & 3);
+    *m1 = f->patterns[h & pm];
+    *w2 = s2 * 4 + ((h >> 18) & 3);
+    *m2 = f->patterns[(h >> 20) & pm];
+}
+
+template <class K>
+static int cturtle_impl(const uint8_t *bases, const uint64_t *off, uint64_t n_reads, int k, oracle_pbbf *f,
+                        oracle_result *res) {
+    std::vector<K> keys;
+    windows_of_reads<K>(bases, off, 0, n_reads, k, keys);
+    const int words = sizeof(K) == 8 ? 1 : 2;
+    std::vector<K> reported;
+    for (size_t i = 0; i < keys.size(); i++) {
+        uint64_t kw[2];
+        put_key<K>(kw, keys[i], words);
+        const uint64_t h = pbbf_hash(kw, words);
+        uint64_t w1, m1, w2, m2;
+        cturtle_addr(f, h, &w1, &m1, &w2, &m2);
+        if ((f->words[w1] & m1) != m1) {  // first sighting
+            f->words[w1] |= m1;
+            continue;
+        }
+        if ((f->words[w2] & m2) != m2) {  // second sighting: report once
+            f->words[w2] |= m2;
+            reported.push_back(keys[i]);
+        }
+    }
+    res->words = words;
+    res->n = reported.size();
+    res->n_windows = keys.size();
+    res->keys = (uint64_t *)calloc(res->n * words + 1, 8);
+    res->counts = (uint64_t *)calloc(res->n + 1, 8);
+    for (size_t i = 0; i < reported.size(); i++) put_key<K>(res->keys + i * words, reported[i], words);
+    return 0;
+}
+
+extern "C" {
+
+/* Keys reported by the sequential two-stage filter, in report order (counts are left 0). */
+int oracle_cturtle(const uint8_t *bases, const uint64_t *off, uint64_t n_reads, int k, uint64_t n_sectors,
+                   int pattern_bits, int n_patterns, uint64_t seed, oracle_result *res) {
+    memset(res, 0, sizeof(*res));
+    if (check_args(off, n_reads, k)) return -1;
+    oracle_pbbf *f = oracle_pbbf_new(n_sectors, pattern_bits, n_patterns, seed);
+    if (!f) return -1;
+    const int rc = k <= 32 ? cturtle_impl<uint64_t>(bases, off, n_reads, k, f, res)
+                           : cturtle_impl<u128>(bases, off, n_reads, k, f, res);
+    oracle_pbbf_free(f);
+    return rc;
+}
+
+/*
+ * For n distinct keys: free_out[i] = 1 iff key i's outcome cannot depend on the order of
+ * the windows: its stage-1 pattern has a bit that no other key's stage-1 or stage-2
+ * pattern sets, and its stage-2 pattern has a bit that no other key's patterns (nor its
+ * own stage-1 pattern) set. Such a key is reported exactly when it occurs at least twice,
+ * under any interleaving of test-and-set operations that are each atomic on one word.
+ */
+void oracle_cturtle_collision_free(const uint64_t *keys, uint64_t n, int words, uint64_t n_sectors, int pattern_bits,
+                                   int n_patterns, uint64_t seed, uint8_t *free_out) {
+    oracle_pbbf *f = oracle_pbbf_new(n_sectors, pattern_bits, n_patterns, seed);
+    if (!f) return;
+    std::vector<uint64_t> w1(n), m1(n), w2(n), m2(n);
+    std::map<uint64_t, std::vector<std::pair<uint64_t, uint64_t>>> by_word;  // word -> (key index, mask)
+    for (uint64_t i = 0; i < n; i++) {
+        cturtle_addr(f, pbbf_hash(keys + i * words, words), &w1[i], &m1[i], &w2[i], &m2[i]);
+        by_word[w1[i]].push_back(std::make_pair(i, m1[i]));
+        by_word[w2[i]].push_back(std::make_pair(i, m2[i]));
+    }
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t other1 = 0, other2 = 0;
+        for (auto &e : by_word[w1[i]])
+            if (e.first != i) other1 |= e.second;
+        for (auto &e : by_word[w2[i]])
+            if (e.first != i) other2 |= e.second;
+        if (w2[i] == w1[i]) other2 |= m1[i];
+        free_out[i] = (uint8_t)((m1[i] & ~other1) != 0 && (m2[i] & ~other2) != 0);
+    }
+    oracle_pbbf_free(f);
+}
+
 } /* extern "C" */

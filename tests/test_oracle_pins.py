@@ -232,3 +232,71 @@ def test_standard_bloom_sizing_quoted_in_paper():
     bits[rng.integers(0, m, size=(n, 7))] = True
     fp = bits[rng.integers(0, m, size=(200_000, 7))].all(axis=1).mean()
     assert abs(fp - 0.01) < 4 * math.sqrt(0.01 * 0.99 / 200_000) + 5e-4
+
+
+# ---------------------------------------------------------------- cTurtle (Sec. 2.2)
+def _ct_reads(seed, n, G=4000):
+    rng = np.random.default_rng(seed)
+    g = "".join(rng.choice(list("ACGT"), size=G))
+    return [g[s:s + 80] for s in rng.integers(0, G - 80, size=n)] + _reads_mixed(rng, 30, 20, 90)
+
+
+@pytest.mark.parametrize("k", [5, 21, 32, 33, 64])
+def test_cturtle_large_filter_reports_each_repeated_kmer_once(k):
+    """With every key collision-free (a filter far larger than the key set), cTurtle reports
+    exactly the k-mers seen at least twice, each once (string brute force)."""
+    reads = _ct_reads(300 + k, 120)
+    bases, offs = brute.pack(reads)
+    n_sectors = 1 << 20
+    keys, nw = oracle.cturtle(bases, offs, k, n_sectors)
+    assert nw == brute.n_windows(reads, k)
+    got = [brute.decode(x, k) for x in keys]
+    assert len(got) == len(set(got))
+    assert set(got) == set(brute.kmer_counts(reads, k, 2))
+    distinct, _, _ = oracle.count(bases, offs, k, 1)
+    assert oracle.cturtle_collision_free(distinct, n_sectors).all()
+
+
+def test_cturtle_stages_by_hand():
+    """k = 3: AAA seen 4 times, AAC once, ACG twice (its reverse complement CGT is the same
+    k-mer): reported AAA then ACG, in the order of their second sightings, each once."""
+    reads = ["AAAC", "AAA", "ACGT", "AAAA"]  # windows: AAA AAC | AAA | ACG CGT(=ACG) | AAA AAA
+    bases, offs = brute.pack(reads)
+    keys, nw = oracle.cturtle(bases, offs, 3, 1 << 16)
+    assert nw == 7
+    assert [brute.decode(x, 3) for x in keys] == ["AAA", "ACG"]
+
+
+@pytest.mark.parametrize("n_sectors", [1 << 6, 1 << 9])
+def test_cturtle_collision_free_keys_follow_their_counts(n_sectors):
+    """In a crowded filter, a key no other key's patterns can cover is reported exactly when it
+    occurs at least twice; colliding keys may be missed (false negatives) or reported as
+    singletons (false positives), but nothing is reported twice and nothing foreign appears."""
+    reads = _ct_reads(9, 200, G=3000)
+    bases, offs = brute.pack(reads)
+    k = 21
+    keys, _ = oracle.cturtle(bases, offs, k, n_sectors)
+    distinct, counts, _ = oracle.count(bases, offs, k, 1)
+    free = oracle.cturtle_collision_free(distinct, n_sectors)
+    assert 0 < free.sum() < len(free)  # both kinds present
+    rep = set(int(x) for x in keys)
+    assert len(rep) == len(keys) and rep <= set(int(x) for x in distinct)
+    for key, c, f in zip(distinct, counts, free):
+        if f:
+            assert (int(key) in rep) == (c >= 2)
+
+
+def test_cturtle_error_rates_shrink_with_the_filter():
+    """Sec. 2.2: false positives plus false negatives against the exact set of k-mers seen twice
+    fall as the filter grows (4,594 such k-mers here): hundreds with 64 sectors, a handful at most
+    once the filter has ~15 bits per distinct k-mer."""
+    reads = _ct_reads(21, 300, G=6000)
+    bases, offs = brute.pack(reads)
+    k = 25
+    truth = set(int(x) for x in oracle.count(bases, offs, k, 2)[0])
+    errs = []
+    for n_sectors in (1 << 6, 1 << 8, 1 << 10, 1 << 13, 1 << 16):
+        rep = set(int(x) for x in oracle.cturtle(bases, offs, k, n_sectors)[0])
+        errs.append(len(rep - truth) + len(truth - rep))
+    assert errs[0] > errs[1] > errs[2] and errs[0] > 0.2 * len(truth)
+    assert max(errs[3:]) <= 2
