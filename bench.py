@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk", "served", "batched"])
+    ap.add_argument("--method", default="scturtle", choices=["scturtle", "cturtle"],
+                    help="cturtle: the approximate two-stage counting filter (k-mers seen twice, no counts)")
+    ap.add_argument("--cturtle-bits", type=int, default=0, help="cturtle filter bits per window (0 = default 8)")
     ap.add_argument("--jobs", type=int, default=1000, help="served: number of jobs (Poisson arrivals, 50/s)")
     ap.add_argument("--max-batch", type=int, default=4, help="served: most queued jobs batched into one run")
     ap.add_argument("--saturate-jobs", type=int, default=300,
@@ -518,10 +521,67 @@ def run_batched(args):
             "identical_results": ok}
 
 
+def run_cturtle(args):
+    """cTurtle (Sec. 2.2) on the chosen library, device-resident: k-mers/s, and its false positives and
+    false negatives against the exact set of k-mers seen at least twice (from the exact path)."""
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    if args.workload not in ("fly", "small"):
+        raise SystemExit("--method cturtle runs on the in-memory workloads (fly, small)")
+    torch.cuda.set_device(0)
+    lib, desc = workload(args.workload, args.scale, 0)
+    bases = torch.from_numpy(lib.bases).cuda()
+    offs = torch.from_numpy(lib.offsets.astype(np.int64)).cuda()
+    ctx = pkg.Context(0)
+    prm = pkg.Params.default(timing=1, cturtle_bits_per_window=args.cturtle_bits)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.turtle_frequent_device(bases, offs, lib.k, prm, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        keys, W = ctx.turtle_frequent_device(bases, offs, lib.k, prm, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ctx.stats()
+    got = keys.clone()
+    ek, _, _ = ctx.turtle_count_device(bases, offs, lib.k, 2, pkg.Params.default())
+    exact = ek.clone()
+
+    if got.dim() == 1:
+        hit = torch.isin(got, exact)
+        n_fp = int((~hit).sum())
+        n_fn = int(exact.numel() - hit.sum())
+    else:  # 128-bit keys: compare on the host
+        a = set(map(tuple, got.cpu().numpy().tolist()))
+        b = set(map(tuple, exact.cpu().numpy().tolist()))
+        n_fp, n_fn = len(a - b), len(b - a)
+    n_true = int(exact.shape[0])
+    return {"metric": "cTurtle: canonical k-mers/s (k-mers seen twice, no counts)", "value": W / (ms / 1e3),
+            "unit": METRIC, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u64" if lib.k <= 32 else "u128",
+            "config": {"workload": desc, "k": lib.k, "windows": W,
+                       "filter_bytes": st["filter_bytes"], "bits_per_window": args.cturtle_bits or 8},
+            "reported": int(got.shape[0]), "exact_seen_twice": n_true,
+            "false_positives": n_fp, "false_negatives": n_fn,
+            "fp_rate": n_fp / max(n_true, 1), "fn_rate": n_fn / max(n_true, 1),
+            "stage_ms": {k: round(v, 3) for k, v in st["stage_ms"].items() if v > 0}, "clocks": clocks}
+
+
 def main():
     args = parse()
     if args.workload == "batched":
         print(json.dumps(run_batched(args)), flush=True)
+        return
+    if args.method == "cturtle":
+        print(json.dumps(run_cturtle(args)), flush=True)
         return
     if args.workload == "served":
         print(json.dumps(run_served(args)), flush=True)

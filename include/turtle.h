@@ -101,7 +101,9 @@ typedef struct {
                                       8192 slots (1024 threads, one CTA per SM; default), 4096 = 4096 slots
                                       (512 threads, two CTAs per SM; half the distinct keys per bucket
                                       before a bucket is split) */
-    uint32_t reserved;
+    uint32_t cturtle_bits_per_window; /* turtle_frequent: bits of its two-stage filter per valid window
+                                         (rounded up to a power of two of 32-byte sectors); 0 = 8. Its
+                                         false-positive and false-negative rates fall as this grows. */
 } turtle_params;
 
 /* Fill *p with the defaults above. */
@@ -168,6 +170,26 @@ typedef struct {
 int turtle_count_device(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
                         uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, void *stream,
                         turtle_device_result *out);
+
+/*
+ * cTurtle (Sec. 2.2 of the paper): the k-mers seen at least twice, without counts, from a
+ * two-stage counting pattern-blocked Bloom filter in one pass over the windows. A key's
+ * first sighting sets its pattern in its block; a later sighting that finds that pattern
+ * complete tests and sets a second pattern in the adjacent block, and the sighting that
+ * completes the second pattern reports the key (each key at most once). Approximate, as in
+ * the paper: a singleton whose first pattern other keys have completed is reported (false
+ * positive); a repeated key whose second pattern other keys have completed is not (false
+ * negative); which colliding keys these are depends on the order the GPU takes the windows
+ * in. Keys come out ascending; the result's counts pointer is NULL. Memory: the filter
+ * (params.cturtle_bits_per_window) plus room for the reported keys (one key per valid window,
+ * at most 40% of the free device memory; TURTLE_E_CAPACITY if more keys are reported).
+ */
+int turtle_frequent(const turtle_reads *reads, int k, const turtle_params *params, void *stream,
+                    turtle_result *out);
+/* Device-resident form of turtle_frequent (arguments as turtle_count_device; out->counts NULL). */
+int turtle_frequent_device(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                           uint64_t n_reads, int k, const turtle_params *params, void *stream,
+                           turtle_device_result *out);
 
 /* Stages of one turtle_count_device call, in launch order. */
 enum {

@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
                 ("n_patterns", u32), ("pattern_seed", u64), ("timing", u32), ("l2_fetch_bytes", u32),
                 ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
                 ("stream_chunk_mib", u32), ("sort_tile", u32),
-                ("compact", u32), ("bucket_slots", u32), ("reserved", u32)]
+                ("compact", u32), ("bucket_slots", u32),
+                ("cturtle_bits_per_window", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":
@@ -105,6 +106,8 @@ def load():
         "turtle_ctx_destroy": (None, [_p]),
         "turtle_ctx_stats": (ctypes.c_int, [_p, _p]),
         "turtle_count_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p]),
+        "turtle_frequent": (ctypes.c_int, [_p, ctypes.c_int, _p, _p, _p]),
+        "turtle_frequent_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, _p, _p, _p]),
         "turtle_extract": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, _p, _p, _p, _p]),
         "turtle_filter": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, _p, u64, _p, ctypes.c_int, _p, _p]),
         "turtle_sort_compact": (ctypes.c_int, [_p, _p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
@@ -172,7 +175,8 @@ def _take(lib, res, k):
         return _shape_keys(np.zeros(0, dtype=np.uint64), 0, k), np.zeros(0, np.uint32), nw
     owner = _ResultOwner(lib, res)
     keys = np.asarray(_View(owner, ctypes.cast(res.keys, ctypes.c_void_p).value, n * w, "<u8"))
-    counts = np.asarray(_View(owner, ctypes.cast(res.counts, ctypes.c_void_p).value, n, "<u4"))
+    cptr = ctypes.cast(res.counts, ctypes.c_void_p).value
+    counts = np.asarray(_View(owner, cptr, n, "<u4")) if cptr else None
     return _shape_keys(keys, n, k), counts, nw
 
 
@@ -187,6 +191,21 @@ def turtle_count(bases, offsets, k: int, min_count: int = 2, params: Params | No
                              _stream_ptr(stream), ctypes.byref(res))
     _check(rc, "turtle_count")
     return _take(lib, res, k)
+
+
+def turtle_frequent(bases, offsets, k: int, params: Params | None = None, stream=None):
+    """cTurtle (Sec. 2.2): (keys, n_windows) of the k-mers seen at least twice, approximate, no counts;
+    keys ascending, uint64[n] or uint64[n, 2] (hi, lo)."""
+    lib = load()
+    b = _np(bases, np.uint8)
+    o = _np(offsets, np.uint64)
+    reads = _Reads(b.ctypes.data if b.size else None, o.ctypes.data, o.size - 1)
+    res = _Result()
+    rc = lib.turtle_frequent(ctypes.byref(reads), k, ctypes.byref(params) if params else None, _stream_ptr(stream),
+                             ctypes.byref(res))
+    _check(rc, "turtle_frequent")
+    keys, _, nw = _take(lib, res, k)
+    return keys, nw
 
 
 def _stream_ptr(stream):
@@ -366,6 +385,23 @@ class Context:
                                            _stream_ptr(stream), ctypes.byref(out))
         _check(rc, "turtle_count_device")
         return self._views(out)
+
+    def turtle_frequent_device(self, bases, offsets, k: int, params: Params | None = None, stream=None):
+        """cTurtle on device-resident reads: (keys, n_windows), keys a torch CUDA view of context-owned
+        memory valid until this context's next call."""
+        import torch
+        assert bases.is_cuda and offsets.is_cuda and bases.dtype == torch.uint8
+        assert offsets.dtype in (torch.int64, torch.uint64) and offsets.is_contiguous() and bases.is_contiguous()
+        out = _DeviceResult()
+        rc = self._lib.turtle_frequent_device(self._h, _dptr(bases), bases.numel(), _dptr(offsets),
+                                              offsets.numel() - 1, k, ctypes.byref(params) if params else None,
+                                              _stream_ptr(stream), ctypes.byref(out))
+        _check(rc, "turtle_frequent_device")
+        n, w = int(out.n), int(out.key_words)
+        if n == 0:
+            return torch.zeros((0, 2) if w == 2 else (0,), dtype=torch.int64, device="cuda"), int(out.n_windows)
+        keys = torch.as_tensor(_CudaArray(out.keys, (n, 2) if w == 2 else (n,), "<i8", self), device="cuda")
+        return keys, int(out.n_windows)
 
     def _views(self, out):
         import torch

@@ -160,6 +160,7 @@ void read_back(turtle_ctx *c, cudaStream_t s) {
     const uint32_t e = *c->h_err;
     if (e & ERR_BAD_OFFSETS) throw Fail{TURTLE_E_ARG};
     if (e & ERR_COUNT_OVERFLOW) throw Fail{TURTLE_E_OVERFLOW};
+    if (e & ERR_CAND_OVERFLOW) throw Fail{TURTLE_E_CAPACITY};  // an output larger than the room given to it
     if (e) throw Fail{TURTLE_E_DEVICE};
 }
 
@@ -347,10 +348,76 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     return PartOut{okeys, ocounts, n_out};
 }
 
+// cTurtle (Sec. 2.2) on packed reads with W valid windows: the two-stage counting filter reports
+// the keys seen (probably) at least twice, then they are sorted ascending. No counts.
+constexpr uint32_t CTURTLE_BITS_DEFAULT = 8;
+template <class K>
+void run_cturtle(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, const PackLayout &L, int k,
+                 const uint64_t *P, const uint64_t *V, uint64_t W, const turtle_params &prm, cudaStream_t s,
+                 DeviceOut &out) {
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+    const double bits = prm.cturtle_bits_per_window ? prm.cturtle_bits_per_window : CTURTLE_BITS_DEFAULT;
+    FilterGeom fg{};
+    fg.n_sectors = pow2_at_least((uint64_t)((double)W * bits / 256.0) + 1);
+    if (fg.n_sectors < 2) fg.n_sectors = 2;
+    fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+    fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
+    ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
+    fg.patterns = ctx_patterns(c, prm, s);
+    fg.pat_mask = prm.n_patterns - 1;
+    st.filter_bytes = 32 * fg.n_sectors;
+    // reported keys <= distinct keys <= W; room for all of them unless that exceeds 40% of free memory
+    size_t free_b = 0, total_b = 0;
+    ck(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t cap = W;
+    if ((double)cap * sizeof(K) > 0.4 * (double)free_b) cap = (uint64_t)(0.4 * (double)free_b / sizeof(K));
+    K *emit = (K *)ctx_alloc(c, sizeof(K) * (cap ? cap : 1), s);
+    ck(cudaMemsetAsync(ctr + C_CAND, 0, 8, s));
+    tm.start(TURTLE_STAGE_FILTER);
+    launch_cturtle<K>(lc, L, k, P, V, fg, fg.n_sectors - 1, emit, ctr + C_CAND, cap, err);
+    tm.stop(TURTLE_STAGE_FILTER);
+    read_back(c, s);
+    const uint64_t n = c->h_ctr[C_CAND];
+    SortScratch ss{};
+    ss.alt = ctx_alloc(c, sizeof(K) * (n ? n : 1), s);
+    ss.hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ss.lookback_words = sort_lookback_words(n, sizeof(K) / 8);
+    ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
+    ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
+    int passes = 0;
+    tm.start(TURTLE_STAGE_SORT);
+    K *sorted = launch_radix_sort<K>(lc, emit, n, 2 * k, ss, err, false, 0, &passes, 0);
+    tm.stop(TURTLE_STAGE_SORT);
+    K *okeys = (K *)ctx_alloc(c, sizeof(K) * (n ? n : 1), s, true);
+    if (n) ck(cudaMemcpyAsync(okeys, sorted, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+    read_back(c, s);
+    st.stage_launches[TURTLE_STAGE_FILTER] = 1;
+    st.stage_launches[TURTLE_STAGE_SORT] = n > 1 ? passes + 2 : 0;
+    st.sort_passes = (uint32_t)passes;
+    st.n_candidates = n;
+    st.n_out = n;
+    st.super_partitions = 1;
+    out.keys = okeys;
+    out.counts = nullptr;
+    out.n = n;
+    if (prm.timing)
+        for (int i : {(int)TURTLE_STAGE_PACK, (int)TURTLE_STAGE_VALID, (int)TURTLE_STAGE_FILTER, (int)TURTLE_STAGE_SORT}) {
+            float ms = 0.f;
+            if ((i != TURTLE_STAGE_PACK || st.stage_launches[i]) &&
+                cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess)
+                st.stage_ms[i] = ms;
+            else cudaGetLastError();
+        }
+    for (int i = 0; i < TURTLE_STAGE_COUNT; i++) st.launches += st.stage_launches[i];
+    st.scratch_bytes = c->scratch_bytes;
+    c->stats = st;
+}
+
 template <class K>
 void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
                int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s, DeviceOut &out,
-               const PrePacked *pre = nullptr, const BatchTag *tag = nullptr) {
+               const PrePacked *pre = nullptr, const BatchTag *tag = nullptr, bool cturtle = false) {
     constexpr int KW = sizeof(K) / 8;
     const LaunchCfg lc{c->sms, s};
     turtle_stats st{};
@@ -402,6 +469,10 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         return;
     }
 
+    if (cturtle) {
+        run_cturtle<K>(c, lc, tm, st, L, k, P, V, W, prm, s, out);
+        return;
+    }
     const bool use_filter = min_count >= 2;
     const bool firsts_mode = use_filter && (!prm.recount_windows || tag);  // batches recount from first sightings
     const int key_bits = 2 * k + (tag ? tag->tag_bits : 0);
@@ -747,15 +818,16 @@ struct L2Fetch {
 
 int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
                       uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, cudaStream_t s,
-                      DeviceOut &o) {
+                      DeviceOut &o, bool cturtle = false) {
     if (!c || k < 1 || k > 64 || min_count < 1 || !offsets || (n_bases && !bases)) return TURTLE_E_ARG;
     const turtle_params prm = resolve(params);
     if (!params_ok(prm)) return TURTLE_E_ARG;
     try {
         ctx_begin(c, s);
         L2Fetch l2(prm.l2_fetch_bytes);
-        if (k <= 32) run_count<uint64_t>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
-        else run_count<Key128>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o);
+        if (k <= 32) run_count<uint64_t>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o, nullptr, nullptr,
+                                         cturtle);
+        else run_count<Key128>(c, bases, n_bases, offsets, n_reads, k, min_count, prm, s, o, nullptr, nullptr, cturtle);
         ctx_end(c, s);
         return TURTLE_OK;
     } catch (Fail f) {
@@ -835,7 +907,7 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
 // Host-memory input streamed through two device staging buffers, then the path on the packed reads.
 int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off, int k,
                         uint32_t min_count, const turtle_params *params, size_t chunk, cudaStream_t s,
-                        DeviceOut &o) {
+                        DeviceOut &o, bool cturtle = false) {
     const turtle_params prm = resolve(params);
     if (!params_ok(prm)) return TURTLE_E_ARG;
     try {
@@ -844,8 +916,10 @@ int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bas
         const LaunchCfg lc{c->sms, s};
         PrePacked pp{};
         pack_streamed(c, reads, n_bases, d_off, chunk, s, pp, lc);
-        if (k <= 32) run_count<uint64_t>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp);
-        else run_count<Key128>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp);
+        if (k <= 32)
+            run_count<uint64_t>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp, nullptr,
+                                cturtle);
+        else run_count<Key128>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp, nullptr, cturtle);
         c->stats.stage_launches[TURTLE_STAGE_PACK] = (uint32_t)((n_bases + chunk - 1) / chunk + 1);
         c->stats.launches += c->stats.stage_launches[TURTLE_STAGE_PACK];
         ctx_end(c, s);
@@ -1159,6 +1233,23 @@ int turtle_count_device(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, c
     return TURTLE_OK;
 }
 
+int turtle_frequent_device(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                           uint64_t n_reads, int k, const turtle_params *params, void *stream,
+                           turtle_device_result *out) {
+    if (!out) return TURTLE_E_ARG;
+    memset(out, 0, sizeof(*out));
+    DeviceOut o;
+    const int rc = count_device_impl(c, bases, n_bases, offsets, n_reads, k, 2, params, (cudaStream_t)stream, o, true);
+    if (rc) return rc;
+    out->k = k;
+    out->key_words = k <= 32 ? 1 : 2;
+    out->n = o.n;
+    out->keys = (const uint64_t *)o.keys;
+    out->counts = nullptr;
+    out->n_windows = o.n_windows;
+    return TURTLE_OK;
+}
+
 static turtle_ctx *default_ctx(int *rc) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1192,7 +1283,7 @@ uint64_t footprint_estimate(uint64_t n_bases, uint64_t n_reads, int k, uint32_t 
 
 // Host-memory form on a given context: copy (or stream) the reads in, run the path, copy the result out.
 int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
-                    void *stream, turtle_result *out) {
+                    void *stream, turtle_result *out, bool cturtle) {
     if (!out) return TURTLE_E_ARG;
     memset(out, 0, sizeof(*out));
     if (!reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64 || min_count < 1)
@@ -1225,21 +1316,21 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         return f.code;
     }
     DeviceOut o;
-    if (streamed) rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o);
-    else rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o);
+    if (streamed) rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o, cturtle);
+    else rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o, cturtle);
     if (d_bases) cudaFreeAsync(d_bases, s);
     cudaFreeAsync(d_off, s);
     if (rc) return rc;
     const int kw = k <= 32 ? 1 : 2;
     out->keys = (uint64_t *)malloc(8 * kw * (o.n ? o.n : 1));
-    out->counts = (uint32_t *)malloc(4 * (o.n ? o.n : 1));
-    if (!out->keys || !out->counts) {
+    out->counts = o.counts ? (uint32_t *)malloc(4 * (o.n ? o.n : 1)) : nullptr;  // cTurtle keeps no counts
+    if (!out->keys || (o.counts && !out->counts)) {
         turtle_result_free(out);
         return TURTLE_E_NOMEM;
     }
     try {
         copy_to_host(c, out->keys, o.keys, 8 * kw * o.n, s);
-        copy_to_host(c, out->counts, o.counts, 4 * o.n, s);
+        if (o.counts) copy_to_host(c, out->counts, o.counts, 4 * o.n, s);
     } catch (Fail f) {
         cudaGetLastError();
         turtle_result_free(out);
@@ -1264,7 +1355,19 @@ int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const 
     int rc = 0;
     turtle_ctx *c = default_ctx(&rc);
     if (!c) return rc;
-    return count_host_impl(c, reads, k, min_count, params, stream, out);
+    return count_host_impl(c, reads, k, min_count, params, stream, out, false);
+}
+
+int turtle_frequent(const turtle_reads *reads, int k, const turtle_params *params, void *stream, turtle_result *out) {
+    if (!out) return TURTLE_E_ARG;
+    memset(out, 0, sizeof(*out));
+    if (!reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64) return TURTLE_E_ARG;
+    if (reads->offsets[reads->n_reads] < reads->offsets[0]) return TURTLE_E_ARG;
+    std::lock_guard<std::mutex> g(g_default_mu);
+    int rc = 0;
+    turtle_ctx *c = default_ctx(&rc);
+    if (!c) return rc;
+    return count_host_impl(c, reads, k, 2, params, stream, out, true);
 }
 
 int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_params *params, void *stream,

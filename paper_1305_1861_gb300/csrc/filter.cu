@@ -222,6 +222,85 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
         if (s_hist[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)s_hist[i]);
 }
 
+// cTurtle (Sec. 2.2): a two-stage counting filter. Stage 1 is pass 1's test-and-set in the key's
+// block; a window that finds its stage-1 pattern complete tests and sets a second pattern in the
+// adjacent block (sector s + 1, word (h >> 18) & 3, pattern (h >> 20) & mask), and the window whose
+// atomicOr completes that pattern reports the key. Each stage is one atomic on one word, so a key
+// is reported at most once; which colliding keys are missed or reported as singletons depends on
+// the order of the windows, as in the paper's sequential tool.
+template <class K>
+__global__ void __launch_bounds__(P1_BLOCK) k_cturtle(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                      uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
+                                                      uint64_t sector_mask, const uint64_t *__restrict__ patterns,
+                                                      uint32_t pat_mask, K *out, unsigned long long *out_count,
+                                                      uint64_t out_cap, uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    K *s_buf = reinterpret_cast<K *>(smem);
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS);
+    for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    K *wbuf = s_buf + warp * P1_BUF;
+    int nbuf = 0;
+    const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
+    for (uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp; t < tiles; t += (uint64_t)gridDim.x * P1_WARPS) {
+        const uint64_t base = t * P1_TILE;
+        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const int r = lane + WARP * i;
+            const uint64_t s = base + r;
+            const bool ok = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
+            K key{};
+            bool emit = false;
+            if (ok) {
+                key = canonical<K>(P, s, k);
+                const uint64_t h = key_hash(key);
+                const uint64_t s1 = sector_shift < 64 ? (h >> sector_shift) : 0;
+                uint64_t *a1 = filter + s1 * 4 + ((h >> 16) & 3);
+                const uint64_t m1 = s_pat[h & pat_mask];
+                bool seen = (__ldcg(a1) & m1) == m1;
+                if (!seen) seen = (atomicOr((unsigned long long *)a1, (unsigned long long)m1) & m1) == m1;
+                if (seen) {
+                    uint64_t *a2 = filter + ((s1 + 1) & sector_mask) * 4 + ((h >> 18) & 3);
+                    const uint64_t m2 = s_pat[(h >> 20) & pat_mask];
+                    if ((__ldcg(a2) & m2) != m2)
+                        emit = (atomicOr((unsigned long long *)a2, (unsigned long long)m2) & m2) != m2;
+                }
+            }
+            const uint32_t b = __ballot_sync(FULL, emit);
+            if (emit) wbuf[nbuf + __popc(b & lt)] = key;
+            nbuf += __popc(b);
+            if (nbuf >= P1_STAGE) flush_full(wbuf, nbuf, out, out_count, out_cap, err, lane);
+        }
+    }
+    __syncwarp();
+    flush_rest(wbuf, nbuf, out, out_count, out_cap, err, lane);
+}
+
+template <class K>
+void launch_cturtle(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                    const FilterGeom &f, uint64_t sector_mask, K *out, unsigned long long *out_count,
+                    uint64_t out_cap, uint32_t *err) {
+    const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
+    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS + sizeof(uint64_t) * (f.pat_mask + 1);
+    cudaFuncSetAttribute(k_cturtle<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cturtle<K>, P1_BLOCK, smem);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t need = (tiles + P1_WARPS - 1) / P1_WARPS, cap = (uint64_t)c.sms * per_sm;
+    const int grid = (int)(need < cap ? (need ? need : 1) : cap);
+    k_cturtle<K><<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, sector_mask,
+                                                     f.patterns, f.pat_mask, out, out_count, out_cap, err);
+}
+template void launch_cturtle<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
+                                       const uint64_t *, const FilterGeom &, uint64_t, uint64_t *,
+                                       unsigned long long *, uint64_t, uint32_t *);
+template void launch_cturtle<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
+                                     const FilterGeom &, uint64_t, Key128 *, unsigned long long *, uint64_t,
+                                     uint32_t *);
+
 // Number of valid windows in each of the 2^part_bits key-range parts (sizes the super-partitions).
 template <class K>
 __global__ void __launch_bounds__(256) k_part_count(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,

@@ -12,9 +12,10 @@
 
 #include "turtle.h"
 
-// Host-memory form of turtle_count on a given context (copies or streams the reads in).
+// Host-memory form of turtle_count (or, with cturtle, turtle_frequent) on a given context
+// (copies or streams the reads in).
 int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
-                    void *stream, turtle_result *out);
+                    void *stream, turtle_result *out, bool cturtle);
 
 // Upper estimate of the device memory one call needs for n_bases bases (no key-range split):
 // the reads, their packed form and bitmaps, and the per-window buffers of the post-filter stages.

@@ -95,6 +95,12 @@ void launch_split_tags(const LaunchCfg &c, K *keys, uint64_t n, int shift, uint6
 template <class K>
 void launch_tag_starts(const LaunchCfg &c, const K *keys, uint64_t n, int shift, uint64_t *starts);
 // Valid windows per key-range part (counts: 2^part_bits zeroed counters).
+// cTurtle (Sec. 2.2): two-stage counting filter; keys whose second pattern a window completes
+// are appended to out (stage 2 in sector (s + 1) & sector_mask).
+template <class K>
+void launch_cturtle(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                    const FilterGeom &f, uint64_t sector_mask, K *out, unsigned long long *out_count,
+                    uint64_t out_cap, uint32_t *err);
 template <class K>
 void launch_part_count(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                        int part_bits, unsigned long long *counts);
