@@ -474,8 +474,12 @@ def run_served(args):
     served = drive(args.max_batch)
     plain = drive(1)
     burst = jobs[: args.saturate_jobs]
-    sat_served = drive(args.max_batch, burst, paced=False)
+    # saturated: the two modes alternate twice and the second run of each counts (host-side warm-up
+    # and page-cache effects otherwise favour whichever mode runs later)
+    drive(1, burst, paced=False)
+    drive(args.max_batch, burst, paced=False)
     sat_plain = drive(1, burst, paced=False)
+    sat_served = drive(args.max_batch, burst, paced=False)
     return {"metric": "served: p50/p99 job latency and aggregate canonical k-mers/s", "value": served["kmers_per_s"],
             "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "served: %d jobs, Poisson arrivals 50/s, read bases log-uniform %.1f-%.0f Mbase, "
