@@ -137,7 +137,10 @@ int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_re
 int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
                     void *stream, turtle_result *out);
 
-/* Free the arrays of a turtle_result (safe on a zeroed or already freed result). */
+/* Free the arrays of a turtle_result (safe on a zeroed or already freed result). The library
+ * keeps recently freed result arrays (up to 8 GiB in all) and hands them out again for later
+ * results of a similar size: their pages already exist, so the device fills them without first
+ * faulting every page in. */
 void turtle_result_free(turtle_result *r);
 
 /* Static description of an error code. */

@@ -865,10 +865,67 @@ void first_touch(void *p, size_t bytes) {
     for (auto &x : th) x.join();
 }
 
-// Into a freshly allocated host buffer. Synchronises s.
-void copy_to_host(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+// Result buffers (host) are recycled: turtle_result_free keeps recent ones, up to 8 GiB in all,
+// and the next result of a similar size reuses one whose pages already exist, so the device
+// writes it at full speed without the first touch.
+std::mutex g_rbuf_mu;
+std::map<void *, size_t> g_rbuf_live;       // buffers handed out in results: pointer -> capacity
+std::multimap<size_t, void *> g_rbuf_idle;  // recycled: capacity -> pointer
+size_t g_rbuf_idle_bytes = 0;
+constexpr size_t RBUF_IDLE_MAX = (size_t)8 << 30;
+constexpr size_t RBUF_MIN = (size_t)1 << 20;  // smaller buffers are not worth keeping
+
+// *fresh: the buffer's pages may not exist yet.
+void *result_alloc(size_t bytes, bool *fresh) {
+    {
+        std::lock_guard<std::mutex> g(g_rbuf_mu);
+        auto it = g_rbuf_idle.lower_bound(bytes);
+        if (it != g_rbuf_idle.end() && it->first <= 2 * bytes + RBUF_MIN) {
+            void *p = it->second;
+            const size_t cap = it->first;
+            g_rbuf_idle.erase(it);
+            g_rbuf_idle_bytes -= cap;
+            g_rbuf_live[p] = cap;
+            *fresh = false;
+            return p;
+        }
+    }
+    void *p = malloc(bytes ? bytes : 1);
+    if (!p) return nullptr;
+    std::lock_guard<std::mutex> g(g_rbuf_mu);
+    g_rbuf_live[p] = bytes;
+    *fresh = true;
+    return p;
+}
+
+void result_release(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(g_rbuf_mu);
+    auto it = g_rbuf_live.find(p);
+    if (it == g_rbuf_live.end()) {  // not one of ours
+        free(p);
+        return;
+    }
+    const size_t cap = it->second;
+    g_rbuf_live.erase(it);
+    if (cap < RBUF_MIN || cap > RBUF_IDLE_MAX) {
+        free(p);
+        return;
+    }
+    g_rbuf_idle.emplace(cap, p);
+    g_rbuf_idle_bytes += cap;
+    while (g_rbuf_idle_bytes > RBUF_IDLE_MAX) {  // give back the smallest first
+        auto s = g_rbuf_idle.begin();
+        g_rbuf_idle_bytes -= s->first;
+        free(s->second);
+        g_rbuf_idle.erase(s);
+    }
+}
+
+// Into a host result buffer (first touched when fresh). Synchronises s.
+void copy_to_host(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s, bool fresh = true) {
     if (bytes) {
-        first_touch(dst, bytes);
+        if (fresh) first_touch(dst, bytes);
         ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
     }
     ck(cudaStreamSynchronize(s));
@@ -1003,16 +1060,17 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
                 r.k = k;
                 r.n = starts[l + 1] - starts[l];
                 r.n_windows = lib_windows[l];
-                r.keys = (uint64_t *)malloc(8 * kw * (r.n ? r.n : 1));
-                r.counts = (uint32_t *)malloc(4 * (r.n ? r.n : 1));
+                bool fk = true, fc = true;
+                r.keys = (uint64_t *)result_alloc(8 * kw * (r.n ? r.n : 1), &fk);
+                r.counts = (uint32_t *)result_alloc(4 * (r.n ? r.n : 1), &fc);
                 if (!r.keys || !r.counts) {
                     rc = TURTLE_E_NOMEM;
                     break;
                 }
                 if (r.n) {
                     try {
-                        copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os);
-                        copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, os);
+                        copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os, fk);
+                        copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, os, fc);
                     } catch (Fail f) {
                         rc = f.code;
                     }
@@ -1281,6 +1339,117 @@ uint64_t footprint_estimate(uint64_t n_bases, uint64_t n_reads, int k, uint32_t 
     return (uint64_t)(per_base * (double)n_bases) + 8 * (n_reads + 1) + (64ull << 20);
 }
 
+// Host reads, one key range, bucketed form: the reads are copied in chunks on the copy stream while
+// the GPU packs, validates and filters the windows whose bases have all arrived, so the input
+// transfer overlaps pass 1. The number of windows is known only after the last chunk, so the
+// filter, the bucket geometry and the candidate buffer are sized for n_bases windows, an upper
+// bound (the result does not depend on these sizes).
+constexpr size_t OVERLAP_MIN = (size_t)64 << 20;  // inputs from this size on overlap their copy
+
+// Positions per chunk: an eighth of the input, 16-256 MiB, a multiple of 128 (whole pass-1 tiles).
+uint64_t overlap_chunk(uint64_t n_bases) {
+    uint64_t c = (n_bases / 8 + 127) & ~(uint64_t)127;
+    return std::min<uint64_t>(std::max<uint64_t>(c, (uint64_t)16 << 20), (uint64_t)256 << 20);
+}
+template <class K>
+void run_count_overlapped(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, uint8_t *d_bases,
+                          const uint64_t *d_off, int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s,
+                          DeviceOut &out) {
+    const LaunchCfg lc{c->sms, s};
+    turtle_stats st{};
+    Timer tm{c, s, prm.timing != 0};
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+    const uint64_t n_reads = reads->n_reads;
+    const PackLayout L = PackLayout::of(n_bases);
+    uint64_t *P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
+    uint64_t *B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *V = (uint64_t *)ctx_alloc(c, 8 * L.v_words, s);
+    ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
+    ck(cudaMemsetAsync(V + (L.v_words - 2), 0, 16, s));
+    launch_mark_starts(lc, d_off, n_reads, L, S, err);  // read starts (and the offsets check) first
+    // buffers: n_bases windows at most; sizes of the filter and of the buckets: n_bases - n_reads (k - 1),
+    // the exact count when no read is shorter than k and none holds an ambiguous call
+    const uint64_t Wmax = n_bases;
+    const uint64_t lost = n_reads * (uint64_t)(k - 1);
+    const uint64_t West = std::max<uint64_t>(n_bases > lost ? n_bases - lost : 0, n_bases / 4);
+    const bool use_filter = min_count >= 2;
+    FilterGeom fg{};
+    if (use_filter) {
+        fg.n_sectors = pow2_at_least((uint64_t)((double)West * prm.filter_bits_per_window / 256.0) + 1);
+        fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+        fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
+        ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
+        fg.patterns = ctx_patterns(c, prm, s);
+        fg.pat_mask = prm.n_patterns - 1;
+        st.filter_bytes = 32 * fg.n_sectors;
+    }
+    constexpr int PART_BITS = 6;
+    int bucket_bits = 0;
+    const BucketGeom bg = bucket_geom(West, 0u, 1u << PART_BITS, PART_BITS, k, &bucket_bits);
+    const int hist_passes = (bucket_bits + 7) / 8;
+    uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
+    K *cand = (K *)ctx_alloc(c, sizeof(K) * Wmax, s);
+    K *firsts = use_filter ? cand : nullptr;  // first sightings fill the same buffer from the top
+    ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
+    const uint64_t n_words = L.v_words - 2, all_tiles = (n_bases + 127) / 128;
+    const uint64_t chunk = overlap_chunk(n_bases);
+    const uint64_t n_chunks = (n_bases + chunk - 1) / chunk;
+    uint64_t w_done = 0, t_done = 0;
+    // d_bases was allocated on s (stream-ordered): the copy stream starts after that point
+    ck(cudaEventRecord(c->ev_packed[0], s));
+    ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
+    tm.start(TURTLE_STAGE_FILTER);  // copies, packing, validity and pass 1, overlapped
+    for (uint64_t i = 0; i < n_chunks; i++) {
+        const uint64_t c0 = i * chunk, c1 = std::min<uint64_t>(c0 + chunk, n_bases);
+        const bool last = i + 1 == n_chunks;
+        ck(cudaMemcpyAsync(d_bases + c0, reads->bases + c0, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
+        ck(cudaEventRecord(c->ev_h2d[0], c->copy_stream));
+        ck(cudaStreamWaitEvent(s, c->ev_h2d[0], 0));
+        launch_pack_groups(lc, d_bases, d_off, n_reads, L, c0 / 32, last ? L.pack_groups() : c1 / 32, P, B);
+        // validity word w needs positions below 64 (w + 2); a pass-1 tile covers two words
+        const uint64_t w_ready = last ? n_words : (c1 / 64 > 1 ? c1 / 64 - 1 : 0);
+        const uint64_t t_ready = last ? all_tiles : w_ready / 2;
+        launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS, w_done, w_ready);
+        if (w_ready > w_done) w_done = w_ready;
+        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wmax, firsts, ctr + C_FIRST, Wmax, hist,
+                        hist_passes, 0, 0u, 1u << PART_BITS, nullptr, 0, nullptr, err, &bg, t_done, t_ready);
+        if (t_ready > t_done) t_done = t_ready;
+    }
+    tm.stop(TURTLE_STAGE_FILTER);
+    st.stage_launches[TURTLE_STAGE_PACK] = (uint32_t)n_chunks + 1;
+    st.stage_launches[TURTLE_STAGE_VALID] = (uint32_t)n_chunks;
+    st.stage_launches[TURTLE_STAGE_FILTER] = (uint32_t)n_chunks;
+    read_back(c, s);
+    const uint64_t W = c->h_ctr[C_WINDOWS], n_cand = c->h_ctr[C_CAND], n_first = c->h_ctr[C_FIRST];
+    st.n_windows = W;
+    st.n_candidates = n_cand;
+    st.n_firsts = n_first;
+    st.super_partitions = 1;
+    out.n_windows = W;
+    const PartOut po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, use_filter ? cand + (Wmax - n_first) : nullptr,
+                                        n_first, bg, bucket_bits, hist, true,
+                                        prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
+                                        prm.bucket_slots != 4096, s);
+    out.keys = po.keys;
+    out.counts = po.counts;
+    out.n = po.n;
+    st.n_out = po.n;
+    if (prm.timing)
+        for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
+            float ms = 0.f;
+            if ((i == TURTLE_STAGE_FILTER || st.stage_launches[i]) &&
+                cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess)
+                st.stage_ms[i] = ms;
+            else cudaGetLastError();
+        }
+    for (int i = 0; i < TURTLE_STAGE_COUNT; i++) st.launches += st.stage_launches[i];
+    st.scratch_bytes = c->scratch_bytes;
+    c->stats = st;
+}
+
 // Host-memory form on a given context: copy (or stream) the reads in, run the path, copy the result out.
 int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
                     void *stream, turtle_result *out, bool cturtle) {
@@ -1302,13 +1471,26 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         cudaGetLastError();
     }
     const bool streamed = chunk != 0;
+    // large host inputs, one key range, bucketed form: overlap the copy with pass 1
+    bool overlapped = false;
+    if (!streamed && !cturtle && prm.compact == 0 && (min_count == 1 || !prm.recount_windows) &&
+        n_bases >= OVERLAP_MIN && params_ok(prm)) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaSetDevice(c->device) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const double kb = k <= 32 ? 8.0 : 16.0;
+            const double need = (double)n_bases * (1.0 + 0.25 + 0.5 + 3.0 * kb + 8.0 + prm.filter_bits_per_window / 8.0);
+            overlapped = need <= 0.7 * (double)free_b;
+        }
+        cudaGetLastError();
+    }
     uint8_t *d_bases = nullptr;
     uint64_t *d_off = nullptr;
     try {
         ck(cudaSetDevice(c->device));
         if (!streamed) ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
         ck(cudaMallocFromPoolAsync((void **)&d_off, 8 * (reads->n_reads + 1), c->pool, s));
-        if (n_bases && !streamed) ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
+        if (n_bases && !streamed && !overlapped)
+            ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
         copy_to_device(c, d_off, reads->offsets, 8 * (reads->n_reads + 1), s);
     } catch (Fail f) {
         if (d_bases) cudaFreeAsync(d_bases, s);
@@ -1316,21 +1498,37 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         return f.code;
     }
     DeviceOut o;
-    if (streamed) rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o, cturtle);
-    else rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o, cturtle);
+    if (overlapped) {
+        try {
+            ctx_begin(c, s);
+            L2Fetch l2(prm.l2_fetch_bytes);
+            if (k <= 32) run_count_overlapped<uint64_t>(c, reads, n_bases, d_bases, d_off, k, min_count, prm, s, o);
+            else run_count_overlapped<Key128>(c, reads, n_bases, d_bases, d_off, k, min_count, prm, s, o);
+            ctx_end(c, s);
+        } catch (Fail f) {
+            rc = fail_code(s, c, f.code);
+        } catch (std::bad_alloc &) {
+            rc = fail_code(s, c, TURTLE_E_NOMEM);
+        }
+    } else if (streamed) {
+        rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o, cturtle);
+    } else {
+        rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o, cturtle);
+    }
     if (d_bases) cudaFreeAsync(d_bases, s);
     cudaFreeAsync(d_off, s);
     if (rc) return rc;
     const int kw = k <= 32 ? 1 : 2;
-    out->keys = (uint64_t *)malloc(8 * kw * (o.n ? o.n : 1));
-    out->counts = o.counts ? (uint32_t *)malloc(4 * (o.n ? o.n : 1)) : nullptr;  // cTurtle keeps no counts
+    bool fk = true, fc = true;
+    out->keys = (uint64_t *)result_alloc(8 * kw * (o.n ? o.n : 1), &fk);
+    out->counts = o.counts ? (uint32_t *)result_alloc(4 * (o.n ? o.n : 1), &fc) : nullptr;  // cTurtle: no counts
     if (!out->keys || (o.counts && !out->counts)) {
         turtle_result_free(out);
         return TURTLE_E_NOMEM;
     }
     try {
-        copy_to_host(c, out->keys, o.keys, 8 * kw * o.n, s);
-        if (o.counts) copy_to_host(c, out->counts, o.counts, 4 * o.n, s);
+        copy_to_host(c, out->keys, o.keys, 8 * kw * o.n, s, fk);
+        if (o.counts) copy_to_host(c, out->counts, o.counts, 4 * o.n, s, fc);
     } catch (Fail f) {
         cudaGetLastError();
         turtle_result_free(out);
@@ -1411,8 +1609,8 @@ int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_re
 
 void turtle_result_free(turtle_result *r) {
     if (!r) return;
-    free(r->keys);
-    free(r->counts);
+    result_release(r->keys);
+    result_release(r->counts);
     r->keys = nullptr;
     r->counts = nullptr;
     r->n = 0;

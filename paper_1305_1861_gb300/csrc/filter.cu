@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     uint64_t *hist, int hist_passes, int part_bits, uint32_t part_lo,
                                                     uint32_t part_hi, const uint64_t *__restrict__ lib_starts,
                                                     int n_libs, const uint64_t *__restrict__ lib_filter,
-                                                    BucketGeom bg, int by_bucket, uint32_t *err) {
+                                                    BucketGeom bg, int by_bucket, uint64_t t_begin, uint64_t t_end,
+                                                    uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
     // by_bucket: first sightings get their own histograms, after the candidates'
@@ -122,8 +123,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
     K *wbuf = s_buf + warp * P1_BUF * NBUF;
     K *fbuf = wbuf + P1_BUF;  // firsts staging (EMIT_FIRSTS only)
     int nbuf = 0, nfirst = 0;
-    const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
-    for (uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp; t < tiles; t += (uint64_t)gridDim.x * P1_WARPS) {
+    for (uint64_t t = t_begin + (uint64_t)blockIdx.x * P1_WARPS + warp; t < t_end; t += (uint64_t)gridDim.x * P1_WARPS) {
         const uint64_t base = t * P1_TILE;
         const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
         bool ok[P1_ILP];
@@ -352,8 +352,12 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
-                  const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket) {
-    const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
+                  const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket, uint64_t t_begin,
+                  uint64_t t_end) {
+    const uint64_t all_tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
+    if (t_end > all_tiles) t_end = all_tiles;
+    if (t_begin >= t_end) return;
+    const uint64_t tiles = t_end - t_begin;
     const bool emit_firsts = use_filter && firsts != nullptr;
     if (!hist) hist_passes = 0;
     const BucketGeom bg = bucket ? *bucket : BucketGeom{};
@@ -372,7 +376,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
                                              cand, cand_count, cand_cap, firsts, first_count, first_cap, hist,
                                              hist_passes, part_bits, part_lo, part_hi, lib_starts, n_libs,
-                                             lib_filter, bg, by_bucket, err);
+                                             lib_filter, bg, by_bucket, t_begin, t_end, err);
 }
 
 template <class K>
@@ -386,11 +390,12 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
                                      unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, const uint64_t *, int,
-                                     const uint64_t *, uint32_t *, const BucketGeom *);
+                                     const uint64_t *, uint32_t *, const BucketGeom *, uint64_t, uint64_t);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
                                    unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
-                                   const uint64_t *, int, const uint64_t *, uint32_t *, const BucketGeom *);
+                                   const uint64_t *, int, const uint64_t *, uint32_t *, const BucketGeom *, uint64_t,
+                                   uint64_t);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

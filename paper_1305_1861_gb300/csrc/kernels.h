@@ -51,8 +51,9 @@ void launch_pack_groups(const LaunchCfg &c, const uint8_t *bases, const uint64_t
 void launch_mark_starts(const LaunchCfg &c, const uint64_t *offsets, uint64_t n_reads, const PackLayout &L,
                         uint64_t *S, uint32_t *err);
 // a1/a2: V <- valid-window bits for k; *n_windows += popcount(V) (zero it first).
+// Words [w_begin, w_end) only (window starts 64 w_begin ..): word w needs positions below 64 (w + 2) packed.
 void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *B, const uint64_t *S,
-                  uint64_t *V, unsigned long long *n_windows);
+                  uint64_t *V, unsigned long long *n_windows, uint64_t w_begin = 0, uint64_t w_end = ~0ull);
 // a2 alone: keys[s] <- canonical key of every valid window start s.
 void launch_extract(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                     uint64_t *keys);
@@ -79,7 +80,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
-                  const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr);
+                  const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr, uint64_t t_begin = 0,
+                  uint64_t t_end = ~0ull);
 // Valid windows of each library of a batch (counts: n_libs zeroed counters).
 void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,
                         int n_libs, unsigned long long *counts);

@@ -101,10 +101,10 @@ __device__ __forceinline__ unsigned __int128 smear(unsigned __int128 x, int len)
 }
 
 __global__ void __launch_bounds__(256) k_valid(const uint64_t *__restrict__ B, const uint64_t *__restrict__ S,
-                                               uint64_t n_words, int k, uint64_t *__restrict__ V,
+                                               uint64_t w_begin, uint64_t w_end, int k, uint64_t *__restrict__ V,
                                                unsigned long long *n_windows) {
     uint32_t mine = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_words;
+    for (uint64_t i = w_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < w_end;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const unsigned __int128 b = ((unsigned __int128)B[i + 1] << 64) | B[i];
         const unsigned __int128 s = ((unsigned __int128)S[i + 1] << 64) | S[i];
@@ -222,9 +222,11 @@ void launch_pack(const LaunchCfg &c, const uint8_t *bases, const uint64_t *offse
 }
 
 void launch_valid(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *B, const uint64_t *S, uint64_t *V,
-                  unsigned long long *n_windows) {
+                  unsigned long long *n_windows, uint64_t w_begin, uint64_t w_end) {
     const uint64_t n_words = L.v_words - 2;
-    k_valid<<<grid_for(n_words, 256, c.sms, 8), 256, 0, c.stream>>>(B, S, n_words, k, V, n_windows);
+    if (w_end > n_words) w_end = n_words;
+    if (w_begin >= w_end) return;
+    k_valid<<<grid_for(w_end - w_begin, 256, c.sms, 8), 256, 0, c.stream>>>(B, S, w_begin, w_end, k, V, n_windows);
 }
 
 void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,

@@ -275,6 +275,19 @@ def test_host_form_matches_oracle(have_gpu):
         assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
 
 
+@pytest.mark.parametrize("k,min_count", [(31, 2), (21, 1), (45, 3)])
+def test_host_form_overlapped_copy(have_gpu, k, min_count):
+    """~100 Mbase of host reads: copied in chunks while earlier chunks are packed and filtered
+    (reads and windows straddle the chunk boundaries); the result is the oracle's."""
+    import paper_1305_1861_gb300 as pkg
+
+    lib = synth.fly(seed=12, scale=0.034)
+    assert lib.bases.size >= 64 << 20
+    keys, counts, nw = pkg.turtle_count(lib.bases, lib.offsets, k, min_count)
+    ok, oc, onw = oracle.count(lib.bases, lib.offsets, k, min_count)
+    assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+
+
 def test_fly_shaped_scaled_with_repeats_and_n(ctx):
     """Fly-shaped library at 1/100 scale (1 Mbp + repeats, 300k reads, 0.05% N): exact."""
     lib = synth.fly(seed=2, scale=0.01)
