@@ -348,6 +348,44 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     return PartOut{okeys, ocounts, n_out};
 }
 
+// Batch: one filter region per library, each sized for that library's windows (lib_w); the
+// device table gives each library's first sector and hash shift. Returns the total sectors.
+uint64_t lib_filter_regions(turtle_ctx *c, const std::vector<unsigned long long> &lib_w, float bits_per_window,
+                            uint64_t **d_table, cudaStream_t s) {
+    std::vector<uint64_t> lf(2 * lib_w.size());
+    uint64_t at = 0;
+    for (size_t l = 0; l < lib_w.size(); l++) {
+        const uint64_t sec = pow2_at_least((uint64_t)(lib_w[l] * bits_per_window / 256.0) + 1);
+        lf[2 * l] = at;
+        lf[2 * l + 1] = (uint64_t)(64 - log2_exact(sec));
+        at += sec;
+    }
+    *d_table = (uint64_t *)ctx_alloc(c, 8 * lf.size(), s);
+    ck(cudaMemcpyAsync(*d_table, lf.data(), 8 * lf.size(), cudaMemcpyHostToDevice, s));
+    return at;
+}
+
+// Batch: each library its own range of buckets, sized by its windows (lib_w); *bits = index bits.
+BucketGeom lib_buckets(turtle_ctx *c, const std::vector<unsigned long long> &lib_w, int k, int *bits,
+                       cudaStream_t s) {
+    std::vector<int> lb;
+    *bits = batch_bucket_bits(lib_w, lb);
+    std::vector<uint4> lg(lib_w.size());
+    uint32_t at = 0;
+    for (size_t l = 0; l < lib_w.size(); l++) {
+        lg[l] = make_uint4(at, 1u << lb[l], (uint32_t)(62 - lb[l]), 0u);
+        at += 1u << lb[l];
+    }
+    uint4 *d_lg = (uint4 *)ctx_alloc(c, sizeof(uint4) * lg.size(), s);
+    ck(cudaMemcpyAsync(d_lg, lg.data(), sizeof(uint4) * lg.size(), cudaMemcpyHostToDevice, s));
+    BucketGeom bg{};
+    bg.k = k;
+    bg.n_buckets = at;
+    bg.tag_shift = 2 * k;
+    bg.lib = d_lg;
+    return bg;
+}
+
 // cTurtle (Sec. 2.2) on packed reads with W valid windows: the two-stage counting filter reports
 // the keys seen (probably) at least twice, then they are sorted ascending. No counts.
 constexpr uint32_t CTURTLE_BITS_DEFAULT = 8;
@@ -545,17 +583,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         uint64_t *lib_filter = nullptr;
         if (use_filter) {
             if (tag) {  // one region per library, each sized for that library's windows
-                std::vector<uint64_t> lf(2 * tag->n_libs);
-                uint64_t at = 0;
-                for (int l = 0; l < tag->n_libs; l++) {
-                    const uint64_t sec = pow2_at_least((uint64_t)(lib_w[l] * prm.filter_bits_per_window / 256.0) + 1);
-                    lf[2 * l] = at;
-                    lf[2 * l + 1] = (uint64_t)(64 - log2_exact(sec));
-                    at += sec;
-                }
-                fg.n_sectors = at;
-                lib_filter = (uint64_t *)ctx_alloc(c, 8 * lf.size(), s);
-                ck(cudaMemcpyAsync(lib_filter, lf.data(), 8 * lf.size(), cudaMemcpyHostToDevice, s));
+                fg.n_sectors = lib_filter_regions(c, lib_w, prm.filter_bits_per_window, &lib_filter, s);
                 fg.sector_shift = 64;
             } else {
                 const double bits = (double)Wg * prm.filter_bits_per_window;
@@ -574,20 +602,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         int bucket_bits = 0;
         BucketGeom bg{};
         if (bucketed && tag) {  // batch: each library its own range of buckets, sized by its windows
-            std::vector<int> lb;
-            bucket_bits = batch_bucket_bits(lib_w, lb);
-            std::vector<uint4> lg(tag->n_libs);
-            uint32_t at = 0;
-            for (int l = 0; l < tag->n_libs; l++) {
-                lg[l] = make_uint4(at, 1u << lb[l], (uint32_t)(62 - lb[l]), 0u);
-                at += 1u << lb[l];
-            }
-            uint4 *d_lg = (uint4 *)ctx_alloc(c, sizeof(uint4) * lg.size(), s);
-            ck(cudaMemcpyAsync(d_lg, lg.data(), sizeof(uint4) * lg.size(), cudaMemcpyHostToDevice, s));
-            bg.k = k;
-            bg.n_buckets = at;
-            bg.tag_shift = 2 * k;
-            bg.lib = d_lg;
+            bg = lib_buckets(c, lib_w, k, &bucket_bits, s);
         } else if (bucketed) {  // every window of the range becomes a candidate or a first sighting: Wg of them
             bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
                              PART_BITS, k, &bucket_bits);
@@ -988,6 +1003,141 @@ int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bas
     }
 }
 
+// Host reads (one library, or a batch of them), one key range, bucketed form: the reads are copied
+// in chunks on the copy stream while the GPU packs, validates and filters the windows whose bases
+// have all arrived, so the input transfer overlaps pass 1. The number of windows is known only
+// after the last chunk: the candidate buffer holds n_bases keys (an upper bound), and the filter
+// and the buckets are sized from estimates of the windows (the result does not depend on them).
+constexpr size_t OVERLAP_MIN = (size_t)64 << 20;  // inputs from this size on overlap their copy
+
+// Positions per chunk: an eighth of the input, 16-256 MiB, a multiple of 128 (whole pass-1 tiles).
+uint64_t overlap_chunk(uint64_t n_bases) {
+    uint64_t c = (n_bases / 8 + 127) & ~(uint64_t)127;
+    return std::min<uint64_t>(std::max<uint64_t>(c, (uint64_t)16 << 20), (uint64_t)256 << 20);
+}
+struct HostPiece {  // bases [start, start + len) of the concatenated positions live at src
+    uint64_t start, len;
+    const char *src;
+};
+
+template <class K>
+void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, uint64_t n_bases, uint64_t n_reads,
+                          uint8_t *d_bases, const uint64_t *d_off, int k, uint32_t min_count,
+                          const turtle_params &prm, cudaStream_t s, DeviceOut &out, const BatchTag *tag = nullptr,
+                          const std::vector<unsigned long long> *lib_w_est = nullptr) {
+    const LaunchCfg lc{c->sms, s};
+    turtle_stats st{};
+    Timer tm{c, s, prm.timing != 0};
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+    const PackLayout L = PackLayout::of(n_bases);
+    uint64_t *P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
+    uint64_t *B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
+    uint64_t *V = (uint64_t *)ctx_alloc(c, 8 * L.v_words, s);
+    ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
+    ck(cudaMemsetAsync(V + (L.v_words - 2), 0, 16, s));
+    launch_mark_starts(lc, d_off, n_reads, L, S, err);  // read starts (and the offsets check) first
+    // buffers: n_bases windows at most; sizes of the filter and of the buckets: n_bases - n_reads (k - 1),
+    // the exact count when no read is shorter than k and none holds an ambiguous call
+    const uint64_t Wmax = n_bases;
+    const uint64_t lost = n_reads * (uint64_t)(k - 1);
+    const uint64_t West = std::max<uint64_t>(n_bases > lost ? n_bases - lost : 0, n_bases / 4);
+    const bool use_filter = min_count >= 2;
+    FilterGeom fg{};
+    uint64_t *lib_filter = nullptr;
+    if (use_filter) {
+        if (tag) {
+            fg.n_sectors = lib_filter_regions(c, *lib_w_est, prm.filter_bits_per_window, &lib_filter, s);
+            fg.sector_shift = 64;
+        } else {
+            fg.n_sectors = pow2_at_least((uint64_t)((double)West * prm.filter_bits_per_window / 256.0) + 1);
+            fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+        }
+        fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
+        ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
+        fg.patterns = ctx_patterns(c, prm, s);
+        fg.pat_mask = prm.n_patterns - 1;
+        st.filter_bytes = 32 * fg.n_sectors;
+    }
+    constexpr int PART_BITS = 6;
+    int bucket_bits = 0;
+    const BucketGeom bg = tag ? lib_buckets(c, *lib_w_est, k, &bucket_bits, s)
+                              : bucket_geom(West, 0u, 1u << PART_BITS, PART_BITS, k, &bucket_bits);
+    const int hist_passes = (bucket_bits + 7) / 8;
+    uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
+    K *cand = (K *)ctx_alloc(c, sizeof(K) * Wmax, s);
+    K *firsts = use_filter ? cand : nullptr;  // first sightings fill the same buffer from the top
+    ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
+    const uint64_t n_words = L.v_words - 2, all_tiles = (n_bases + 127) / 128;
+    const uint64_t chunk = overlap_chunk(n_bases);
+    const uint64_t n_chunks = (n_bases + chunk - 1) / chunk;
+    uint64_t w_done = 0, t_done = 0;
+    // d_bases was allocated on s (stream-ordered): the copy stream starts after that point
+    ck(cudaEventRecord(c->ev_packed[0], s));
+    ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
+    tm.start(TURTLE_STAGE_FILTER);  // copies, packing, validity and pass 1, overlapped
+    size_t pi = 0;  // first piece that may overlap the chunk
+    for (uint64_t i = 0; i < n_chunks; i++) {
+        const uint64_t c0 = i * chunk, c1 = std::min<uint64_t>(c0 + chunk, n_bases);
+        const bool last = i + 1 == n_chunks;
+        while (pi < pieces.size() && pieces[pi].start + pieces[pi].len <= c0) pi++;
+        for (size_t q = pi; q < pieces.size() && pieces[q].start < c1; q++) {
+            const uint64_t a = std::max(c0, pieces[q].start), b = std::min(c1, pieces[q].start + pieces[q].len);
+            if (b > a)
+                ck(cudaMemcpyAsync(d_bases + a, pieces[q].src + (a - pieces[q].start), b - a, cudaMemcpyHostToDevice,
+                                   c->copy_stream));
+        }
+        ck(cudaEventRecord(c->ev_h2d[0], c->copy_stream));
+        ck(cudaStreamWaitEvent(s, c->ev_h2d[0], 0));
+        launch_pack_groups(lc, d_bases, d_off, n_reads, L, c0 / 32, last ? L.pack_groups() : c1 / 32, P, B);
+        // validity word w needs positions below 64 (w + 2); a pass-1 tile covers two words
+        const uint64_t w_ready = last ? n_words : (c1 / 64 > 1 ? c1 / 64 - 1 : 0);
+        const uint64_t t_ready = last ? all_tiles : w_ready / 2;
+        launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS, w_done, w_ready);
+        if (w_ready > w_done) w_done = w_ready;
+        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wmax, firsts, ctr + C_FIRST, Wmax, hist,
+                        hist_passes, 0, 0u, 1u << PART_BITS, tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0,
+                        lib_filter, err, &bg, t_done, t_ready);
+        if (t_ready > t_done) t_done = t_ready;
+    }
+    tm.stop(TURTLE_STAGE_FILTER);
+    st.stage_launches[TURTLE_STAGE_PACK] = (uint32_t)n_chunks + 1;
+    st.stage_launches[TURTLE_STAGE_VALID] = (uint32_t)n_chunks;
+    st.stage_launches[TURTLE_STAGE_FILTER] = (uint32_t)n_chunks;
+    if (tag) {  // per-library window counts, for the results
+        ck(cudaMemsetAsync(tag->lib_windows, 0, 8 * tag->n_libs, s));
+        launch_lib_windows(lc, L, V, tag->lib_starts, tag->n_libs, tag->lib_windows);
+    }
+    read_back(c, s);
+    const uint64_t W = c->h_ctr[C_WINDOWS], n_cand = c->h_ctr[C_CAND], n_first = c->h_ctr[C_FIRST];
+    st.n_windows = W;
+    st.n_candidates = n_cand;
+    st.n_firsts = n_first;
+    st.super_partitions = 1;
+    out.n_windows = W;
+    const PartOut po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, use_filter ? cand + (Wmax - n_first) : nullptr,
+                                        n_first, bg, bucket_bits, hist, true,
+                                        prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
+                                        prm.bucket_slots != 4096, s);
+    out.keys = po.keys;
+    out.counts = po.counts;
+    out.n = po.n;
+    st.n_out = po.n;
+    if (prm.timing)
+        for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
+            float ms = 0.f;
+            if ((i == TURTLE_STAGE_FILTER || st.stage_launches[i]) &&
+                cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess)
+                st.stage_ms[i] = ms;
+            else cudaGetLastError();
+        }
+    for (int i = 0; i < TURTLE_STAGE_COUNT; i++) st.launches += st.stage_launches[i];
+    st.scratch_bytes = c->scratch_bytes;
+    c->stats = st;
+}
+
 // One batched run: libraries `idx` (same k and min_count) concatenated on the device, counted by
 // one pipeline with library-tagged keys, results split back per library into outs[] by a host
 // thread of bo, which also frees the run's device results.
@@ -1017,10 +1167,17 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         uint64_t *d_off = (uint64_t *)ctx_alloc(c, 8 * (n_reads + 1), s);
         uint64_t *d_tab = (uint64_t *)ctx_alloc(c, 8 * 2 * (n_libs + 1), s);  // lib_starts, entry_starts
         unsigned long long *d_lw = (unsigned long long *)ctx_alloc(c, 8 * n_libs, s);
-        for (int l = 0; l < n_libs; l++) {  // one copy per library straight into place
+        // the bucketed form overlaps the copy of the bases with pass 1; the global form copies first
+        const bool overlapped = prm.compact == 0 && n_bases >= OVERLAP_MIN;
+        std::vector<HostPiece> pieces;
+        std::vector<unsigned long long> w_est(n_libs);
+        for (int l = 0; l < n_libs; l++) {
             const turtle_job &j = jobs[idx[l]];
             const uint64_t nb = lib_starts[l + 1] - lib_starts[l];
-            copy_to_device(c, d_bases + lib_starts[l], j.bases + j.offsets[0], nb, s);
+            const uint64_t lost = j.n_reads * (uint64_t)(k - 1);
+            w_est[l] = std::max<uint64_t>(nb > lost ? nb - lost : 0, nb / 4);
+            if (overlapped) pieces.push_back(HostPiece{lib_starts[l], nb, j.bases + j.offsets[0]});
+            else copy_to_device(c, d_bases + lib_starts[l], j.bases + j.offsets[0], nb, s);
             copy_to_device(c, d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), s);
         }
         ck(cudaMemcpyAsync(d_tab, lib_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
@@ -1028,7 +1185,9 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         launch_batch_offsets(lc, d_src, d_tab + n_libs + 1, d_tab, n_libs, d_off, n_reads + 1);
         BatchTag tag{d_tab, n_libs, tag_bits, d_lw};
         L2Fetch l2(prm.l2_fetch_bytes);
-        run_count<K>(c, d_bases, n_bases, d_off, n_reads, k, min_count, prm, s, o, nullptr, &tag);
+        if (overlapped)
+            run_count_overlapped<K>(c, pieces, n_bases, n_reads, d_bases, d_off, k, min_count, prm, s, o, &tag, &w_est);
+        else run_count<K>(c, d_bases, n_bases, d_off, n_reads, k, min_count, prm, s, o, nullptr, &tag);
         // split on the device: library boundaries + tag bits cleared, then one copy per library
         std::vector<uint64_t> starts(n_libs + 1, ~0ull);
         if (tag_bits) {
@@ -1339,117 +1498,6 @@ uint64_t footprint_estimate(uint64_t n_bases, uint64_t n_reads, int k, uint32_t 
     return (uint64_t)(per_base * (double)n_bases) + 8 * (n_reads + 1) + (64ull << 20);
 }
 
-// Host reads, one key range, bucketed form: the reads are copied in chunks on the copy stream while
-// the GPU packs, validates and filters the windows whose bases have all arrived, so the input
-// transfer overlaps pass 1. The number of windows is known only after the last chunk, so the
-// filter, the bucket geometry and the candidate buffer are sized for n_bases windows, an upper
-// bound (the result does not depend on these sizes).
-constexpr size_t OVERLAP_MIN = (size_t)64 << 20;  // inputs from this size on overlap their copy
-
-// Positions per chunk: an eighth of the input, 16-256 MiB, a multiple of 128 (whole pass-1 tiles).
-uint64_t overlap_chunk(uint64_t n_bases) {
-    uint64_t c = (n_bases / 8 + 127) & ~(uint64_t)127;
-    return std::min<uint64_t>(std::max<uint64_t>(c, (uint64_t)16 << 20), (uint64_t)256 << 20);
-}
-template <class K>
-void run_count_overlapped(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, uint8_t *d_bases,
-                          const uint64_t *d_off, int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s,
-                          DeviceOut &out) {
-    const LaunchCfg lc{c->sms, s};
-    turtle_stats st{};
-    Timer tm{c, s, prm.timing != 0};
-    uint32_t *err = c->d_err;
-    unsigned long long *ctr = c->d_ctr;
-    const uint64_t n_reads = reads->n_reads;
-    const PackLayout L = PackLayout::of(n_bases);
-    uint64_t *P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
-    uint64_t *B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
-    uint64_t *S = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
-    uint64_t *V = (uint64_t *)ctx_alloc(c, 8 * L.v_words, s);
-    ck(cudaMemsetAsync(S, 0, 8 * L.b_words, s));
-    ck(cudaMemsetAsync(V + (L.v_words - 2), 0, 16, s));
-    launch_mark_starts(lc, d_off, n_reads, L, S, err);  // read starts (and the offsets check) first
-    // buffers: n_bases windows at most; sizes of the filter and of the buckets: n_bases - n_reads (k - 1),
-    // the exact count when no read is shorter than k and none holds an ambiguous call
-    const uint64_t Wmax = n_bases;
-    const uint64_t lost = n_reads * (uint64_t)(k - 1);
-    const uint64_t West = std::max<uint64_t>(n_bases > lost ? n_bases - lost : 0, n_bases / 4);
-    const bool use_filter = min_count >= 2;
-    FilterGeom fg{};
-    if (use_filter) {
-        fg.n_sectors = pow2_at_least((uint64_t)((double)West * prm.filter_bits_per_window / 256.0) + 1);
-        fg.sector_shift = 64 - log2_exact(fg.n_sectors);
-        fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
-        ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
-        fg.patterns = ctx_patterns(c, prm, s);
-        fg.pat_mask = prm.n_patterns - 1;
-        st.filter_bytes = 32 * fg.n_sectors;
-    }
-    constexpr int PART_BITS = 6;
-    int bucket_bits = 0;
-    const BucketGeom bg = bucket_geom(West, 0u, 1u << PART_BITS, PART_BITS, k, &bucket_bits);
-    const int hist_passes = (bucket_bits + 7) / 8;
-    uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
-    ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
-    K *cand = (K *)ctx_alloc(c, sizeof(K) * Wmax, s);
-    K *firsts = use_filter ? cand : nullptr;  // first sightings fill the same buffer from the top
-    ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
-    const uint64_t n_words = L.v_words - 2, all_tiles = (n_bases + 127) / 128;
-    const uint64_t chunk = overlap_chunk(n_bases);
-    const uint64_t n_chunks = (n_bases + chunk - 1) / chunk;
-    uint64_t w_done = 0, t_done = 0;
-    // d_bases was allocated on s (stream-ordered): the copy stream starts after that point
-    ck(cudaEventRecord(c->ev_packed[0], s));
-    ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
-    tm.start(TURTLE_STAGE_FILTER);  // copies, packing, validity and pass 1, overlapped
-    for (uint64_t i = 0; i < n_chunks; i++) {
-        const uint64_t c0 = i * chunk, c1 = std::min<uint64_t>(c0 + chunk, n_bases);
-        const bool last = i + 1 == n_chunks;
-        ck(cudaMemcpyAsync(d_bases + c0, reads->bases + c0, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
-        ck(cudaEventRecord(c->ev_h2d[0], c->copy_stream));
-        ck(cudaStreamWaitEvent(s, c->ev_h2d[0], 0));
-        launch_pack_groups(lc, d_bases, d_off, n_reads, L, c0 / 32, last ? L.pack_groups() : c1 / 32, P, B);
-        // validity word w needs positions below 64 (w + 2); a pass-1 tile covers two words
-        const uint64_t w_ready = last ? n_words : (c1 / 64 > 1 ? c1 / 64 - 1 : 0);
-        const uint64_t t_ready = last ? all_tiles : w_ready / 2;
-        launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS, w_done, w_ready);
-        if (w_ready > w_done) w_done = w_ready;
-        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wmax, firsts, ctr + C_FIRST, Wmax, hist,
-                        hist_passes, 0, 0u, 1u << PART_BITS, nullptr, 0, nullptr, err, &bg, t_done, t_ready);
-        if (t_ready > t_done) t_done = t_ready;
-    }
-    tm.stop(TURTLE_STAGE_FILTER);
-    st.stage_launches[TURTLE_STAGE_PACK] = (uint32_t)n_chunks + 1;
-    st.stage_launches[TURTLE_STAGE_VALID] = (uint32_t)n_chunks;
-    st.stage_launches[TURTLE_STAGE_FILTER] = (uint32_t)n_chunks;
-    read_back(c, s);
-    const uint64_t W = c->h_ctr[C_WINDOWS], n_cand = c->h_ctr[C_CAND], n_first = c->h_ctr[C_FIRST];
-    st.n_windows = W;
-    st.n_candidates = n_cand;
-    st.n_firsts = n_first;
-    st.super_partitions = 1;
-    out.n_windows = W;
-    const PartOut po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, use_filter ? cand + (Wmax - n_first) : nullptr,
-                                        n_first, bg, bucket_bits, hist, true,
-                                        prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
-                                        prm.bucket_slots != 4096, s);
-    out.keys = po.keys;
-    out.counts = po.counts;
-    out.n = po.n;
-    st.n_out = po.n;
-    if (prm.timing)
-        for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
-            float ms = 0.f;
-            if ((i == TURTLE_STAGE_FILTER || st.stage_launches[i]) &&
-                cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess)
-                st.stage_ms[i] = ms;
-            else cudaGetLastError();
-        }
-    for (int i = 0; i < TURTLE_STAGE_COUNT; i++) st.launches += st.stage_launches[i];
-    st.scratch_bytes = c->scratch_bytes;
-    c->stats = st;
-}
-
 // Host-memory form on a given context: copy (or stream) the reads in, run the path, copy the result out.
 int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
                     void *stream, turtle_result *out, bool cturtle) {
@@ -1502,8 +1550,11 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         try {
             ctx_begin(c, s);
             L2Fetch l2(prm.l2_fetch_bytes);
-            if (k <= 32) run_count_overlapped<uint64_t>(c, reads, n_bases, d_bases, d_off, k, min_count, prm, s, o);
-            else run_count_overlapped<Key128>(c, reads, n_bases, d_bases, d_off, k, min_count, prm, s, o);
+            const std::vector<HostPiece> pieces{HostPiece{0, n_bases, reads->bases}};
+            if (k <= 32)
+                run_count_overlapped<uint64_t>(c, pieces, n_bases, reads->n_reads, d_bases, d_off, k, min_count, prm, s,
+                                               o);
+            else run_count_overlapped<Key128>(c, pieces, n_bases, reads->n_reads, d_bases, d_off, k, min_count, prm, s, o);
             ctx_end(c, s);
         } catch (Fail f) {
             rc = fail_code(s, c, f.code);

@@ -50,3 +50,19 @@ def test_batch_equals_plain_calls(have_gpu):
     for (b, o, k, m), (keys, counts, nw) in zip(jobs, got):
         pk, pc, pn = pkg.turtle_count(b, o, k, m)
         assert nw == pn and np.array_equal(keys, pk) and np.array_equal(counts, pc)
+
+
+def test_batch_overlapped_copy_equals_plain_calls(have_gpu):
+    """A batch of more than 64 MiB copies its libraries in chunks while earlier chunks are packed
+    and filtered (chunks straddle library boundaries); each result equals the plain call's."""
+    import paper_1305_1861_gb300 as pkg
+
+    specs = synth.batched_specs(seed=7, n_libs=10, scale=0.1)
+    for sp in specs:
+        sp["k"] = 21  # one run holds them all: ~100 Mbase
+    jobs = [(l.bases, l.offsets, l.k, l.min_count) for l in map(synth.library_from_spec, specs)]
+    assert sum(b.size for b, _, _, _ in jobs) >= 64 << 20
+    got = pkg.turtle_count_batch(jobs)
+    for (b, o, k, m), (keys, counts, nw) in zip(jobs, got):
+        pk, pc, pn = pkg.turtle_count(b, o, k, m)
+        assert nw == pn and np.array_equal(keys, pk) and np.array_equal(counts, pc)
