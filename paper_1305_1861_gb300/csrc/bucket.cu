@@ -298,19 +298,25 @@ __global__ __launch_bounds__(C::THREADS, C::MINB) void k_bucket_count(const K *_
                 continue;
             }
             // first sightings of this key range: +1 for keys that are candidates too
-            for (uint64_t i = f0 + tid; i < f1; i += C::THREADS) {
-                const K x = first[i];
-                const u128 v = as_u128(x);
-                if (v < lo || v > hi) continue;
-                uint32_t h = slot_hash<C::LOG2>(x);
-                for (uint32_t probe = 0; probe < C::SLOTS; probe++) {
-                    const K y = sm.key[h];
-                    if (KeyT<K>::eq(y, x)) {
-                        if (atomicAdd(&sm.count[h], 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
-                        break;
+            for (uint64_t i = f0 + tid; i < f1; i += 4 * C::THREADS) {
+                K xs[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) xs[j] = i + j * C::THREADS < f1 ? first[i + j * C::THREADS] : E;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const K x = xs[j];
+                    const u128 v = as_u128(x);
+                    if (KeyT<K>::eq(x, E) || v < lo || v > hi) continue;
+                    uint32_t h = slot_hash<C::LOG2>(x);
+                    for (uint32_t probe = 0; probe < C::SLOTS; probe++) {
+                        const K y = sm.key[h];
+                        if (KeyT<K>::eq(y, x)) {
+                            if (atomicAdd(&sm.count[h], 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
+                            break;
+                        }
+                        if (KeyT<K>::eq(y, E)) break;
+                        h = (h + 1) & (C::SLOTS - 1);
                     }
-                    if (KeyT<K>::eq(y, E)) break;
-                    h = (h + 1) & (C::SLOTS - 1);
                 }
             }
             __syncthreads();
