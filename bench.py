@@ -35,7 +35,7 @@ HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/s
 # DRAM bytes (read + write) per unit of each kernel, from ncu captures of the current kernels on the
 # fly-shaped library at 1/10 scale (profiles/); scaled to a full launch by the units it processes.
 # A kernel is left out (traffic null) until it has been captured again after a change.
-NCU_BYTES_PER_UNIT = {"k_pass1": 99.39, "k_onesweep": 16.16, "k_bucket_count": 8.67}
+NCU_BYTES_PER_UNIT = {"k_pass1": 99.39, "k_onesweep": 16.06, "k_bucket_count": 8.66}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -293,9 +293,10 @@ def run_ours(args, rank, world):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(args.e2e_steps):  # each result is released before the next call (a streaming consumer)
         keys, counts, nw = pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count)
         keys_n = len(counts)
+        del keys, counts
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     if world > 1:
         import torch.distributed as dist
