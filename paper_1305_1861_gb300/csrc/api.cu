@@ -1,12 +1,19 @@
 // libturtle C ABI: contexts, device memory, stage orchestration, host <-> device copies.
 //
 // One call of turtle_count_device runs steps a1..a6 on one stream:
-//   pack + valid  -> W (window count)        [sync: sizes the candidate buffer and the filter]
-//   pass 1        -> candidates              [sync: sizes the sort]
-//   radix sort + run-length compaction       [sync: sizes the recount table]
-//   table insert, pass 2 (recount), threshold -> result in key order
-// Scratch comes from a per-context CUDA memory pool whose memory is retained
-// between calls, so repeated calls do not return to the driver.
+//   pack + valid -> W (window count)              [sync: sizes the filter and the key buffers]
+//   pass 1 -> candidates + first sightings, with the bucket-index digit histograms
+//                                                 [sync: their numbers]
+//   bucketed form (default): two radix passes on the bucket index for each stream, bucket
+//     bounds, the per-bucket kernel (merge, recount, threshold, sort), an output scan
+//                                                 [sync: the output size] -> gather
+//   global form: radix sort of the candidates, run-length compaction [sync], recount table,
+//     first sightings (or pass 2), threshold -> result in key order
+// Inputs larger than the device's budget run once per key range (super-partitions). Host
+// calls copy the reads in chunks alongside pass 1 (run_count_overlapped), or stream them
+// through staging buffers when they exceed a quarter of the free memory. Scratch comes from
+// a per-context CUDA memory pool whose memory is retained between calls, so repeated calls do
+// not return to the driver.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -184,7 +191,8 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
 }
 
 bool params_ok(const turtle_params &p) {
-    return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 && p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
+    return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 &&
+           p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
            p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 1 &&
            (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192);
@@ -236,9 +244,9 @@ struct PartOut {
     uint64_t n;
 };
 
-// Bucketed sort-and-compact of one key range [part_lo, part_hi) of the 2^part_bits parts: stable
-// radix sort of the candidates and of the first sightings by bucket index, bucket bounds, then per
-// bucket merge + first-sighting recount + threshold + sort, then a dense gather.
+// Bucketed sort-and-compact: stable radix sort of the candidates and of the first sightings by
+// bucket index, bucket bounds, then per bucket merge + first-sighting recount + threshold + sort,
+// then a dense gather (bucketed_part below).
 constexpr uint64_t BUCKET_WINDOWS = 16384;  // candidates + first sightings per bucket, about
 
 // Bucket-index bits actually used, given the bits wanted: 8 per sort pass, and up to three bits
@@ -289,6 +297,9 @@ int batch_bucket_bits(const std::vector<unsigned long long> &lib_w, std::vector<
     return bits;
 }
 
+// One key range: candidates cand[0, n_cand) and first sightings first_keys[0, n_first) (which may
+// sit in the top of the same buffer), bucket geometry bg with `bits` index bits and pass 1's digit
+// histograms in hist. Returns the range's output, ascending.
 template <class K>
 PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, uint32_t min_count,
                       K *cand, uint64_t n_cand, K *first_keys, uint64_t n_first, const BucketGeom &bg, int bits,
@@ -326,7 +337,7 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     K *tmp = sc == cand ? alt : cand;
     tm.start(TURTLE_STAGE_RLE);
     ck(cudaMemsetAsync(ticket, 0, 16, s));
-    // cand is free after the scatter: it receives each bucket's results at the bucket's candidate offset
+    // each bucket's results land in tmp at the bucket's candidate offset (room for all its candidates)
     launch_bucket_count<K>(lc, sc, off_c, sf, off_f, B, min_count, tmp, tmp_counts, nrep, ticket, ctr + C_UNIQUE,
                            err, large_table ? 1 : 0);
     launch_scan_u64(lc, nrep, B, out_off);
