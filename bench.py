@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--member-filter", action="store_true", help="screen first sightings with a membership bitmap")
     ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..3 (-1 = default)")
     ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
-    ap.add_argument("--compact", type=int, default=-1, help="0 = bucketed, 1 = global sort-and-compact")
+    ap.add_argument("--compact", type=int, default=-1,
+                    help="0 = bucketed, 1 = global sort-and-compact, 2 = hash-table counting")
     ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
     ap.add_argument("--pattern-bits", type=int, default=0, help="Bloom pattern bits (0 = library default)")
     ap.add_argument("--micro", action="store_true",
@@ -171,6 +172,35 @@ def cpu_baseline(lib, sample_reads: int):
 # The kernel behind each timed stage (bucketed form / global form of sort-and-compact).
 STAGE_KERNEL = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_bucket_count", "recount": "k_add_firsts"}
 STAGE_KERNEL_GLOBAL = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_rle", "recount": "k_add_firsts"}
+STAGE_KERNEL_HASH = {"filter": "k_pass1", "table": "k_hash_insert", "recount": "k_hash_firsts",
+                     "threshold": "k_hash_extract", "sort": "k_onesweep"}
+
+
+def stage_bytes_hash(stage: str, st: dict, lib):
+    """Byte model of the hash-table form (compact = 2), as stage_bytes: (bytes, launches, units).
+
+      table     sketch (candidates read), clear (table written), k_hash_insert: candidates read, one
+                slot sector read and written back each; unit = candidate
+      recount   k_hash_firsts: first sightings read, one slot sector each; unit = first sighting
+      threshold k_hash_extract: table read, kept keys written; unit = kept key
+      sort      onesweep passes over the kept keys, then one slot sector and a count per kept key;
+                unit = key-pass
+    """
+    W = st["n_windows"]
+    kw = 8 if lib.k <= 32 else 16
+    parts = max(st["super_partitions"], 1)
+    nc, nf, no = st["n_candidates"], st["n_firsts"], st["n_out"]
+    tb = st["table_bytes"]
+    passes = max(st["sort_passes"], 1)
+    if stage == "table":
+        return 2.0 * kw * nc + tb + 64.0 * nc, parts, nc
+    if stage == "recount":
+        return nf * (kw + 32.0), parts, nf
+    if stage == "threshold":
+        return tb + kw * no, parts, no
+    if stage == "sort":
+        return passes * 2.0 * kw * no + no * (kw + 36.0), passes * parts, passes * no
+    return stage_bytes(stage, st, lib, False)
 
 
 def stage_bytes(stage: str, st: dict, lib, bucketed: bool):
@@ -289,12 +319,16 @@ def run_ours(args, rank, world):
     pin_b = torch.from_numpy(lib.bases).pin_memory()
     pin_o = torch.from_numpy(lib.offsets.astype(np.uint64).view(np.int64)).pin_memory()
     keys_n = 0
-    pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count)  # warm the default context
+    prm_e2e = pkg.Params.from_buffer_copy(prm)  # the same form and knobs, without stage events
+    prm_e2e.timing = 0
+    pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count,
+                     prm_e2e)  # warm the default context
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):  # each result is released before the next call (a streaming consumer)
-        keys, counts, nw = pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count)
+        keys, counts, nw = pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count,
+                                            prm_e2e)
         keys_n = len(counts)
         del keys, counts
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
@@ -310,11 +344,14 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel, from the live per-stage CUDA events of the timed steps
     avg = {s: float(np.mean(v)) for s, v in stage_ms.items()}
     bucketed = prm.compact == 0 and not prm.recount_windows
-    dom = max(("filter", "sort", "rle", "recount"), key=lambda s: avg[s])
+    hashed = prm.compact == 2
+    kernels = STAGE_KERNEL_HASH if hashed else (STAGE_KERNEL if bucketed else STAGE_KERNEL_GLOBAL)
+    dom = max(kernels, key=lambda s: avg[s])
     hbm, src = peaks()
-    total_bytes, n_launch, units = stage_bytes(dom, st, lib, bucketed)
+    total_bytes, n_launch, units = (stage_bytes_hash(dom, st, lib) if hashed else
+                                    stage_bytes(dom, st, lib, bucketed))
     ach = total_bytes / (avg[dom] / 1e3) / 1e9  # = bytes per launch / average launch time
-    kern = (STAGE_KERNEL if bucketed else STAGE_KERNEL_GLOBAL)[dom]
+    kern = kernels[dom]
     # per-unit DRAM bytes were captured on the fly-shaped library at default parameters only
     per_unit = (NCU_BYTES_PER_UNIT.get(kern) if args.workload == "fly" and bucketed and args.filter_bits <= 0
                 and args.scale == 1.0 else None)
@@ -332,6 +369,8 @@ def run_ours(args, rank, world):
            "config": {"workload": desc, "k": lib.k, "min_count": lib.min_count, "windows": W,
                       "n_reads": lib.n_reads, "bases": int(lib.bases.size), "candidates": st["n_candidates"],
                       "unique_candidates": st["n_unique"], "reported": st["n_out"],
+                      "form": "hash table" if hashed else ("bucketed" if bucketed else "global sort"),
+                      "scratch_bytes": st["scratch_bytes"], "table_bytes": st["table_bytes"],
                       "l2": "inputs larger than L2 (%.1f GB of reads resident)" % (lib.bases.nbytes / 1e9),
                       "parallelism": "replicas%d" % world if world > 1 else "single"},
            "e2e": e2e, "roofline": roof, "clocks": clocks, "gpu_launches": launches,

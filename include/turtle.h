@@ -96,7 +96,12 @@ typedef struct {
                                       merged into run lengths, first sightings add one, counts below
                                       min_count are dropped and the rest sorted. 1 = global: LSD radix sort
                                       of all candidates, run-length compaction, recount table, threshold.
-                                      Both are exact. recount_windows = 1 uses the global form. */
+                                      2 = hash table (the hash-table side of Table 1): candidates are
+                                      counted in an open-addressing table sized from a HyperLogLog
+                                      estimate of their distinct keys, first sightings add one, the keys
+                                      whose count reaches min_count are extracted and radix-sorted.
+                                      All three are exact. recount_windows = 1 uses the global form
+                                      (0) or is ignored (2: first sightings). */
     uint32_t bucket_slots;         /* bucketed form: shared-memory table of one bucket CTA: 0 or 8192 =
                                       8192 slots (1024 threads, one CTA per SM; default), 4096 = 4096 slots
                                       (512 threads, two CTAs per SM; half the distinct keys per bucket
@@ -104,6 +109,9 @@ typedef struct {
     uint32_t cturtle_bits_per_window; /* turtle_frequent: bits of its two-stage filter per valid window
                                          (rounded up to a power of two of 32-byte sectors); 0 = 8. Its
                                          false-positive and false-negative rates fall as this grows. */
+    uint32_t hash_slots_log2;      /* compact = 2: 0 = size the table from the distinct-key estimate (load
+                                      at most 1/2); n = start with 2^n slots. A table in which a key finds
+                                      no free slot within 32 lines is doubled and the counting redone. */
 } turtle_params;
 
 /* Fill *p with the defaults above. */

@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
                 ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
                 ("stream_chunk_mib", u32), ("sort_tile", u32),
                 ("compact", u32), ("bucket_slots", u32),
-                ("cturtle_bits_per_window", u32)]
+                ("cturtle_bits_per_window", u32), ("hash_slots_log2", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":

@@ -194,7 +194,7 @@ bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 &&
            p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
-           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 1 &&
+           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 2 && p.hash_slots_log2 <= 40 &&
            (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192);
 }
 
@@ -359,6 +359,115 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     return PartOut{okeys, ocounts, n_out};
 }
 
+// HyperLogLog estimate of the number of distinct keys from 2^bits registers (Flajolet, Fusy,
+// Gandouet & Meunier 2007), with linear counting when the raw estimate is small.
+double hll_estimate(const uint32_t *regs, int bits) {
+    const double m = (double)(1u << bits);
+    double sum = 0.0;
+    int zeros = 0;
+    for (uint32_t j = 0; j < (1u << bits); j++) {
+        sum += std::ldexp(1.0, -(int)regs[j]);
+        zeros += regs[j] == 0;
+    }
+    const double e = 0.7213 / (1.0 + 1.079 / m) * m * m / sum;
+    return (e <= 2.5 * m && zeros) ? m * std::log(m / zeros) : e;
+}
+
+void ctx_free(turtle_ctx *c, void *p, cudaStream_t s) {
+    for (auto it = c->scratch.begin(); it != c->scratch.end(); ++it)
+        if (*it == p) {
+            c->scratch.erase(it);
+            cudaFreeAsync(p, s);
+            return;
+        }
+}
+
+// Hash-table form of one key range (params.compact = 2): count the candidates in an
+// open-addressing table, add the first sightings, extract the keys that reach min_count and sort
+// them, then look their counts up. Returns the range's output, ascending.
+template <class K>
+PartOut hashed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, uint32_t min_count,
+                    const K *cand, uint64_t n_cand, const K *first_keys, uint64_t n_first, int key_bits,
+                    bool check_overflow, bool result_buffers, const turtle_params &prm, cudaStream_t s) {
+    constexpr int KW = sizeof(K) / 8;
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+    const int S = hash_slots_per_line(KW);
+    const int rbits = hash_sketch_bits();
+    uint32_t *regs = (uint32_t *)ctx_alloc(c, 4u << rbits, s);
+    uint32_t *full = (uint32_t *)ctx_alloc(c, 16, s);
+    uint32_t *h_words = reinterpret_cast<uint32_t *>(c->h_hist);  // pinned, 32 KB
+    tm.start(TURTLE_STAGE_TABLE);
+    uint64_t lines = 1;
+    if (prm.hash_slots_log2) {
+        lines = std::max<uint64_t>(1, (1ull << prm.hash_slots_log2) / S);
+    } else {
+        ck(cudaMemsetAsync(regs, 0, 4u << rbits, s));
+        launch_hash_sketch<K>(lc, cand, n_cand, regs);
+        st.stage_launches[TURTLE_STAGE_TABLE] += n_cand ? 1 : 0;
+        ck(cudaMemcpyAsync(h_words, regs, 4u << rbits, cudaMemcpyDeviceToHost, s));
+        read_back(c, s);
+        const double distinct = n_cand ? hll_estimate(h_words, rbits) : 0.0;
+        // 10% above the estimate (eight standard errors of 2^12 registers), load at most 1/2
+        lines = pow2_at_least((uint64_t)(1.1 * distinct / (0.5 * S)) + 1);
+    }
+    void *table = nullptr;
+    for (;;) {
+        table = ctx_alloc(c, 128 * lines, s);
+        ck(cudaMemsetAsync(full, 0, 4, s));
+        ck(cudaMemsetAsync(ctr + C_UNIQUE, 0, 8, s));
+        launch_hash_clear<K>(lc, table, lines);
+        launch_hash_insert<K>(lc, cand, n_cand, table, lines, check_overflow, ctr + C_UNIQUE, full, err);
+        st.stage_launches[TURTLE_STAGE_TABLE] += n_cand ? 2 : 1;
+        ck(cudaMemcpyAsync(h_words, full, 4, cudaMemcpyDeviceToHost, s));
+        read_back(c, s);
+        if (!h_words[0]) break;
+        ctx_free(c, table, s);  // a key found no room: count again in a table twice as large
+        lines *= 2;
+    }
+    tm.stop(TURTLE_STAGE_TABLE);
+    st.table_bytes = std::max<uint64_t>(st.table_bytes, 128 * lines);
+    const uint64_t nu = c->h_ctr[C_UNIQUE];
+    st.n_unique += nu;
+    tm.start(TURTLE_STAGE_RECOUNT);
+    if (first_keys) launch_hash_firsts<K>(lc, first_keys, n_first, table, lines, check_overflow, err);
+    tm.stop(TURTLE_STAGE_RECOUNT);
+    st.stage_launches[TURTLE_STAGE_RECOUNT] += first_keys && n_first ? 1 : 0;
+    K *kept = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s);
+    K *alt = (K *)ctx_alloc(c, sizeof(K) * (nu ? nu : 1), s);
+    ck(cudaMemsetAsync(ctr + C_OUT, 0, 8, s));
+    tm.start(TURTLE_STAGE_THRESHOLD);
+    launch_hash_extract<K>(lc, table, lines, min_count, kept, nu, ctr + C_OUT, err);
+    tm.stop(TURTLE_STAGE_THRESHOLD);
+    st.stage_launches[TURTLE_STAGE_THRESHOLD] += 1;
+    read_back(c, s);
+    const uint64_t n_out = c->h_ctr[C_OUT];
+    SortScratch ss{};
+    ss.alt = alt;
+    ss.hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    ss.lookback_words = sort_lookback_words(n_out, KW);
+    ss.lookback = (uint64_t *)ctx_alloc(c, 8 * ss.lookback_words, s);
+    ss.tile_ctr = (uint32_t *)ctx_alloc(c, 4 * 32, s);
+    uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (n_out ? n_out : 1), s, result_buffers);
+    tm.start(TURTLE_STAGE_SORT);
+    int passes = 0;
+    K *sorted = launch_radix_sort<K>(lc, kept, n_out, key_bits, ss, err, false, 0, &passes,
+                                     prm.sort_tile == 3 ? 0 : (int)prm.sort_tile);
+    launch_hash_lookup<K>(lc, sorted, n_out, table, lines, ocounts, err);
+    tm.stop(TURTLE_STAGE_SORT);
+    st.sort_passes = (uint32_t)passes;
+    st.stage_launches[TURTLE_STAGE_SORT] += (n_out > 1 && passes ? passes + 2 : 0) + (n_out ? 1 : 0);
+    if (result_buffers) {  // the sorted keys are part of the result
+        for (auto it = c->scratch.begin(); it != c->scratch.end(); ++it)
+            if (*it == (void *)sorted) {
+                c->result.push_back(*it);
+                c->scratch.erase(it);
+                break;
+            }
+    }
+    return PartOut{sorted, ocounts, n_out};
+}
+
 // Batch: one filter region per library, each sized for that library's windows (lib_w); the
 // device table gives each library's first sector and hash shift. Returns the total sectors.
 uint64_t lib_filter_regions(turtle_ctx *c, const std::vector<unsigned long long> &lib_w, float bits_per_window,
@@ -450,6 +559,7 @@ void run_cturtle(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st
     out.keys = okeys;
     out.counts = nullptr;
     out.n = n;
+    if (prm.timing) ck(cudaStreamSynchronize(s));  // the last stage's events may still be pending
     if (prm.timing)
         for (int i : {(int)TURTLE_STAGE_PACK, (int)TURTLE_STAGE_VALID, (int)TURTLE_STAGE_FILTER, (int)TURTLE_STAGE_SORT}) {
             float ms = 0.f;
@@ -523,7 +633,9 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         return;
     }
     const bool use_filter = min_count >= 2;
-    const bool firsts_mode = use_filter && (!prm.recount_windows || tag);  // batches recount from first sightings
+    const bool hashed = prm.compact == 2;
+    // batches and the hash-table form recount from first sightings
+    const bool firsts_mode = use_filter && (!prm.recount_windows || tag || hashed);
     const int key_bits = 2 * k + (tag ? tag->tag_bits : 0);
     const int passes = sort_passes_for(key_bits);
     const uint64_t *patterns = use_filter ? ctx_patterns(c, prm, s) : nullptr;
@@ -537,8 +649,11 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     // the bucketed form of sort-and-compact; the window-recount mode uses the global form
     const bool bucketed = prm.compact == 0 && (firsts_mode || !use_filter);
     const double filter_bpw = use_filter ? prm.filter_bits_per_window / 8.0 : 0.0;
+    // Hash table: the candidate buffer, a table of at most two slots per distinct key (taken as up to
+    // half the windows) and the kept keys with their sort buffer.
     const double bytes_per_window = bucketed ? 2.0 * sizeof(K) + 8.0 + filter_bpw
-                                                  : 2.0 * sizeof(K) + 20.0 + filter_bpw;
+                                    : hashed ? 2.0 * sizeof(K) + 2.0 * sizeof(K) + filter_bpw
+                                             : 2.0 * sizeof(K) + 20.0 + filter_bpw;
     // free device memory, plus what this context's pool holds unused from earlier calls
     size_t free_b = 0, total_b = 0;
     ck(cudaMemGetInfo(&free_b, &total_b));
@@ -618,7 +733,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
                              PART_BITS, k, &bucket_bits);
         }
-        const int hist_passes = bucketed ? (bucket_bits + 7) / 8 : passes;
+        const int hist_passes = bucketed ? (bucket_bits + 7) / 8 : hashed ? 0 : passes;
         ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
         tm.start(TURTLE_STAGE_FILTER);
         launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wg, firsts, ctr + C_FIRST, Wg, hist,
@@ -627,7 +742,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
                         bucketed ? &bg : nullptr);
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;
-        if (!bucketed) ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
+        if (!bucketed && !hashed) ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
         read_back(c, s);
         const uint64_t n_cand = c->h_ctr[C_CAND];
         const uint64_t n_first = c->h_ctr[C_FIRST];
@@ -641,6 +756,9 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
                                   bucket_bits, hist, !parted,
                                   prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
                                   prm.bucket_slots != 4096, s);
+        } else if (hashed) {
+            po = hashed_part<K>(c, lc, tm, st, min_count, cand, n_cand, first_keys, n_first, key_bits,
+                                W >= 0xfffffffeull, !parted, prm, s);
         } else {
         // a4: sort + compact
         SortScratch ss{};
@@ -755,6 +873,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         }
         }  // global form
         if (prm.timing) {  // accumulate this super-partition's stage times (events are reused per part)
+            ck(cudaStreamSynchronize(s));  // the last stage's events may still be pending
             for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] += ms;
@@ -1136,6 +1255,7 @@ void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, u
     out.counts = po.counts;
     out.n = po.n;
     st.n_out = po.n;
+    if (prm.timing) ck(cudaStreamSynchronize(s));  // the last stage's events may still be pending
     if (prm.timing)
         for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
             float ms = 0.f;

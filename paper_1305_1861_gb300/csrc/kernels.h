@@ -191,4 +191,31 @@ void launch_bucket_gather(const LaunchCfg &c, const K *tmp_keys, const uint32_t 
                           const unsigned long long *off, const unsigned long long *out_off, uint32_t B, K *okeys,
                           uint32_t *ocounts);
 
+// ---------------------------------------------------------------- hash-table counting (hashcount.cu)
+// Open-addressing table of 128-byte lines (8 slots of 16 B for 64-bit keys, 4 of 32 B for 128-bit),
+// lines a power of two. regs: 2^hash_sketch_bits() zeroed uint32 HyperLogLog registers.
+int hash_sketch_bits();
+int hash_slots_per_line(int key_words);
+template <class K>
+void launch_hash_sketch(const LaunchCfg &c, const K *keys, uint64_t n, uint32_t *regs);
+template <class K>
+void launch_hash_clear(const LaunchCfg &c, void *table, uint64_t lines);
+// +1 on the slot of every key of keys[0 .. n); *n_distinct += slots taken; *full = 1 when a key found
+// no slot within its probe bound (the counts are then incomplete: clear a larger table and redo).
+template <class K>
+void launch_hash_insert(const LaunchCfg &c, const K *keys, uint64_t n, void *table, uint64_t lines,
+                        bool check_overflow, unsigned long long *n_distinct, uint32_t *full, uint32_t *err);
+// +1 on the slot of every key of keys[0 .. n) that is in the table.
+template <class K>
+void launch_hash_firsts(const LaunchCfg &c, const K *keys, uint64_t n, void *table, uint64_t lines,
+                        bool check_overflow, uint32_t *err);
+// out[0 .. *n_out) <- the keys whose count >= min_count (in no particular order; *n_out zeroed first).
+template <class K>
+void launch_hash_extract(const LaunchCfg &c, const void *table, uint64_t lines, uint32_t min_count, K *out,
+                         uint64_t cap, unsigned long long *n_out, uint32_t *err);
+// counts[i] <- count of keys[i] (every key must be in the table).
+template <class K>
+void launch_hash_lookup(const LaunchCfg &c, const K *keys, uint64_t n, const void *table, uint64_t lines,
+                        uint32_t *counts, uint32_t *err);
+
 }  // namespace turtle

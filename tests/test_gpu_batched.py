@@ -16,9 +16,10 @@ def _lib(seed, G, cov, R, k, m, err=0.01):
     return (b, o, k, m)
 
 
-@pytest.mark.parametrize("compact", [0, 1])
+@pytest.mark.parametrize("compact", [0, 1, 2])
 def test_batch_matches_oracle_per_library(have_gpu, compact):
-    """Both forms of sort-and-compact (bucketed: per-library bucket ranges; global: recount table)."""
+    """Every form of counting (bucketed: per-library bucket ranges; global: recount table; hash table:
+    one table keyed by the library-tagged keys)."""
     import paper_1305_1861_gb300 as pkg
 
     jobs = []

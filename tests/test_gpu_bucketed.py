@@ -25,8 +25,8 @@ def ctx(have_gpu):
     c.close()
 
 
-# (compact, bucket_slots, sort_tile): bucketed with both table sizes and two tile shapes, and global
-FORMS = [(0, 0, 0), (0, 8192, 3), (1, 0, 0)]
+# (compact, bucket_slots, sort_tile): bucketed with both table sizes and two tile shapes, global, hash table
+FORMS = [(0, 0, 0), (0, 8192, 3), (1, 0, 0), (2, 0, 0)]
 
 
 def _run(ctx, bases, offs, k, min_count, form):

@@ -183,9 +183,9 @@ def _check_count(ctx, bases, offs, k, min_count, params=None):
 
 @pytest.mark.parametrize("k", KS)
 @pytest.mark.parametrize("min_count", [1, 2, 3])
-@pytest.mark.parametrize("compact", [0, 1])
+@pytest.mark.parametrize("compact", [0, 1, 2])
 def test_count_small_library_all_k(ctx, k, min_count, compact):
-    """Both forms of sort-and-compact: bucketed (default) and global."""
+    """All three forms of counting the candidates: bucketed (default), global sort, hash table."""
     import paper_1305_1861_gb300 as pkg
 
     lib = synth.small(seed=k, scale=0.02)  # 20 kbp genome, 4000 reads: many tiles, ragged tails
