@@ -74,7 +74,10 @@ __global__ void k_scan_bins(uint64_t *hist) {
     h[threadIdx.x] = s[threadIdx.x];
 }
 
-template <class K, int ITEMS, int MINB, class D>
+// STABLE = false: the first pass of a sort, whose input order carries no information. Each key
+// then takes its place with one shared-memory atomic on its warp's digit counter, in any order
+// among the warp's keys of the same digit, without the warp match and broadcast.
+template <class K, int ITEMS, int MINB, class D, bool STABLE>
 __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
                                                             int shift, const uint64_t *__restrict__ bin_base,
                                                             uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
@@ -142,8 +145,19 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     // 3. stable ranking straight into shared memory: rows in order, lanes in order within a row.
     //    The leader of each group of equal digits advances the warp's counter by the group size;
     //    a warp's shared-memory atomics complete in issue order, so rows cannot overtake each other.
+    if (!STABLE) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
+        for (int i = 0; i < ITEMS; i++) {
+            if (full || (uint32_t)(i * WARP + lane) < n_in_warp) {
+                const uint32_t d = (dig[i >> 2] >> (8 * (i & 3))) & 0xffu;
+                const uint32_t pos = atomicAdd(&whist[warp][d], 1u);
+                skeys[pos] = key[i];
+                sdig[pos] = (uint8_t)d;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < (STABLE ? ITEMS : 0); i++) {
         const bool valid = full || (uint32_t)(i * WARP + lane) < n_in_warp;
         const uint32_t d = valid ? ((dig[i >> 2] >> (8 * (i & 3))) & 0xffu) : (BINS + lane);
         const uint32_t peers = __match_any_sync(FULL, d);
@@ -173,15 +187,24 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     }
 }
 
-template <class K, int V, class D = RawDigit<K>>
-static void onesweep_pass(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
-                          uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err, D digit = D{}) {
+template <class K, int V, class D, bool STABLE>
+static void onesweep_launch(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
+                            uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err, D digit) {
     constexpr int ITEMS = SortCfg<K>::V_ITEMS[V], MINB = SortCfg<K>::V_MINB[V];
     const uint64_t tiles = (n + S_BLOCK * ITEMS - 1) / (S_BLOCK * ITEMS);
     const size_t smem = sizeof(K) * S_BLOCK * ITEMS;
-    cudaFuncSetAttribute(k_onesweep<K, ITEMS, MINB, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_onesweep<K, ITEMS, MINB, D><<<(int)tiles, S_BLOCK, smem, c.stream>>>(src, dst, n, shift, bin_base, lookback,
-                                                                          tile_ctr, epoch, err, digit);
+    auto kern = k_onesweep<K, ITEMS, MINB, D, STABLE>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(int)tiles, S_BLOCK, smem, c.stream>>>(src, dst, n, shift, bin_base, lookback, tile_ctr, epoch, err, digit);
+}
+
+// One digit pass; stable = false for the first pass of a sort.
+template <class K, int V, class D = RawDigit<K>>
+static void onesweep_pass(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
+                          uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err, D digit = D{},
+                          bool stable = true) {
+    if (stable) onesweep_launch<K, V, D, true>(c, src, dst, n, shift, bin_base, lookback, tile_ctr, epoch, err, digit);
+    else onesweep_launch<K, V, D, false>(c, src, dst, n, shift, bin_base, lookback, tile_ctr, epoch, err, digit);
 }
 
 template <class K>
@@ -203,11 +226,13 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
     }
     k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
     K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
+    int done = 0;  // the first pass run needs no stability: the input order carries no information
     for (int p = 0; p < passes; p++) {
         if ((skip_mask >> p) & 1u) continue;  // every key has the same digit here: the pass would be a copy
         auto pass = variant == 0 ? onesweep_pass<K, 0> : (variant == 1 ? onesweep_pass<K, 1> : onesweep_pass<K, 2>);
         pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err,
-             RawDigit<K>{});
+             RawDigit<K>{}, done > 0);
+        done++;
         if (passes_run) (*passes_run)++;
         K *t = src;
         src = dst;
@@ -242,7 +267,7 @@ K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom 
         auto pass = variant == 0 ? onesweep_pass<K, 0, BucketDigit<K>>
                                  : (variant == 1 ? onesweep_pass<K, 1, BucketDigit<K>> : onesweep_pass<K, 2, BucketDigit<K>>);
         pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err,
-             dig);
+             dig, p > 0);
         if (passes_run) (*passes_run)++;
         K *t = src;
         src = dst;
