@@ -4,7 +4,7 @@
 // merges runs of equal keys. On the GPU the sort is a least-significant-digit
 // radix sort in the onesweep style (Adinets & Merrill 2022): one kernel reads the
 // keys once and builds the 256-bin histograms of every 8-bit digit; then each
-// digit pass is ONE kernel in which a tile ranks its keys locally (warp match +
+// digit pass is ONE kernel in which a tile ranks its keys locally (warp ballots +
 // per-warp counters, stable), publishes its per-digit counts, obtains the counts
 // of all earlier tiles through decoupled look-back (one status chain per digit)
 // and scatters its keys, staged through shared memory so that each run of equal
@@ -142,9 +142,8 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
         }
     }
     __syncthreads();
-    // 3. stable ranking straight into shared memory: rows in order, lanes in order within a row.
-    //    The leader of each group of equal digits advances the warp's counter by the group size;
-    //    a warp's shared-memory atomics complete in issue order, so rows cannot overtake each other.
+    // 3. ranking straight into shared memory. Stable: rows in order, lanes in order within a row,
+    //    equal digits found by ballots. Unstable (first pass): one shared atomic per key.
     if (!STABLE) {
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
@@ -160,11 +159,22 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     for (int i = 0; i < (STABLE ? ITEMS : 0); i++) {
         const bool valid = full || (uint32_t)(i * WARP + lane) < n_in_warp;
         const uint32_t d = valid ? ((dig[i >> 2] >> (8 * (i & 3))) & 0xffu) : (BINS + lane);
-        const uint32_t peers = __match_any_sync(FULL, d);
+        uint32_t peers = FULL;  // lanes whose digit equals this lane's: one ballot per digit bit
+#pragma unroll
+        for (int b = 0; b < 9; b++) {
+            if (b == 8 && full) break;  // bit 8 only separates the invalid lanes of a partial tile
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(FULL, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        // Every peer reads the warp's counter for its digit; then the group's highest lane advances
+        // it by the group size (one writer per digit: the warp owns its counters).
         const int leader = 31 - __clz(peers);
         uint32_t pos = 0;
-        if (valid && lane == leader) pos = atomicAdd(&whist[warp][d], (uint32_t)__popc(peers));
-        pos = __shfl_sync(FULL, pos, leader);
+        if (valid) pos = whist[warp][d];
+        __syncwarp();
+        if (valid && lane == leader) whist[warp][d] = pos + (uint32_t)__popc(peers);
+        __syncwarp();
         if (valid) {
             skeys[pos + __popc(peers & lt)] = key[i];
             sdig[pos + __popc(peers & lt)] = (uint8_t)d;
