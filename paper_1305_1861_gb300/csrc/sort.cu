@@ -24,8 +24,8 @@ constexpr int MAX_PASSES = 16;
 // Variant 0 is the default; the others trade tile size against occupancy.
 template <class K> struct SortCfg;
 template <> struct SortCfg<uint64_t> {
-    static constexpr int V_ITEMS[3] = {32, 20, 24};  // default: 8192 keys (64 KB) per tile, 2 CTAs/SM
-    static constexpr int V_MINB[3] = {2, 3, 2};
+    static constexpr int V_ITEMS[3] = {32, 16, 24};  // default: 8192 keys (64 KB) per tile, 2 CTAs/SM
+    static constexpr int V_MINB[3] = {2, 4, 2};
     static constexpr int MIN_TILE = 256 * 16;
 };
 template <> struct SortCfg<Key128> {
