@@ -23,15 +23,16 @@ constexpr int MAX_PASSES = 16;
 // Onesweep tile shapes (keys per thread, CTAs per SM), selected at run time (params.sort_tile).
 // Variant 0 is the default; the others trade tile size against occupancy.
 template <class K> struct SortCfg;
+constexpr int min3(const int (&v)[3]) { return v[0] < v[1] ? (v[0] < v[2] ? v[0] : v[2]) : (v[1] < v[2] ? v[1] : v[2]); }
 template <> struct SortCfg<uint64_t> {
     static constexpr int V_ITEMS[3] = {32, 16, 24};  // default: 8192 keys (64 KB) per tile, 2 CTAs/SM
     static constexpr int V_MINB[3] = {2, 4, 2};
-    static constexpr int MIN_TILE = 256 * 16;
+    static constexpr int MIN_TILE = 256 * min3(V_ITEMS);  // sizes the look-back status array
 };
 template <> struct SortCfg<Key128> {
     static constexpr int V_ITEMS[3] = {16, 8, 12};   // default: 4096 keys (64 KB) per tile
     static constexpr int V_MINB[3] = {2, 3, 2};
-    static constexpr int MIN_TILE = 256 * 8;
+    static constexpr int MIN_TILE = 256 * min3(V_ITEMS);
 };
 
 int sort_passes_for(int key_bits) { return (key_bits + 7) / 8; }
@@ -201,6 +202,7 @@ template <class K, int V, class D, bool STABLE>
 static void onesweep_launch(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
                             uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err, D digit) {
     constexpr int ITEMS = SortCfg<K>::V_ITEMS[V], MINB = SortCfg<K>::V_MINB[V];
+    static_assert(S_BLOCK * ITEMS >= SortCfg<K>::MIN_TILE, "look-back array sized for larger tiles");
     const uint64_t tiles = (n + S_BLOCK * ITEMS - 1) / (S_BLOCK * ITEMS);
     const size_t smem = sizeof(K) * S_BLOCK * ITEMS;
     auto kern = k_onesweep<K, ITEMS, MINB, D, STABLE>;
