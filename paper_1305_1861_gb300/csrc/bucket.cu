@@ -157,10 +157,21 @@ struct BucketSmem {
     unsigned long long out_at, n_distinct;
 };
 
+// +1 on a slot's count. A bucket with fewer than 2^32 - 2 keys cannot overflow a count, and then
+// the add needs no result.
+__device__ __forceinline__ void bt_add(uint32_t *count, bool check, uint32_t *err) {
+    if (check) {
+        if (atomicAdd(count, 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
+    } else {
+        atomicAdd(count, 1u);
+    }
+}
+
 // Insert one candidate: claim its slot or add to the slot that holds it. Gives up (returns) once
-// the table has been declared over its limit for this attempt.
+// the table has been declared over its limit for this attempt. (Reading a 64-bit slot before the
+// compare-and-swap, to skip the swap for keys already present, was slower.)
 template <class K, class C>
-__device__ __forceinline__ void bt_insert(BucketSmem<K, C> &sm, K key, uint32_t *err) {
+__device__ __forceinline__ void bt_insert(BucketSmem<K, C> &sm, K key, bool check, uint32_t *err) {
     const K E = empty_key<K>();
     uint32_t h = slot_hash<C::LOG2>(key);
     for (uint32_t probe = 0; probe < C::SLOTS; probe++) {
@@ -174,7 +185,7 @@ __device__ __forceinline__ void bt_insert(BucketSmem<K, C> &sm, K key, uint32_t 
             return;
         }
         if (KeyT<K>::eq(old, key)) {
-            if (atomicAdd(&sm.count[h], 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
+            bt_add(&sm.count[h], check, err);
             return;
         }
         h = (h + 1) & (C::SLOTS - 1);
@@ -216,6 +227,7 @@ __global__ __launch_bounds__(C::THREADS, C::MINB) void k_bucket_count(const K *_
         if (b >= B) break;
         const uint64_t c0 = off_c[b], c1 = off_c[b + 1];
         const uint64_t f0 = first ? off_f[b] : 0, f1 = first ? off_f[b + 1] : 0;
+        const bool check = (c1 - c0) + (f1 - f0) >= 0xfffffffeull;  // a count could reach 2^32 - 2
         bool narrowed = false;
         while (sm.top > 0) {  // uniform: every thread reads top after the same barrier
             const u128 lo = sm.lo[sm.top - 1], hi = sm.hi[sm.top - 1];
@@ -239,7 +251,7 @@ __global__ __launch_bounds__(C::THREADS, C::MINB) void k_bucket_count(const K *_
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const u128 v = as_u128(kk[j]);
-                    if (!KeyT<K>::eq(kk[j], E) && v >= lo && v <= hi) bt_insert(sm, kk[j], err);
+                    if (!KeyT<K>::eq(kk[j], E) && v >= lo && v <= hi) bt_insert(sm, kk[j], check, err);
                 }
             }
             __syncthreads();
@@ -311,7 +323,7 @@ __global__ __launch_bounds__(C::THREADS, C::MINB) void k_bucket_count(const K *_
                     for (uint32_t probe = 0; probe < C::SLOTS; probe++) {
                         const K y = sm.key[h];
                         if (KeyT<K>::eq(y, x)) {
-                            if (atomicAdd(&sm.count[h], 1u) >= 0xfffffffeu) atomicOr(err, ERR_COUNT_OVERFLOW);
+                            bt_add(&sm.count[h], check, err);
                             break;
                         }
                         if (KeyT<K>::eq(y, E)) break;
