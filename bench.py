@@ -35,7 +35,7 @@ HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/s
 # DRAM bytes (read + write) per unit of each kernel, from ncu captures of the current kernels on the
 # fly-shaped library at 1/10 scale (profiles/); scaled to a full launch by the units it processes.
 # A kernel is left out (traffic null) until it has been captured again after a change.
-NCU_BYTES_PER_UNIT = {"k_pass1": 99.39, "k_onesweep": 16.06, "k_bucket_count": 8.66}
+NCU_BYTES_PER_UNIT = {"k_pass1": 99.39, "k_onesweep": 16.18, "k_bucket_count": 8.66, "k_hash_insert": 221.8}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -353,8 +353,8 @@ def run_ours(args, rank, world):
     ach = total_bytes / (avg[dom] / 1e3) / 1e9  # = bytes per launch / average launch time
     kern = kernels[dom]
     # per-unit DRAM bytes were captured on the fly-shaped library at default parameters only
-    per_unit = (NCU_BYTES_PER_UNIT.get(kern) if args.workload == "fly" and bucketed and args.filter_bits <= 0
-                and args.scale == 1.0 else None)
+    per_unit = (NCU_BYTES_PER_UNIT.get(kern) if args.workload == "fly" and (bucketed or hashed)
+                and args.filter_bits <= 0 and args.scale == 1.0 else None)
     traffic = per_unit * units / n_launch if per_unit else None
     roof = {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
