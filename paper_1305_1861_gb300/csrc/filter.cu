@@ -88,7 +88,7 @@ __device__ __forceinline__ void hist_keys(const K *buf, int count, uint32_t *s_h
 // (when EMIT_FIRSTS) the windows whose atomicOr completed their pattern go to
 // firsts. Since that atomicOr is one linearizable operation, at most one
 // occurrence of a key can ever be a first.
-template <class K, bool USE_FILTER, bool EMIT_FIRSTS>
+template <class K, bool USE_FILTER, bool EMIT_FIRSTS, bool BATCHED>
 __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
                                                     uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
                                                     const uint64_t *__restrict__ patterns, uint32_t pat_mask,
@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
     uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
     __shared__ uint64_t s_lib[65];
     __shared__ uint64_t s_lf[128];  // per-library filter region: first sector, shift of the hash
-    if (n_libs)
+    if (BATCHED)
         for (int i = threadIdx.x; i <= n_libs; i += P1_BLOCK) s_lib[i] = lib_starts[i];
-    if (n_libs && lib_filter)
+    if (BATCHED && lib_filter)
         for (int i = threadIdx.x; i < 2 * n_libs; i += P1_BLOCK) s_lf[i] = lib_filter[i];
     if (USE_FILTER)
         for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
@@ -131,6 +131,15 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
         uint64_t *addr[P1_ILP];
         uint64_t mask[P1_ILP];
         uint32_t libi[P1_ILP];
+        int lib0 = 0;  // batched form: library of the tile's first position (binary search, once per tile)
+        if (BATCHED) {
+            int hi = n_libs;
+            while (hi - lib0 > 1) {
+                const int mid = (lib0 + hi) >> 1;
+                if (s_lib[mid] <= base) lib0 = mid;
+                else hi = mid;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
             const int r = lane + WARP * i;
@@ -138,13 +147,9 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             ok[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
             if (ok[i]) {
                 key[i] = canonical<K>(P, s, k);
-                if (n_libs) {  // batched form: tag the key with its library (binary search of its position)
-                    int lo = 0, hi = n_libs;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_lib[mid] <= s) lo = mid;
-                        else hi = mid;
-                    }
+                if (BATCHED) {  // batched form: tag the key with its library (the tile's, or a later one)
+                    int lo = lib0;
+                    while (lo + 1 < n_libs && s_lib[lo + 1] <= s) lo++;
                     key[i] = add_tag(key[i], (uint32_t)lo, 2 * k);
                     libi[i] = (uint32_t)lo;
                 }
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                 if (USE_FILTER) {
                     const uint64_t h = key_hash(key[i]);
                     uint64_t sector;
-                    if (n_libs && lib_filter) {  // batched: each library has its own region, hot in L2 while its
+                    if (BATCHED && lib_filter) {  // batched: each library has its own region, hot in L2 while its
                         const uint64_t sh = s_lf[2 * libi[i] + 1];  // windows are being processed
                         sector = s_lf[2 * libi[i]] + (sh < 64 ? (h >> sh) : 0);
                     } else {
@@ -365,7 +370,11 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
                         4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) +
                         (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
-    auto kern = emit_firsts ? k_pass1<K, true, true> : (use_filter ? k_pass1<K, true, false> : k_pass1<K, false, false>);
+    // the batched form (n_libs > 0) has kernels of its own: the others carry none of its library lookups
+    auto kern = n_libs ? (emit_firsts ? k_pass1<K, true, true, true>
+                                      : (use_filter ? k_pass1<K, true, false, true> : k_pass1<K, false, false, true>))
+                       : (emit_firsts ? k_pass1<K, true, true, false>
+                                      : (use_filter ? k_pass1<K, true, false, false> : k_pass1<K, false, false, false>));
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P1_BLOCK, smem);

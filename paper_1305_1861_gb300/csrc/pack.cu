@@ -129,8 +129,16 @@ __global__ void __launch_bounds__(256) k_extract(const uint64_t *__restrict__ P,
 }
 
 // Per-library valid-window counts: each 64-position word is split among the libraries it touches.
-__global__ void k_lib_windows(const uint64_t *__restrict__ V, uint64_t n_words, const uint64_t *__restrict__ lib_starts,
-                              int n_libs, unsigned long long *counts) {
+__global__ void __launch_bounds__(256) k_lib_windows(const uint64_t *__restrict__ V, uint64_t n_words,
+                                                     const uint64_t *__restrict__ lib_starts, int n_libs,
+                                                     unsigned long long *counts) {
+    // The library table and the counts stay in shared memory: one global add per block and library
+    // (a global add per word would serialise on the few library counters).
+    __shared__ uint64_t s_lib[65];
+    __shared__ unsigned long long s_cnt[64];
+    for (int i = threadIdx.x; i <= n_libs; i += blockDim.x) s_lib[i] = lib_starts[i];
+    for (int i = threadIdx.x; i < n_libs; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_words;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t v = V[i];
@@ -139,18 +147,21 @@ __global__ void k_lib_windows(const uint64_t *__restrict__ V, uint64_t n_words, 
         int lo = 0, hi = n_libs;  // library holding p0
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (lib_starts[mid] <= p0) lo = mid;
+            if (s_lib[mid] <= p0) lo = mid;
             else hi = mid;
         }
-        for (int l = lo; l < n_libs && lib_starts[l] < p1; l++) {
-            const uint64_t a = lib_starts[l] > p0 ? lib_starts[l] - p0 : 0;
-            const uint64_t b = lib_starts[l + 1] < p1 ? lib_starts[l + 1] - p0 : 64;
+        for (int l = lo; l < n_libs && s_lib[l] < p1; l++) {
+            const uint64_t a = s_lib[l] > p0 ? s_lib[l] - p0 : 0;
+            const uint64_t b = s_lib[l + 1] < p1 ? s_lib[l + 1] - p0 : 64;
             if (b <= a) continue;
             const uint64_t m = (b - a == 64) ? ~0ull : (((1ull << (b - a)) - 1) << a);
             const int c = __popcll(v & m);
-            if (c) atomicAdd(&counts[l], (unsigned long long)c);
+            if (c) atomicAdd(&s_cnt[l], (unsigned long long)c);
         }
     }
+    __syncthreads();
+    for (int l = threadIdx.x; l < n_libs; l += blockDim.x)
+        if (s_cnt[l]) atomicAdd(&counts[l], s_cnt[l]);
 }
 
 // Concatenated per-library offsets -> offsets into the concatenated bases (one thread per output entry).
