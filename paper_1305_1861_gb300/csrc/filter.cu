@@ -88,7 +88,12 @@ __device__ __forceinline__ void hist_keys(const K *buf, int count, uint32_t *s_h
 // (when EMIT_FIRSTS) the windows whose atomicOr completed their pattern go to
 // firsts. Since that atomicOr is one linearizable operation, at most one
 // occurrence of a key can ever be a first.
-template <class K, bool USE_FILTER, bool EMIT_FIRSTS, bool BATCHED>
+// MODE bits: P1_BATCHED (windows tagged with their library), P1_PARTED (only the windows of key-range
+// parts [part_lo, part_hi)), P1_BY_BUCKET (histograms of the bucket index rather than the key). Each
+// combination is its own kernel, so none carries the lookups of the forms it does not serve.
+constexpr int P1_BATCHED = 1, P1_PARTED = 2, P1_BY_BUCKET = 4;
+
+template <class K, bool USE_FILTER, bool EMIT_FIRSTS, int MODE>
 __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
                                                     uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
                                                     const uint64_t *__restrict__ patterns, uint32_t pat_mask,
@@ -101,8 +106,11 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
+    constexpr bool BATCHED = (MODE & P1_BATCHED) != 0, PARTED = (MODE & P1_PARTED) != 0;
+    constexpr bool BY_BUCKET = (MODE & P1_BY_BUCKET) != 0;
+    (void)by_bucket;
     // by_bucket: first sightings get their own histograms, after the candidates'
-    const int n_hist = 256 * hist_passes * (by_bucket && EMIT_FIRSTS ? 2 : 1);
+    const int n_hist = 256 * hist_passes * (BY_BUCKET && EMIT_FIRSTS ? 2 : 1);
     K *s_buf = reinterpret_cast<K *>(smem);
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
     uint32_t *s_fhist = s_hist + 256 * hist_passes;
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                     key[i] = add_tag(key[i], (uint32_t)lo, 2 * k);
                     libi[i] = (uint32_t)lo;
                 }
-                if (part_bits) {  // keys of other key ranges wait for their own super-partition
+                if (PARTED) {  // keys of other key ranges wait for their own super-partition
                     const uint32_t pt = key_part(key[i], k, part_bits);
                     ok[i] = pt >= part_lo && pt < part_hi;
                 }
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             nbuf += __popc(b);
             if (nbuf >= P1_STAGE) {
                 __syncwarp();
-                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane, bg, by_bucket);
+                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane, bg, BY_BUCKET);
                 flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
             }
             if (EMIT_FIRSTS) {
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                 if (f) fbuf[nfirst + __popc(bf & lt)] = key[i];
                 nfirst += __popc(bf);
                 if (nfirst >= P1_STAGE) {
-                    if (by_bucket) {
+                    if (BY_BUCKET) {
                         __syncwarp();
                         hist_keys(fbuf, P1_STAGE, s_fhist, hist_passes, lane, bg, true);
                     }
@@ -216,10 +224,10 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
         }
     }
     __syncwarp();
-    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane, bg, by_bucket);
+    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane, bg, BY_BUCKET);
     flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
     if (EMIT_FIRSTS) {
-        if (by_bucket) hist_keys(fbuf, nfirst, s_fhist, hist_passes, lane, bg, true);
+        if (BY_BUCKET) hist_keys(fbuf, nfirst, s_fhist, hist_passes, lane, bg, true);
         flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
     }
     __syncthreads();
@@ -352,6 +360,26 @@ __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys,
     }
 }
 
+template <class K, bool F, bool E>
+static auto pass1_by_mode(int mode) -> decltype(&k_pass1<K, F, E, 0>) {
+    switch (mode) {  // the combinations the pipeline uses (batches are never split into key ranges)
+    case P1_BATCHED: return k_pass1<K, F, E, P1_BATCHED>;
+    case P1_PARTED: return k_pass1<K, F, E, P1_PARTED>;
+    case P1_BY_BUCKET: return k_pass1<K, F, E, P1_BY_BUCKET>;
+    case P1_BATCHED | P1_BY_BUCKET: return k_pass1<K, F, E, P1_BATCHED | P1_BY_BUCKET>;
+    case P1_PARTED | P1_BY_BUCKET: return k_pass1<K, F, E, P1_PARTED | P1_BY_BUCKET>;
+    case P1_BATCHED | P1_PARTED: return k_pass1<K, F, E, P1_BATCHED | P1_PARTED>;
+    case P1_BATCHED | P1_PARTED | P1_BY_BUCKET: return k_pass1<K, F, E, P1_BATCHED | P1_PARTED | P1_BY_BUCKET>;
+    default: return k_pass1<K, F, E, 0>;
+    }
+}
+template <class K>
+static auto pass1_kernel(bool use_filter, bool emit_firsts, int mode) -> decltype(&k_pass1<K, true, true, 0>) {
+    if (emit_firsts) return pass1_by_mode<K, true, true>(mode);
+    if (use_filter) return pass1_by_mode<K, true, false>(mode);
+    return pass1_by_mode<K, false, false>(mode);
+}
+
 template <class K>
 void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                   bool use_filter, const FilterGeom &f, K *cand, unsigned long long *cand_count, uint64_t cand_cap,
@@ -370,11 +398,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
                         4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) +
                         (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
-    // the batched form (n_libs > 0) has kernels of its own: the others carry none of its library lookups
-    auto kern = n_libs ? (emit_firsts ? k_pass1<K, true, true, true>
-                                      : (use_filter ? k_pass1<K, true, false, true> : k_pass1<K, false, false, true>))
-                       : (emit_firsts ? k_pass1<K, true, true, false>
-                                      : (use_filter ? k_pass1<K, true, false, false> : k_pass1<K, false, false, false>));
+    const int mode = (n_libs ? P1_BATCHED : 0) | (part_bits ? P1_PARTED : 0) | (by_bucket ? P1_BY_BUCKET : 0);
+    auto kern = pass1_kernel<K>(use_filter, emit_firsts, mode);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P1_BLOCK, smem);
