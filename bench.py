@@ -547,16 +547,27 @@ def run_batched(args):
     def batched():
         return pkg.turtle_count_batch(jobs)
 
+    # The two forms alternate step by step and each reports its median, so a drift in the host's
+    # speed during the run (boxes differ and vary by up to 2x on the host side) hits both alike.
+    fns = (("plain_64_calls", plain), ("batched", batched))
+    for _ in range(max(1, args.warmup)):
+        for _, fn in fns:
+            out = fn()
+            del out
+    times = {name: [] for name, _ in fns}
+    W = 0
+    for step in range(args.steps):
+        for name, fn in (fns if step % 2 == 0 else fns[::-1]):
+            t0 = time.perf_counter()
+            out = fn()
+            times[name].append(time.perf_counter() - t0)
+            W = sum(o[2] for o in out)
+            del out
     res = {}
-    for name, fn in (("plain_64_calls", plain), ("batched", batched)):
-        for _ in range(max(1, args.warmup)):
-            out = fn()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            out = fn()
-        dt = (time.perf_counter() - t0) / args.steps
-        W = sum(o[2] for o in out)
-        res[name] = {"s_per_batch": dt, "kmers_per_s": W / dt, "windows": W}
+    for name, _ in fns:
+        dt = float(np.median(times[name]))
+        res[name] = {"s_per_batch": dt, "kmers_per_s": W / dt, "windows": W,
+                     "s_per_batch_all": [round(t, 4) for t in times[name]]}
     ok = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(plain(), batched()))
     return {"metric": "batched vs plain: canonical k-mers/s over 64 libraries", "value": res["batched"]["kmers_per_s"],
             "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "steps": args.steps,
