@@ -23,15 +23,25 @@ __device__ __forceinline__ uint32_t bucket_of(K key, const BucketGeom &g) {
 }
 
 // Radix digit policies for the onesweep passes: a byte of the key, or a byte of its bucket index.
+// same_low(x, y, shift): x and y agree in every digit below `shift` (what earlier passes sorted by).
 template <class K>
 struct RawDigit {
     __device__ __forceinline__ uint32_t operator()(K key, int shift) const { return KeyT<K>::digit(key, shift); }
+    __device__ __forceinline__ bool same_low(K x, K y, int shift) const {
+        for (int s = 0; s < shift; s += 8)
+            if (KeyT<K>::digit(x, s) != KeyT<K>::digit(y, s)) return false;
+        return true;
+    }
 };
 template <class K>
 struct BucketDigit {
     BucketGeom g;
     __device__ __forceinline__ uint32_t operator()(K key, int shift) const {
         return (bucket_of(key, g) >> shift) & 0xffu;
+    }
+    __device__ __forceinline__ bool same_low(K x, K y, int shift) const {
+        const uint32_t m = shift ? 0xffffffffu >> (32 - shift) : 0u;
+        return ((bucket_of(x, g) ^ bucket_of(y, g)) & m) == 0;
     }
 };
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     __shared__ uint32_t s_texcl[BINS];
     __shared__ uint64_t s_glob[BINS];
     __shared__ uint32_t s_scan[S_WARPS];
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_tile, s_uniform;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < S_WARPS * BINS; i += S_BLOCK) (&whist[0][0])[i] = 0;
@@ -121,6 +121,14 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
         if ((i & 3) == 0) dig[i >> 2] = d;
         else dig[i >> 2] |= d << (8 * (i & 3));
     }
+    // A stable pass's input is sorted by the lower digits, so its tile holds one value of them
+    // exactly when the tile's first and last keys agree. Then no two keys of the tile need a
+    // relative order (equal digits there mean equal sort keys so far), and the tile ranks like a
+    // first pass: one shared atomic per key.
+    if (STABLE && tid == 0) {
+        const uint64_t last = (full ? start + TILE : n) - 1;
+        s_uniform = digit.same_low(in[start], in[last], shift) ? 1u : 0u;
+    }
     // 1. early counts: per-warp digit counts (order-free shared atomics)
 #pragma unroll
     for (int i = 0; i < ITEMS; i++)
@@ -143,9 +151,11 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
         }
     }
     __syncthreads();
-    // 3. ranking straight into shared memory. Stable: rows in order, lanes in order within a row,
-    //    equal digits found by ballots. Unstable (first pass): one shared atomic per key.
-    if (!STABLE) {
+    // 3. ranking straight into shared memory. Unstable (a first pass, or a tile with one value of
+    //    the lower digits): one shared atomic per key. Stable: rows in order, lanes in order within
+    //    a row, equal digits found by ballots.
+    const bool by_atomics = !STABLE || s_uniform;  // read after the barriers that follow its write
+    if (by_atomics) {
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             if (full || (uint32_t)(i * WARP + lane) < n_in_warp) {
@@ -155,30 +165,31 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
                 sdig[pos] = (uint8_t)d;
             }
         }
-    }
+    } else if (STABLE) {
 #pragma unroll
-    for (int i = 0; i < (STABLE ? ITEMS : 0); i++) {
-        const bool valid = full || (uint32_t)(i * WARP + lane) < n_in_warp;
-        const uint32_t d = valid ? ((dig[i >> 2] >> (8 * (i & 3))) & 0xffu) : (BINS + lane);
-        uint32_t peers = FULL;  // lanes whose digit equals this lane's: one ballot per digit bit
+        for (int i = 0; i < ITEMS; i++) {
+            const bool valid = full || (uint32_t)(i * WARP + lane) < n_in_warp;
+            const uint32_t d = valid ? ((dig[i >> 2] >> (8 * (i & 3))) & 0xffu) : (BINS + lane);
+            uint32_t peers = FULL;  // lanes whose digit equals this lane's: one ballot per digit bit
 #pragma unroll
-        for (int b = 0; b < 9; b++) {
-            if (b == 8 && full) break;  // bit 8 only separates the invalid lanes of a partial tile
-            const bool bit = (d >> b) & 1u;
-            const uint32_t bal = __ballot_sync(FULL, bit);
-            peers &= bit ? bal : ~bal;
-        }
-        // Every peer reads the warp's counter for its digit; then the group's highest lane advances
-        // it by the group size (one writer per digit: the warp owns its counters).
-        const int leader = 31 - __clz(peers);
-        uint32_t pos = 0;
-        if (valid) pos = whist[warp][d];
-        __syncwarp();
-        if (valid && lane == leader) whist[warp][d] = pos + (uint32_t)__popc(peers);
-        __syncwarp();
-        if (valid) {
-            skeys[pos + __popc(peers & lt)] = key[i];
-            sdig[pos + __popc(peers & lt)] = (uint8_t)d;
+            for (int b = 0; b < 9; b++) {
+                if (b == 8 && full) break;  // bit 8 only separates the invalid lanes of a partial tile
+                const bool bit = (d >> b) & 1u;
+                const uint32_t bal = __ballot_sync(FULL, bit);
+                peers &= bit ? bal : ~bal;
+            }
+            // Every peer reads the warp's counter for its digit; then the group's highest lane advances
+            // it by the group size (one writer per digit: the warp owns its counters).
+            const int leader = 31 - __clz(peers);
+            uint32_t pos = 0;
+            if (valid) pos = whist[warp][d];
+            __syncwarp();
+            if (valid && lane == leader) whist[warp][d] = pos + (uint32_t)__popc(peers);
+            __syncwarp();
+            if (valid) {
+                skeys[pos + __popc(peers & lt)] = key[i];
+                sdig[pos + __popc(peers & lt)] = (uint8_t)d;
+            }
         }
     }
     // 4. global offsets of this tile's digits (predecessors have usually published by now)
