@@ -35,7 +35,7 @@ HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/s
 # DRAM bytes (read + write) per unit of each kernel, from ncu captures of the current kernels on the
 # fly-shaped library at 1/10 scale (profiles/); scaled to a full launch by the units it processes.
 # A kernel is left out (traffic null) until it has been captured again after a change.
-NCU_BYTES_PER_UNIT = {"k_pass1": 98.95, "k_onesweep": 16.18, "k_bucket_count": 8.66, "k_hash_insert": 221.8}
+NCU_BYTES_PER_UNIT = {"k_pass1": 98.95, "k_onesweep": 16.16, "k_bucket_count": 8.66, "k_hash_insert": 221.8}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
