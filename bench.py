@@ -534,12 +534,37 @@ def run_served(args):
 
 def run_batched(args):
     """Batched form: 64 libraries (genome log-uniform 0.1-20 Mbp, coverage U(10,60), 100/150 bp, 1% errors,
-    k in {21,31,55}) counted by turtle_count_batch vs 64 sequential turtle_count calls (host memory, end to end)."""
+    k in {21,31,55}) counted by turtle_count_batch vs 64 sequential turtle_count calls (host memory, end to end);
+    at full scale also the same recipe at 1/50 scale ("small_libraries")."""
     import paper_1305_1861_gb300 as pkg
 
-    specs = synth.batched_specs(seed=4, n_libs=64, scale=args.scale)
-    libs = [synth.library_from_spec(sp) for sp in specs]
-    jobs = [(lib.bases, lib.offsets, lib.k, lib.min_count) for lib in libs]
+    def compare(scale):
+        specs = synth.batched_specs(seed=4, n_libs=64, scale=scale)
+        libs = [synth.library_from_spec(sp) for sp in specs]
+        jobs = [(lib.bases, lib.offsets, lib.k, lib.min_count) for lib in libs]
+        res, ok = batched_vs_plain(pkg, jobs, args)
+        return res, ok, sum(l.bases.size for l in libs)
+
+    res, ok, n_bases = compare(args.scale)
+    out = {"metric": "batched vs plain: canonical k-mers/s over 64 libraries", "value": res["batched"]["kmers_per_s"],
+           "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "steps": args.steps,
+           "config": {"workload": "batched: 64 libraries, genome log-uniform %.3g-%.3g Mbp, coverage U(10,60), "
+                                  "R in {100,150}, 1%% substitutions, k in {21,31,55}, min_count 2; %.2f Gbase"
+                                  % (0.1 * args.scale, 20 * args.scale, n_bases / 1e9)},
+           "batched": res["batched"], "plain": res["plain_64_calls"],
+           "speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched"]["s_per_batch"],
+           "identical_results": ok}
+    if args.scale == 1.0:  # the same recipe at 1/50 scale: small libraries, where per-call costs dominate
+        res_s, ok_s, nb_s = compare(0.02)
+        out["small_libraries"] = {"bases": nb_s, "batched": res_s["batched"], "plain": res_s["plain_64_calls"],
+                                  "speedup_vs_plain": res_s["plain_64_calls"]["s_per_batch"]
+                                  / res_s["batched"]["s_per_batch"], "identical_results": ok_s}
+    return out
+
+
+def batched_vs_plain(pkg, jobs, args):
+    """64 sequential turtle_count calls vs one turtle_count_batch on the same jobs: medians of alternating
+    steps, and whether every result is identical."""
 
     def plain():
         return [pkg.turtle_count(b, o, k, m) for b, o, k, m in jobs]
@@ -569,14 +594,7 @@ def run_batched(args):
         res[name] = {"s_per_batch": dt, "kmers_per_s": W / dt, "windows": W,
                      "s_per_batch_all": [round(t, 4) for t in times[name]]}
     ok = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(plain(), batched()))
-    return {"metric": "batched vs plain: canonical k-mers/s over 64 libraries", "value": res["batched"]["kmers_per_s"],
-            "unit": METRIC, "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "steps": args.steps,
-            "config": {"workload": "batched: 64 libraries, genome log-uniform %.3g-%.3g Mbp, coverage U(10,60), "
-                                   "R in {100,150}, 1%% substitutions, k in {21,31,55}, min_count 2; %.2f Gbase"
-                                   % (0.1 * args.scale, 20 * args.scale, sum(l.bases.size for l in libs) / 1e9)},
-            "batched": res["batched"], "plain": res["plain_64_calls"],
-            "speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched"]["s_per_batch"],
-            "identical_results": ok}
+    return res, ok
 
 
 def run_cturtle(args):
