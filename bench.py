@@ -93,6 +93,21 @@ def workload(name: str, scale: float, rank: int):
     return lib, desc
 
 
+def reduce_over_ranks(values, ops, device):
+    """Combine per-rank scalars over the process group: values[i] by ops[i] ("max" or "sum"). Without an
+    initialised group of more than one rank the values come back unchanged."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return [float(mx[i]) if op == "max" else float(sm[i]) for i, op in enumerate(ops)]
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -300,15 +315,7 @@ def run_ours(args, rank, world):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     W = st["n_windows"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(W)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_all, W_all = float(mx[0]), float(t[1])
-    else:
-        ms_all, W_all = ms, float(W)
+    ms_all, W_all = reduce_over_ranks([ms, W], ["max", "sum"], "cuda")  # slowest rank, all ranks' windows
     value = W_all / (ms_all / 1e3)
 
     # end to end through the host C ABI: H2D of pinned reads, whole path, D2H of the result
@@ -332,11 +339,7 @@ def run_ours(args, rank, world):
         keys_n = len(counts)
         del keys, counts
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = reduce_over_ranks([e2e_s], ["max"], "cuda")[0]
     e2e = {"value": W_all / e2e_s, "unit": METRIC,
            "h2d_bytes_per_step": int(lib.bases.nbytes + lib.offsets.nbytes),
            "d2h_bytes_per_step": int(keys_n * ((8 if lib.k <= 32 else 16) + 4)), "ms_per_step": e2e_s * 1e3}
