@@ -377,7 +377,9 @@ def run_ours(args, rank, world):
                       "l2": "inputs larger than L2 (%.1f GB of reads resident)" % (lib.bases.nbytes / 1e9),
                       "parallelism": "replicas%d" % world if world > 1 else "single"},
            "e2e": e2e, "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-           "sort_passes": st["sort_passes"], "super_partitions": st["super_partitions"]}
+           "sort_passes": st["sort_passes"], "super_partitions": st["super_partitions"],
+           # digit passes over each key per bit of the key (eight 8-bit passes would be 8 / (2k))
+           "sort_passes_per_key_bit": round(st["sort_passes"] / (2.0 * lib.k), 4)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         frac = 0.01 if lib.k > 32 else 0.1  # about 10-30 s of oracle work
         sample = args.cpu_sample_reads or max(1, int(lib.n_reads * frac))
