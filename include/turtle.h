@@ -81,12 +81,13 @@ typedef struct {
     uint32_t budget_mib;           /* device-memory budget (MiB) for one super-partition's working set;
                                       0 = 80% of the free memory at the start of the call. Inputs whose
                                       working set exceeds it are processed in consecutive key ranges. */
-    uint32_t stream_chunk_mib;     /* host-memory calls: copy the reads to the device in chunks of this many
-                                      MiB through two pinned buffers, packing each chunk as it lands (the
-                                      ASCII is never resident whole); 0 = automatic: reads of 64 MiB or more
-                                      stream in 256 MiB chunks (1 GiB when they exceed a quarter of the
-                                      free device memory), smaller ones are copied at once. Reads already in
-                                      page-locked memory are copied from directly, without staging. */
+    uint32_t stream_chunk_mib;     /* host-memory calls: n > 0 streams the reads to the device in chunks of
+                                      n MiB through two device staging buffers, packing each chunk as it
+                                      lands (the ASCII is never resident whole); 0 = automatic: reads larger
+                                      than a quarter of the free device memory stream in 1 GiB chunks;
+                                      otherwise reads of 64 MiB or more (bucketed form, one key range) are
+                                      copied in chunks that overlap pass 1, and smaller ones at once. Every
+                                      copy reads the caller's memory directly, pageable or page-locked. */
     uint32_t sort_tile;            /* onesweep tile shape (256 threads): 0 = default (global sort: 32 keys per
                                       thread, 16 for 128-bit keys, 2 CTAs/SM; bucket sort: 16, 4 CTAs/SM (8, 3/SM));
                                       1 = 16, 4/SM (8, 3/SM); 2 = 24 (12), 2/SM; 3 = 32 (16), 2/SM */
