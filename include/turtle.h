@@ -235,6 +235,11 @@ const char *turtle_stage_name(int stage);
 /* ------------------------------------------------------------------ per-step entry points
  * Each runs one step of the path on caller-owned DEVICE buffers, for step-wise
  * checking and reuse. All are stream-ordered and synchronise `stream`.
+ * Alignment: buffers of keys are read and written as whole keys, so they must be
+ * aligned to the key width (8 bytes for 64-bit keys, 16 bytes for 128-bit keys);
+ * offsets, bitmaps and filter words to 8 bytes; counts to 4 bytes. A misaligned
+ * buffer returns TURTLE_E_ARG before any work is queued. (turtle_count_device
+ * needs offsets aligned to 8 bytes; its bases may start at any byte.)
  */
 
 /*
@@ -350,11 +355,15 @@ void turtle_server_destroy(turtle_server *server);
  * until the process exits. Limits: n <= TURTLE_NOALLOC_MAX_KEYS64 for 64-bit
  * keys, n <= TURTLE_NOALLOC_MAX_KEYS128 for 128-bit keys; larger n returns
  * TURTLE_E_TOO_LARGE before any work is queued.
+ * Alignment as for turtle_sort_compact (keys 8 bytes, unique 8 * key_words
+ * bytes, counts 4 bytes; TURTLE_E_ARG otherwise, before any work is queued).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture begins. All calls share the one array: calls whose work overlaps on
- * the GPU (different streams or threads at the same time) race and corrupt
- * each other's results; serialise them. The array keeps the previous call's
+ * capture begins. Every call waits for its own work: it synchronises `stream`
+ * and reads the error word and n_unique back to host memory before returning.
+ * All calls share the one array: calls whose work overlaps on the GPU
+ * (different streams or threads at the same time) race and corrupt each
+ * other's results; serialise them. The array keeps the previous call's
  * contents; the call clears what must start at zero itself.
  */
 #define TURTLE_NOALLOC_MAX_KEYS64 (1u << 20)

@@ -190,6 +190,11 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
     return c->d_patterns;
 }
 
+// Caller buffers that kernels read or write as 8- or 16-byte words must be aligned to that width: a
+// 128-bit key is accessed as one 16-byte word, a 64-bit key or word as 8 bytes, a count as 4. A NULL
+// pointer passes (the entry points check NULL separately).
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
 bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 &&
            p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
@@ -965,6 +970,7 @@ int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, con
                       uint64_t n_reads, int k, uint32_t min_count, const turtle_params *params, cudaStream_t s,
                       DeviceOut &o, bool cturtle = false) {
     if (!c || k < 1 || k > 64 || min_count < 1 || !offsets || (n_bases && !bases)) return TURTLE_E_ARG;
+    if (!aligned(offsets, 8)) return TURTLE_E_ARG;
     const turtle_params prm = resolve(params);
     if (!params_ok(prm)) return TURTLE_E_ARG;
     try {
@@ -1801,6 +1807,7 @@ void turtle_result_free(turtle_result *r) {
 int turtle_extract(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
                    int k, void *stream, uint64_t *keys, uint64_t *valid, uint64_t *n_windows) {
     if (!c || k < 1 || k > 64 || !offsets || (n_bases && (!bases || !keys || !valid))) return TURTLE_E_ARG;
+    if (!aligned(offsets, 8) || !aligned(keys, k <= 32 ? 8 : 16) || !aligned(valid, 8)) return TURTLE_E_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     try {
         ctx_begin(c, s);
@@ -1830,6 +1837,7 @@ int turtle_filter(turtle_ctx *c, const uint64_t *keys, uint64_t n, int key_words
     if (!c || (key_words != 1 && key_words != 2) || !filter || n_sectors == 0 || (n_sectors & (n_sectors - 1)) ||
         (n && !keys) || (!set && !seen))
         return TURTLE_E_ARG;
+    if (!aligned(keys, 8 * key_words) || !aligned(filter, 8)) return TURTLE_E_ARG;
     const turtle_params prm = resolve(params);
     if (!params_ok(prm)) return TURTLE_E_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1859,6 +1867,7 @@ int turtle_sort_compact(turtle_ctx *c, const uint64_t *keys, uint64_t n, int key
     if (!c || (key_words != 1 && key_words != 2) || key_bits < 1 || key_bits > 64 * key_words || !n_unique ||
         (n && (!keys || !unique || !counts)))
         return TURTLE_E_ARG;
+    if (!aligned(keys, 8) || !aligned(unique, 8 * key_words) || !aligned(counts, 4)) return TURTLE_E_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     try {
         ctx_begin(c, s);

@@ -74,6 +74,10 @@ extern "C" int turtle_sort_compact_noalloc(const uint64_t *keys, uint64_t n, int
     if ((key_words != 1 && key_words != 2) || key_bits < 1 || key_bits > 64 * key_words || !n_unique ||
         (n && (!keys || !unique || !counts)))
         return TURTLE_E_ARG;
+    // unique is written as whole 8- or 16-byte keys and counts as 4-byte words: a misaligned buffer
+    // would fault on the device, so it is refused here, before anything is queued
+    if (((uintptr_t)keys & 7) || ((uintptr_t)unique & (8 * key_words - 1)) || ((uintptr_t)counts & 3))
+        return TURTLE_E_ARG;
     *n_unique = 0;
     if (n > (key_words == 1 ? (uint64_t)TURTLE_NOALLOC_MAX_KEYS64 : (uint64_t)TURTLE_NOALLOC_MAX_KEYS128))
         return TURTLE_E_TOO_LARGE;

@@ -86,3 +86,21 @@ def test_no_device_reports_nodev(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert lib.turtle_ctx_create(0, ctypes.byref(h)) == -8
+
+
+def test_misaligned_buffers_are_refused_before_any_device_work(lib):
+    """Buffers read or written as whole keys must be aligned to the key width; the allocation-free
+    sort-and-compact checks this before it touches a device, so fake (never dereferenced) pointer
+    values suffice here."""
+    nu = ctypes.c_uint64(99)
+    fn = lib.turtle_sort_compact_noalloc
+    good16, good8, good4 = 0x10000, 0x20000, 0x30000
+    # 128-bit keys need a 16-byte-aligned unique buffer; 8-byte alignment is not enough
+    assert fn(ctypes.c_void_p(good8), 4, 2, 100, ctypes.c_void_p(good16 + 8), ctypes.c_void_p(good4),
+              ctypes.byref(nu), None) == -1
+    # keys on 8 bytes, counts on 4 bytes
+    assert fn(ctypes.c_void_p(good8 + 4), 4, 1, 62, ctypes.c_void_p(good8), ctypes.c_void_p(good4),
+              ctypes.byref(nu), None) == -1
+    assert fn(ctypes.c_void_p(good8), 4, 1, 62, ctypes.c_void_p(good8), ctypes.c_void_p(good4 + 2),
+              ctypes.byref(nu), None) == -1
+    assert nu.value == 99  # refused before any output was written

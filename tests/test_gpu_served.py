@@ -34,9 +34,9 @@ def test_results_alone_equal_results_in_the_mix(have_gpu):
     assert st["completed"] == 24 and st["failed"] == 0 and st["peak_admitted_bytes"] <= 3 << 30
     assert st["largest_batch"] >= 2 and st["batches"] < 24  # queued jobs shared runs
     srv.close()
-    b, o, k, m = jobs[0]
-    ok, oc, _ = oracle.count(b, o, k, m)
-    assert np.array_equal(alone[0][0], ok) and np.array_equal(alone[0][1].astype(np.uint64), oc)
+    for (b, o, k, m), (ak, ac, an) in zip(jobs, alone):  # every job, alone (and so in the mix), is the oracle's
+        ok, oc, onw = oracle.count(b, o, k, m)
+        assert an == onw and np.array_equal(ak, ok) and np.array_equal(ac.astype(np.uint64), oc)
 
 
 def test_admission_refuses_a_job_larger_than_the_budget(have_gpu):

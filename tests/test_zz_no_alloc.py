@@ -1,4 +1,5 @@
-"""The allocation-free sort-and-compact agrees with the allocating one (GPU, through the C ABI).
+"""The allocation-free sort-and-compact agrees with the allocating one and with the oracle (GPU,
+through the C ABI).
 
 turtle_sort_compact_noalloc is for callers that may not allocate device memory
 (fixed budgets, host frameworks that own every allocation, latency-critical
@@ -27,6 +28,7 @@ def _keys(rng, words, n, bits, distinct):
 def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(have_gpu):
     import torch
 
+    import oracle
     import paper_1305_1861_gb300 as pkg
 
     pkg.build()
@@ -50,6 +52,10 @@ def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(have_gpu):
         assert torch.equal(unique[: nu.value], ref_u)
         assert torch.equal(counts[: nu.value], ref_c)
         assert int(counts[: nu.value].sum()) == n
+        ok, oc = oracle.sort_compact(host)  # the plain sort-and-compact of Sec. 2.1.4 on the host
+        got = unique[: nu.value].cpu().numpy().view(np.uint64)
+        assert np.array_equal(got.reshape(ok.shape), ok)
+        assert np.array_equal(counts[: nu.value].cpu().numpy().astype(np.uint64), oc)
     ctx.close()
 
 
