@@ -6,10 +6,14 @@ in HBM. Default workload: the fly-shaped library (100 Mbp genome + 5% repeat
 copies, 30M x 100 bp reads, 1% substitutions, 0.05% N), k=31, min_count=2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload fly|small|longk] [--scale S]
+                    [--workload fly|small|longk|batched|served] [--scale S] [--blocks k64,batched,served]
 
-Prints one JSON line (rank 0). Under torchrun each rank counts its own replica
-library (different seed, same shape): weak scaling, no data-path collective.
+Prints one JSON line (rank 0). Without --workload the line is the fly-shaped headline and,
+on one GPU, nested blocks for the other measured workloads: "k64" (long-k at full size, k = 64,
+with its own roofline, streamed end to end and oracle baseline), "batched" (64 libraries in one
+batched call vs 64 plain calls) and "served" (Poisson arrivals and a saturated queue, continuous
+batching vs one job at a time). Under torchrun each rank counts its own replica library (different
+seed, same shape): weak scaling, no data-path collective; the blocks run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -36,6 +40,7 @@ HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/s
 # fly-shaped library at 1/10 scale (profiles/); scaled to a full launch by the units it processes.
 # A kernel is left out (traffic null) until it has been captured again after a change.
 NCU_BYTES_PER_UNIT = {"k_pass1": 98.95, "k_onesweep": 16.16, "k_bucket_count": 8.66, "k_hash_insert": 221.8}
+NCU_BYTES_PER_UNIT_U128 = {}  # long-k (k = 64): filled from its own captures
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -46,7 +51,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fly", choices=["fly", "small", "longk", "served", "batched"])
+    ap.add_argument("--workload", default=None, choices=["fly", "small", "longk", "served", "batched"],
+                    help="one workload alone (default: the fly-shaped headline plus the --blocks)")
     ap.add_argument("--method", default="scturtle", choices=["scturtle", "cturtle"],
                     help="cturtle: the approximate two-stage counting filter (k-mers seen twice, no counts)")
     ap.add_argument("--cturtle-bits", type=int, default=0, help="cturtle filter bits per window (0 = default 8)")
@@ -55,7 +61,11 @@ def parse():
     ap.add_argument("--saturate-jobs", type=int, default=300,
                     help="served: also submit this many jobs at once (no arrival gaps) to compare capacity")
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--blocks", default="k64,batched,served",
+                    help="default run: also measure these workloads as nested blocks of the same line "
+                         "(k64, batched, served; 'none' for the headline alone)")
+    ap.add_argument("--block-steps", type=int, default=3, help="timed steps of the k64 and batched blocks")
     ap.add_argument("--cpu-sample-reads", type=int, default=0, help="reads in the oracle sample (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--filter-bits", type=float, default=0.0, help="Bloom bits per window (0 = library default)")
@@ -65,7 +75,8 @@ def parse():
     ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..3 (-1 = default)")
     ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
     ap.add_argument("--compact", type=int, default=-1,
-                    help="0 = bucketed, 1 = global sort-and-compact, 2 = hash-table counting")
+                    help="0 = bucketed, 1 = global sort-and-compact, 2 = hash-table counting, "
+                         "3 = lazy sort-and-compact phases (memory-capped, chunked)")
     ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
     ap.add_argument("--pattern-bits", type=int, default=0, help="Bloom pattern bits (0 = library default)")
     ap.add_argument("--micro", action="store_true",
@@ -189,6 +200,45 @@ STAGE_KERNEL = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_bucket_coun
 STAGE_KERNEL_GLOBAL = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_rle", "recount": "k_add_firsts"}
 STAGE_KERNEL_HASH = {"filter": "k_pass1", "table": "k_hash_insert", "recount": "k_hash_firsts",
                      "threshold": "k_hash_extract", "sort": "k_onesweep"}
+STAGE_KERNEL_LAZY = {"filter": "k_pass1", "sort": "k_onesweep", "rle": "k_bucket_count", "merge": "k_merge_counts",
+                     "recount": "k_pass2", "threshold": "k_threshold"}
+
+
+def stage_bytes_lazy(stage: str, st: dict, lib):
+    """Byte model of the lazy form (compact = 3), as stage_bytes: (bytes, launches, units).
+
+      filter    k_pass1 over each chunk: packed reads, one filter sector per window, a first sighting's
+                sector written back, a candidate key written; unit = window
+      sort      bucket-index radix passes over each chunk's candidates; unit = key-pass
+      rle       k_bucket_count: each chunk's candidates read, its distinct keys and counts written; the
+                distinct keys of all chunks are taken as (chunks x the final distinct count), an upper
+                bound; unit = candidate
+      merge     k_merge_counts: the running array and a chunk's distinct keys read, the merged array
+                written, each (key + count), taken as 3 x the final distinct count per merge; unit = key
+      recount   k_pass2: packed reads, one 32-byte table sector per window; unit = window
+      threshold k_threshold: the distinct keys read, one table sector each, kept keys written; unit = key
+    """
+    W = st["n_windows"]
+    kw = 8 if lib.k <= 32 else 16
+    R = float(np.diff(lib.offsets[:2].astype(np.int64))[0]) if lib.n_reads else 100.0
+    packed = (R / 4.0 + R / 8.0) / max(R - lib.k + 1, 1)
+    nc, nu, no = st["n_candidates"], st["n_unique"], st["n_out"]
+    ch = max(st.get("chunks", 1), 1)
+    passes = max(st["sort_passes"], 1)
+    if stage == "filter":
+        return W * packed + W * 32.0 + 32.0 * (W - nc) + kw * nc, ch, W
+    if stage == "sort":
+        return passes * 2.0 * kw * nc, passes * ch, passes * nc
+    if stage == "rle":
+        return kw * nc + (kw + 4.0) * min(nc, ch * nu), ch, nc
+    if stage == "merge":
+        m = max(ch - 1, 1)
+        return m * 3.0 * (kw + 4.0) * nu, m, m * 3 * nu
+    if stage == "recount":
+        return W * packed + W * 32.0, 1, W
+    if stage == "threshold":
+        return nu * (kw + 32.0) + no * (kw + 4.0), 1, nu
+    return 0.0, 1, 0
 
 
 def stage_bytes_hash(stage: str, st: dict, lib):
@@ -254,19 +304,8 @@ def stage_bytes(stage: str, st: dict, lib, bucketed: bool):
     return 0.0, 1, 0
 
 
-def run_ours(args, rank, world):
-    import torch
-
-    import paper_1305_1861_gb300 as pkg
-
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    pkg.load()
-    lib, desc = workload(args.workload, args.scale, rank)
-    bases = torch.from_numpy(lib.bases).cuda()
-    offs = torch.from_numpy(lib.offsets.astype(np.int64)).cuda()
-    ctx = pkg.Context(dev)
-    prm = pkg.Params.default(timing=1)
+def make_params(pkg, args, **kw):
+    prm = pkg.Params.default(timing=1, **kw)
     if args.filter_bits > 0:
         prm.filter_bits_per_window = args.filter_bits
     if args.l2_fetch >= 0:
@@ -285,8 +324,19 @@ def run_ours(args, rank, world):
         prm.budget_mib = args.budget_mib
     if args.pattern_bits:
         prm.pattern_bits = args.pattern_bits
+    return prm
+
+
+def time_device(pkg, ctx, lib, prm, steps, warmup, world=1, dev=0):
+    """Device-resident steps: W untimed, then K timed between CUDA events on the launching stream, with
+    clocks sampled meanwhile. Returns (ms per step (max over ranks), windows (sum over ranks), last stats,
+    per-stage average ms, launches in the timed region, clocks)."""
+    import torch
+
+    bases = torch.from_numpy(lib.bases).cuda()
+    offs = torch.from_numpy(lib.offsets.astype(np.int64)).cuda()
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)
     torch.cuda.synchronize()
 
@@ -303,7 +353,7 @@ def run_ours(args, rank, world):
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         ctx.turtle_count_device(bases, offs, lib.k, lib.min_count, prm, stream)
         st = ctx.stats()
         launches += st["launches"]
@@ -313,70 +363,112 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     W = st["n_windows"]
     ms_all, W_all = reduce_over_ranks([ms, W], ["max", "sum"], "cuda")  # slowest rank, all ranks' windows
-    value = W_all / (ms_all / 1e3)
-
-    # end to end through the host C ABI: H2D of pinned reads, whole path, D2H of the result
-    st_dev = dict(st)
-    ctx.close()  # give the device-resident context's memory back before the host-form calls
-    del bases
+    del bases, offs
     torch.cuda.empty_cache()
-    pin_b = torch.from_numpy(lib.bases).pin_memory()
-    pin_o = torch.from_numpy(lib.offsets.astype(np.uint64).view(np.int64)).pin_memory()
-    keys_n = 0
+    return ms_all, W_all, st, {s: float(np.mean(v)) for s, v in stage_ms.items()}, launches, clocks
+
+
+def time_e2e(pkg, lib, prm, steps, W_all, world=1, dev=0):
+    """End to end through the C ABI (turtle_ctx_count) on the caller's pageable NumPy arrays, as a user
+    calls it: the reads' copy to the device and the result's copy back are inside the timed region.
+    Each result is released before the next call (a streaming consumer). Reports the host-side phases."""
+    import torch
+
     prm_e2e = pkg.Params.from_buffer_copy(prm)  # the same form and knobs, without stage events
     prm_e2e.timing = 0
-    pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count,
-                     prm_e2e)  # warm the default context
-    barrier()
-    torch.cuda.synchronize()
+    ctx = pkg.Context(dev)
+    keys, counts, nw = ctx.turtle_count(lib.bases, lib.offsets, lib.k, lib.min_count, prm_e2e)  # warm the context
+    keys_n = len(counts)
+    del keys, counts
+    phases = {p: [] for p in pkg.HOST_PHASES}
+    h2d = []
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):  # each result is released before the next call (a streaming consumer)
-        keys, counts, nw = pkg.turtle_count(pin_b.numpy(), pin_o.numpy().view(np.uint64), lib.k, lib.min_count,
-                                            prm_e2e)
+    for _ in range(steps):
+        keys, counts, nw = ctx.turtle_count(lib.bases, lib.offsets, lib.k, lib.min_count, prm_e2e)
         keys_n = len(counts)
         del keys, counts
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        st = ctx.stats()
+        for p in pkg.HOST_PHASES:
+            phases[p].append(st["host_ms"][p])
+        h2d.append(st["h2d_ms"])
+    e2e_s = (time.perf_counter() - t0) / steps
+    ctx.close()
+    torch.cuda.empty_cache()
     e2e_s = reduce_over_ranks([e2e_s], ["max"], "cuda")[0]
-    e2e = {"value": W_all / e2e_s, "unit": METRIC,
-           "h2d_bytes_per_step": int(lib.bases.nbytes + lib.offsets.nbytes),
-           "d2h_bytes_per_step": int(keys_n * ((8 if lib.k <= 32 else 16) + 4)), "ms_per_step": e2e_s * 1e3}
+    kw = 8 if lib.k <= 32 else 16
+    return {"value": W_all / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(lib.bases.nbytes + lib.offsets.nbytes),
+            "d2h_bytes_per_step": int(keys_n * (kw + 4)), "ms_per_step": e2e_s * 1e3, "steps": steps,
+            "host": "pageable NumPy arrays (the caller's own memory), turtle_ctx_count",
+            "stages_ms": {p: round(float(np.mean(v)), 3) for p, v in phases.items()},
+            "h2d_copy_span_ms": round(float(np.mean(h2d)), 3),
+            "stages_note": "input: device buffers + offsets copy + queueing the reads' copy; path: device path until "
+                           "the result is in HBM (an overlapped or streamed copy of the reads runs inside it); "
+                           "touch: first touch of fresh host result pages; output: result copy to host"}
 
-    # roofline of the dominant kernel, from the live per-stage CUDA events of the timed steps
-    avg = {s: float(np.mean(v)) for s, v in stage_ms.items()}
+
+def roofline_of(lib, prm, st, avg, args):
     bucketed = prm.compact == 0 and not prm.recount_windows
     hashed = prm.compact == 2
-    kernels = STAGE_KERNEL_HASH if hashed else (STAGE_KERNEL if bucketed else STAGE_KERNEL_GLOBAL)
+    lazy = prm.compact == 3
+    kernels = (STAGE_KERNEL_LAZY if lazy else STAGE_KERNEL_HASH if hashed else
+               (STAGE_KERNEL if bucketed else STAGE_KERNEL_GLOBAL))
     dom = max(kernels, key=lambda s: avg[s])
     hbm, src = peaks()
-    total_bytes, n_launch, units = (stage_bytes_hash(dom, st, lib) if hashed else
-                                    stage_bytes(dom, st, lib, bucketed))
+    total_bytes, n_launch, units = (stage_bytes_lazy(dom, st, lib) if lazy else stage_bytes_hash(dom, st, lib)
+                                    if hashed else stage_bytes(dom, st, lib, bucketed))
     ach = total_bytes / (avg[dom] / 1e3) / 1e9  # = bytes per launch / average launch time
     kern = kernels[dom]
-    # per-unit DRAM bytes were captured on the fly-shaped library at default parameters only
-    per_unit = (NCU_BYTES_PER_UNIT.get(kern) if args.workload == "fly" and (bucketed or hashed)
-                and args.filter_bits <= 0 and args.scale == 1.0 else None)
+    table = NCU_BYTES_PER_UNIT if lib.k <= 32 else NCU_BYTES_PER_UNIT_U128
+    # per-unit DRAM bytes were captured on the fly-shaped (k = 31) and long-k (k = 64) libraries at
+    # default parameters only
+    per_unit = (table.get(kern) if lib.name in ("fly", "longk") and (bucketed or hashed) and not lazy
+                and args.filter_bits <= 0 and args.scale == 1.0 and not args.budget_mib else None)
     traffic = per_unit * units / n_launch if per_unit else None
-    roof = {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
+    return {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
             "bytes_per_launch": total_bytes / n_launch, "launches_per_step": n_launch,
             "traffic_note": ("ncu dram bytes per unit of this kernel (profiles/) x units per launch"
                              if traffic else None),
             "stage_ms": {s: round(v, 3) for s, v in avg.items()}}
 
+
+def config_of(lib, desc, st, prm, world):
+    bucketed = prm.compact == 0 and not prm.recount_windows
+    hashed = prm.compact == 2
+    return {"workload": desc, "k": lib.k, "min_count": lib.min_count, "windows": st["n_windows"],
+            "n_reads": lib.n_reads, "bases": int(lib.bases.size), "candidates": st["n_candidates"],
+            "unique_candidates": st["n_unique"], "reported": st["n_out"],
+            "form": ("lazy sort-and-compact phases (%d chunks)" % st.get("chunks", 0) if prm.compact == 3 else
+                     "hash table" if hashed else ("bucketed" if bucketed else "global sort")),
+            "scratch_bytes": st["scratch_bytes"], "table_bytes": st["table_bytes"],
+            "l2": "inputs larger than L2 (%.1f GB of reads resident)" % (lib.bases.nbytes / 1e9),
+            "parallelism": "replicas%d" % world if world > 1 else "single"}
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    pkg.load()
+    lib, desc = workload(args.workload, args.scale, rank)
+    ctx = pkg.Context(dev)
+    prm = make_params(pkg, args)
+    ms_all, W_all, st, avg, launches, clocks = time_device(pkg, ctx, lib, prm, args.steps, args.warmup, world, dev)
+    ctx.close()  # give the device-resident context's memory back before the host-form calls
+    torch.cuda.empty_cache()
+    value = W_all / (ms_all / 1e3)
+    e2e = time_e2e(pkg, lib, prm, args.e2e_steps, W_all, world, dev)
     out = {"metric": HEADLINE, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u64" if lib.k <= 32 else "u128", "data": "synthetic",
-           "config": {"workload": desc, "k": lib.k, "min_count": lib.min_count, "windows": W,
-                      "n_reads": lib.n_reads, "bases": int(lib.bases.size), "candidates": st["n_candidates"],
-                      "unique_candidates": st["n_unique"], "reported": st["n_out"],
-                      "form": "hash table" if hashed else ("bucketed" if bucketed else "global sort"),
-                      "scratch_bytes": st["scratch_bytes"], "table_bytes": st["table_bytes"],
-                      "l2": "inputs larger than L2 (%.1f GB of reads resident)" % (lib.bases.nbytes / 1e9),
-                      "parallelism": "replicas%d" % world if world > 1 else "single"},
-           "e2e": e2e, "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+           "config": config_of(lib, desc, st, prm, world),
+           "e2e": e2e, "roofline": roofline_of(lib, prm, st, avg, args), "clocks": clocks, "gpu_launches": launches,
            "sort_passes": st["sort_passes"], "super_partitions": st["super_partitions"],
            # digit passes over each key per bit of the key (eight 8-bit passes would be 8 / (2k))
            "sort_passes_per_key_bit": round(st["sort_passes"] / (2.0 * lib.k), 4)}
@@ -384,7 +476,33 @@ def run_ours(args, rank, world):
         frac = 0.01 if lib.k > 32 else 0.1  # about 10-30 s of oracle work
         sample = args.cpu_sample_reads or max(1, int(lib.n_reads * frac))
         out["cpu_baseline"] = cpu_baseline(lib, sample)
-    del st_dev
+    return out
+
+
+def run_k64_block(args):
+    """The long-k workload (k = 64, 128-bit keys) at full size, device-resident, with its own roofline, its
+    end to end streamed through two device staging buffers in 1 GiB chunks, and its oracle baseline."""
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    lib, desc = workload("longk", 1.0, 0)
+    ctx = pkg.Context(0)
+    prm = make_params(pkg, args)
+    steps, warmup = max(1, min(args.steps, args.block_steps)), max(3, min(args.warmup, 3))
+    ms, W, st, avg, launches, clocks = time_device(pkg, ctx, lib, prm, steps, warmup)
+    ctx.close()
+    torch.cuda.empty_cache()
+    e2e = time_e2e(pkg, lib, pkg.Params.default(stream_chunk_mib=1024, timing=1), 2, W)
+    e2e["host"] += ", reads streamed in 1 GiB chunks through two device staging buffers (stream_chunk_mib = 1024)"
+    out = {"metric": "canonical k-mers/s at k=64", "value": W / (ms / 1e3), "unit": METRIC, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms, "dtype": "u128", "config": config_of(lib, desc, st, prm, 1),
+           "e2e": e2e, "roofline": roofline_of(lib, prm, st, avg, args), "clocks": clocks,
+           "gpu_launches": launches, "super_partitions": st["super_partitions"], "sort_passes": st["sort_passes"],
+           "sort_passes_per_key_bit": round(st["sort_passes"] / (2.0 * lib.k), 4)}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(lib, max(1, int(lib.n_reads * 0.01)))
+    del lib
     return out
 
 
@@ -679,8 +797,37 @@ def run_cturtle(args):
             "stage_ms": {k: round(v, 3) for k, v in st["stage_ms"].items() if v > 0}, "clocks": clocks}
 
 
+def run_blocks(args, out):
+    """Nested blocks of the default line: long-k at full size, batched vs plain, served vs plain."""
+    import copy
+
+    import torch
+
+    blocks = [b for b in args.blocks.split(",") if b and b != "none"]
+    for name in blocks:
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        if name == "k64":
+            res = run_k64_block(args)
+        elif name == "batched":
+            a = copy.copy(args)
+            a.scale, a.steps, a.warmup = 1.0, max(1, min(args.steps, args.block_steps)), 1
+            res = run_batched(a)
+        elif name == "served":
+            a = copy.copy(args)
+            a.scale, a.jobs, a.saturate_jobs = 1.0, min(args.jobs, 400), min(args.saturate_jobs, 150)
+            res = run_served(a)
+        else:
+            raise SystemExit("unknown block %r" % name)
+        res["block_wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = res
+
+
 def main():
     args = parse()
+    nested = args.workload is None
+    if nested:
+        args.workload = "fly"
     if args.workload == "batched":
         print(json.dumps(run_batched(args)), flush=True)
         return
@@ -706,6 +853,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     out = run_ours(args, rank, world)
+    if nested and world == 1 and args.method == "scturtle":
+        run_blocks(args, out)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

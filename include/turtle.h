@@ -101,8 +101,16 @@ typedef struct {
                                       counted in an open-addressing table sized from a HyperLogLog
                                       estimate of their distinct keys, first sightings add one, the keys
                                       whose count reaches min_count are extracted and radix-sorted.
-                                      All three are exact. recount_windows = 1 uses the global form
-                                      (0) or is ignored (2: first sightings). */
+                                      3 = lazy sort-and-compact phases (Sec. 2.1.4, Alg. 1), the
+                                      memory-capped form: the reads are taken in chunks of window tiles
+                                      through one shared filter; each chunk's candidates are sorted and
+                                      compacted on their own and merged (merge path) into a running
+                                      sorted array of distinct candidates with counts; then the second
+                                      pass re-extracts every window and counts it in a table of those
+                                      keys. Memory: the packed reads, the filter, the running array
+                                      twice and one chunk, whose size follows budget_mib.
+                                      All four are exact. recount_windows = 1 uses the global form
+                                      (0) or is ignored (2: first sightings; 3: always window recount). */
     uint32_t bucket_slots;         /* bucketed form: shared-memory table of one bucket CTA: 0 or 8192 =
                                       8192 slots (1024 threads, one CTA per SM; default), 4096 = 4096 slots
                                       (512 threads, two CTAs per SM; half the distinct keys per bucket
@@ -113,10 +121,34 @@ typedef struct {
     uint32_t hash_slots_log2;      /* compact = 2: 0 = size the table from the distinct-key estimate (load
                                       at most 1/2); n = start with 2^n slots. A table in which a key finds
                                       no free slot within 32 lines is doubled and the counting redone. */
+    uint32_t shard_count;          /* key-range shards (the paper's routing of k-mers by key to consumers,
+                                      Sec. 2.1.5, across processes or GPUs): 0 or 1 = the whole key space;
+                                      n in 2..TURTLE_PARTS = the call counts only the keys of shard
+                                      shard_index, one of n consecutive key ranges balanced by window
+                                      counts (see turtle_shard_bounds). Every shard reads all the reads;
+                                      concatenating shards 0 .. n-1 in order gives the whole result. Not
+                                      with compact = 3 or the batched form (TURTLE_E_ARG). */
+    uint32_t shard_index;          /* 0 .. shard_count - 1 */
 } turtle_params;
 
 /* Fill *p with the defaults above. */
 void turtle_params_default(turtle_params *p);
+
+/* Key-range parts: the canonical key's top 31 bits v (of its 2k bits) map to f(v) = v (2^32 - v),
+ * which is increasing in v and splits the canonical keys of random sequence into about equal
+ * numbers; part p of TURTLE_PARTS holds the keys with f(v) >> 56 == p, so parts are consecutive key
+ * ranges in ascending order. Super-partitions (budget_mib) and shards are unions of parts. */
+#define TURTLE_PARTS 64
+
+/*
+ * Shard bounds (host only, no device): given the valid windows of each of the n_parts key-range parts
+ * (part_windows[0 .. n_parts)), split the parts into n_shards consecutive ranges of about equal
+ * windows: shard s takes parts [bounds[s], bounds[s+1]); bounds has n_shards + 1 entries, bounds[0] = 0,
+ * bounds[n_shards] = n_parts, non-decreasing; bounds[s] is the first part p at which the windows of
+ * parts below p reach s/n_shards of all windows. A shard may be empty. TURTLE_E_ARG for NULL
+ * pointers, n_parts = 0 or n_shards = 0.
+ */
+int turtle_shard_bounds(const uint64_t *part_windows, uint32_t n_parts, uint32_t n_shards, uint32_t *bounds);
 
 /* ------------------------------------------------------------------ host-memory form */
 typedef struct {
@@ -214,7 +246,18 @@ enum {
     TURTLE_STAGE_TABLE,         /* insert unique candidates into the recount table */
     TURTLE_STAGE_RECOUNT,       /* exact recount: first sightings, or pass 2 over every window */
     TURTLE_STAGE_THRESHOLD,     /* keep count >= min_count in key order */
+    TURTLE_STAGE_MERGE,         /* lazy form (compact = 3): merge a chunk's compacted keys into the running set */
     TURTLE_STAGE_COUNT
+};
+
+/* Where the wall time of a host-memory call (turtle_ctx_count) went, in call order. */
+enum {
+    TURTLE_HOST_INPUT = 0,  /* device buffers for the reads, their offsets copied, and the reads' copy queued
+                               (when it overlaps pass 1 it runs inside TURTLE_HOST_PATH) */
+    TURTLE_HOST_PATH,       /* the device path, until the result is complete in device memory */
+    TURTLE_HOST_TOUCH,      /* first touch of host result pages that did not exist yet */
+    TURTLE_HOST_OUTPUT,     /* the result's copy from device to host memory */
+    TURTLE_HOST_COUNT
 };
 
 typedef struct {
@@ -225,10 +268,23 @@ typedef struct {
     uint32_t launches;                          /* kernels launched by the last call */
     uint32_t stage_launches[TURTLE_STAGE_COUNT];
     float stage_ms[TURTLE_STAGE_COUNT];         /* CUDA-event time per stage (params->timing) */
+    float host_ms[TURTLE_HOST_COUNT];           /* host-memory calls: wall time per phase (always recorded) */
+    float h2d_ms;                               /* host-memory calls: CUDA-event span of the reads' copy to
+                                                   the device, first byte queued to last byte landed */
+    uint64_t h2d_bytes, d2h_bytes;              /* host-memory calls: bytes copied in and out */
+    uint32_t chunks;                            /* lazy form (compact = 3): read chunks merged into the
+                                                   running set (0 in the other forms) */
+    uint32_t pad_;
 } turtle_stats;
 
 /* Statistics of the context's last successful call. */
 int turtle_ctx_stats(const turtle_ctx *ctx, turtle_stats *st);
+
+/* Host-memory form on a caller-owned context: as turtle_count_ex (reads in host memory, result in
+ * library-allocated host arrays owned by *out, free with turtle_result_free), run on `ctx`, whose
+ * statistics then also hold the host-side phases (host_ms, h2d_ms, h2d_bytes, d2h_bytes). */
+int turtle_ctx_count(turtle_ctx *ctx, const turtle_reads *reads, int k, uint32_t min_count,
+                     const turtle_params *params, void *stream, turtle_result *out);
 /* Name of a stage ("pack", "valid", "filter", ...). */
 const char *turtle_stage_name(int stage);
 
@@ -279,12 +335,13 @@ int turtle_sort_compact(turtle_ctx *ctx, const uint64_t *keys, uint64_t n, int k
 
 /* ------------------------------------------------------------------ served form
  * A request loop for many counting jobs (continuous batching). Jobs queue in arrival order;
- * whenever the device is free, the oldest job is admitted together with every queued job of
+ * whenever an executor is free, the oldest job is admitted together with every queued job of
  * the same k and min_count whose device-memory footprint estimate still fits the HBM budget
  * (at most max_batch of them, and at most as many as turtle_count_batch puts in one run), and
- * they run as one batched pipeline. Device work runs one batch at a time; a finished batch's
- * results are copied to the host while the next batch runs. Each result equals turtle_count on
- * the same reads. Reads stay in caller-owned host memory until the job's poll returns.
+ * they run as one batched pipeline on that executor's stream. Runs of different executors are on
+ * the device at the same time; a finished run's results are copied to the host while its
+ * executor's next run executes. Each result equals turtle_count on the same reads. Reads stay in
+ * caller-owned host memory until the job's poll returns.
  */
 typedef struct turtle_server turtle_server;
 
@@ -313,19 +370,29 @@ typedef struct {
     double queue_ms;  /* submit -> admitted */
     double run_ms;    /* admitted -> result ready */
     double total_ms;  /* submit -> result ready */
+    double start_ms, end_ms;  /* admission and completion on one steady clock (ms): jobs of different
+                                 runs whose [start, end) intervals intersect ran at the same time */
 } turtle_job_times;
 
 typedef struct {
     uint64_t budget_bytes, admitted_bytes, peak_admitted_bytes;
     uint64_t submitted, completed, failed, queued, running, peak_running, peak_queued;
     uint64_t batches, largest_batch;  /* batched runs started; most jobs in one run */
+    uint64_t executors;               /* runs that can be on the device at once */
+    uint64_t peak_running_batches;    /* most runs that were on the device at the same time */
 } turtle_server_stats;
 
-/* Start a server on `device`; up to max_batch jobs (1..64) share one run (1 = every job alone,
- * in arrival order). The server owns one context, a stream and two host threads (executor and
- * copy-out). hbm_budget_bytes = 0 takes half of the free device memory. params may be NULL. */
+/* Start a server on `device` with 2 executors (turtle_server_create_ex). */
 int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_batch, const turtle_params *params,
                          turtle_server **server);
+/* Start a server on `device`: up to max_batch jobs (1..64) share one run (1 = every job alone),
+ * and up to `executors` runs (1..16) are on the device at once, each executor with its own
+ * context, stream and copy-out thread, all admitting from one queue (oldest job first) within one
+ * HBM budget: a run is admitted only while the footprint estimates of every admitted job fit
+ * hbm_budget_bytes (0 = half of the free device memory). executors = 1 runs one batch at a time.
+ * params may be NULL. */
+int turtle_server_create_ex(int device, uint64_t hbm_budget_bytes, int max_batch, int executors,
+                            const turtle_params *params, turtle_server **server);
 /* Queue a job; *ticket identifies it. TURTLE_E_BUSY: its footprint estimate exceeds the whole
  * budget, so it could never be admitted. */
 int turtle_submit(turtle_server *server, const turtle_job *job, uint64_t *ticket);

@@ -30,7 +30,8 @@ TURTLE_OK = 0
 ERRORS = {-1: "TURTLE_E_ARG", -2: "TURTLE_E_NOMEM", -3: "TURTLE_E_CUDA", -4: "TURTLE_E_OVERFLOW",
           -5: "TURTLE_E_TIMEOUT", -6: "TURTLE_E_BUSY", -7: "TURTLE_E_DEVICE", -8: "TURTLE_E_NODEV",
           -9: "TURTLE_E_CAPACITY", -10: "TURTLE_E_TOO_LARGE"}
-STAGES = ["pack", "valid", "filter", "hist", "sort", "rle", "table", "recount", "threshold"]
+STAGES = ["pack", "valid", "filter", "hist", "sort", "rle", "table", "recount", "threshold", "merge"]
+HOST_PHASES = ["input", "path", "touch", "output"]
 
 
 class TurtleError(RuntimeError):
@@ -45,7 +46,8 @@ class Params(ctypes.Structure):
                 ("recount_windows", u32), ("member_filter", u32), ("budget_mib", u32),
                 ("stream_chunk_mib", u32), ("sort_tile", u32),
                 ("compact", u32), ("bucket_slots", u32),
-                ("cturtle_bits_per_window", u32), ("hash_slots_log2", u32)]
+                ("cturtle_bits_per_window", u32), ("hash_slots_log2", u32), ("shard_count", u32),
+                ("shard_index", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":
@@ -73,12 +75,15 @@ class _DeviceResult(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n_windows", u64), ("n_candidates", u64), ("n_firsts", u64), ("n_unique", u64), ("n_out", u64),
                 ("filter_bytes", u64), ("table_bytes", u64), ("scratch_bytes", u64), ("sort_passes", u32),
-                ("super_partitions", u32), ("launches", u32), ("stage_launches", u32 * 9), ("stage_ms", ctypes.c_float * 9)]
+                ("super_partitions", u32), ("launches", u32), ("stage_launches", u32 * 10), ("stage_ms", ctypes.c_float * 10),
+                ("host_ms", ctypes.c_float * 4), ("h2d_ms", ctypes.c_float), ("h2d_bytes", u64), ("d2h_bytes", u64),
+                ("chunks", u32), ("pad_", u32)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_launches", "stage_ms")}
-        d["stage_launches"] = {STAGES[i]: int(self.stage_launches[i]) for i in range(9)}
-        d["stage_ms"] = {STAGES[i]: float(self.stage_ms[i]) for i in range(9)}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_launches", "stage_ms", "host_ms", "pad_")}
+        d["stage_launches"] = {STAGES[i]: int(self.stage_launches[i]) for i in range(len(STAGES))}
+        d["stage_ms"] = {STAGES[i]: float(self.stage_ms[i]) for i in range(len(STAGES))}
+        d["host_ms"] = {HOST_PHASES[i]: float(self.host_ms[i]) for i in range(4)}
         return d
 
 
@@ -105,6 +110,8 @@ def load():
         "turtle_ctx_create": (ctypes.c_int, [ctypes.c_int, _p]),
         "turtle_ctx_destroy": (None, [_p]),
         "turtle_ctx_stats": (ctypes.c_int, [_p, _p]),
+        "turtle_shard_bounds": (ctypes.c_int, [_p, u32, u32, _p]),
+        "turtle_ctx_count": (ctypes.c_int, [_p, _p, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_count_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_frequent": (ctypes.c_int, [_p, ctypes.c_int, _p, _p, _p]),
         "turtle_frequent_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, _p, _p, _p]),
@@ -114,6 +121,7 @@ def load():
         "turtle_sort_compact_noalloc": (ctypes.c_int, [_p, u64, ctypes.c_int, ctypes.c_int, _p, _p, _p, _p]),
         "turtle_count_batch": (ctypes.c_int, [_p, ctypes.c_size_t, _p, _p, _p]),
         "turtle_server_create": (ctypes.c_int, [ctypes.c_int, u64, ctypes.c_int, _p, _p]),
+        "turtle_server_create_ex": (ctypes.c_int, [ctypes.c_int, u64, ctypes.c_int, ctypes.c_int, _p, _p]),
         "turtle_submit": (ctypes.c_int, [_p, _p, _p]),
         "turtle_poll": (ctypes.c_int, [_p, u64, ctypes.c_int, _p, _p]),
         "turtle_server_stats_get": (ctypes.c_int, [_p, _p]),
@@ -243,13 +251,14 @@ class _Job(ctypes.Structure):
 
 
 class JobTimes(ctypes.Structure):
-    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, u64) for n in ("budget_bytes", "admitted_bytes", "peak_admitted_bytes", "submitted", "completed",
                                    "failed", "queued", "running", "peak_running", "peak_queued", "batches",
-                                   "largest_batch")]
+                                   "largest_batch", "executors", "peak_running_batches")]
 
 
 def turtle_count_batch(jobs, params: Params | None = None, stream=None):
@@ -276,17 +285,18 @@ def turtle_count_batch(jobs, params: Params | None = None, stream=None):
 class Server:
     """Served form: continuous batching of counting jobs admitted by device-memory footprint.
 
-    Up to max_batch queued jobs with the same k and min_count share one batched run.
+    Up to max_batch queued jobs with the same k and min_count share one batched run, and up to
+    `executors` runs are on the device at once (each executor with its own context and stream).
     """
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_batch: int = 4,
-                 params: Params | None = None):
+                 params: Params | None = None, executors: int = 2):
         self._lib = load()
         self._h = _p()
         self._keep = {}
-        _check(self._lib.turtle_server_create(device, hbm_budget_bytes, max_batch,
-                                              ctypes.byref(params) if params else None, ctypes.byref(self._h)),
-               "turtle_server_create")
+        _check(self._lib.turtle_server_create_ex(device, hbm_budget_bytes, max_batch, executors,
+                                                 ctypes.byref(params) if params else None, ctypes.byref(self._h)),
+               "turtle_server_create_ex")
 
     def submit(self, bases, offsets, k: int, min_count: int = 2) -> int:
         b = _np(bases, np.uint8)
@@ -369,6 +379,19 @@ class Context:
         self.close()
 
     # ------------------------------------------------------------ whole path
+    def turtle_count(self, bases, offsets, k: int, min_count: int = 2, params: Params | None = None, stream=None):
+        """Host-memory form on this context (turtle_ctx_count): NumPy in, (keys, counts, n_windows) out, as
+        the module-level turtle_count; this context's stats() then include the host-side phases."""
+        b = _np(bases, np.uint8)
+        o = _np(offsets, np.uint64)
+        reads = _Reads(b.ctypes.data if b.size else None, o.ctypes.data, o.size - 1)
+        res = _Result()
+        rc = self._lib.turtle_ctx_count(self._h, ctypes.byref(reads), k, min_count,
+                                        ctypes.byref(params) if params else None, _stream_ptr(stream),
+                                        ctypes.byref(res))
+        _check(rc, "turtle_ctx_count")
+        return _take(self._lib, res, k)
+
     def turtle_count_device(self, bases, offsets, k: int, min_count: int = 2, params: Params | None = None,
                             stream=None):
         """bases: CUDA uint8 tensor; offsets: CUDA int64/uint64 tensor (n_reads + 1).

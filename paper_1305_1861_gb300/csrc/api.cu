@@ -21,6 +21,8 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <initializer_list>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <new>
@@ -101,6 +103,7 @@ struct turtle_ctx {
     // streamed input: a copy stream and the events that order it with the packing stream
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_packed[2] = {};
+    cudaEvent_t ev_in[2] = {};  // host-memory calls: first byte of the reads queued, last byte landed
 };
 
 namespace {
@@ -199,8 +202,25 @@ bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 &&
            p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
-           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 2 && p.hash_slots_log2 <= 40 &&
-           (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192);
+           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 3 && p.hash_slots_log2 <= 40 &&
+           (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192) &&
+           p.shard_count <= TURTLE_PARTS && p.shard_index < (p.shard_count ? p.shard_count : 1) &&
+           !(p.shard_count > 1 && p.compact == 3);
+}
+
+// Shard s of n takes the key-range parts [bounds[s], bounds[s+1]): bounds[s] is the first part at which
+// the windows of the parts below it reach s/n of all windows.
+void shard_bounds(const uint64_t *w, uint32_t n_parts, uint32_t n_shards, uint32_t *bounds) {
+    unsigned __int128 total = 0;
+    for (uint32_t p = 0; p < n_parts; p++) total += w[p];
+    uint32_t p = 0;
+    unsigned __int128 below = 0;  // windows of parts [0, p)
+    bounds[0] = 0;
+    for (uint32_t sh = 1; sh < n_shards; sh++) {
+        while (p < n_parts && below * n_shards < total * sh) below += w[p++];
+        bounds[sh] = p;
+    }
+    bounds[n_shards] = n_parts;
 }
 
 turtle_params resolve(const turtle_params *p) {
@@ -578,6 +598,198 @@ void run_cturtle(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st
     c->stats = st;
 }
 
+// Free the context's scratch allocated after position `mark` of its list, except the buffers in `keep`.
+void scratch_trim(turtle_ctx *c, size_t mark, std::initializer_list<const void *> keep, cudaStream_t s) {
+    std::vector<void *> kept;
+    for (size_t i = mark; i < c->scratch.size(); i++) {
+        void *p = c->scratch[i];
+        if (std::find(keep.begin(), keep.end(), (const void *)p) != keep.end()) kept.push_back(p);
+        else cudaFreeAsync(p, s);
+    }
+    c->scratch.resize(mark);
+    c->scratch.insert(c->scratch.end(), kept.begin(), kept.end());
+}
+
+// Free memory on the device for this call: cudaMemGetInfo plus what this context's pool holds unused.
+double device_room(turtle_ctx *c) {
+    size_t free_b = 0, total_b = 0;
+    ck(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t pool_reserved = 0, pool_used = 0;
+    if (cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &pool_reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &pool_used) == cudaSuccess &&
+        pool_reserved > pool_used)
+        free_b += pool_reserved - pool_used;
+    cudaGetLastError();
+    return (double)free_b;
+}
+
+// Lazy sort-and-compact phases (params.compact = 3; Sec. 2.1.4 and Alg. 1), the memory-capped form.
+// The windows are taken in chunks of pass-1 tiles, in read order, through one filter shared by all
+// chunks. A chunk's candidates are sorted and compacted on their own (bucketed form, every key kept
+// with its run length) and merged in one linear pass into the running sorted array of distinct
+// candidates: the compacted prefix is never sorted again. A key seen twice has at least one
+// candidate (the filter has no false negatives), so the running array holds every key that can
+// reach min_count >= 2; the exact count of each is then taken by the second pass, which re-extracts
+// every window and counts it in a table of the running array's keys (the benchmark spec (d)); the keys are
+// kept in the array's order when count >= min_count. With min_count = 1 every window is a
+// candidate and the merged run lengths are the counts.
+template <class K>
+void run_lazy(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, const PackLayout &L, int k,
+              uint32_t min_count, const uint64_t *P, const uint64_t *V, uint64_t W, const turtle_params &prm,
+              cudaStream_t s, DeviceOut &out) {
+    constexpr int KW = sizeof(K) / 8;
+    constexpr int PART_BITS = 6;
+    uint32_t *err = c->d_err;
+    unsigned long long *ctr = c->d_ctr;
+    const bool use_filter = min_count >= 2;
+    FilterGeom fg{};
+    if (use_filter) {
+        fg.n_sectors = pow2_at_least((uint64_t)((double)W * prm.filter_bits_per_window / 256.0) + 1);
+        fg.sector_shift = 64 - log2_exact(fg.n_sectors);
+        fg.words = (uint64_t *)ctx_alloc(c, 32 * fg.n_sectors, s);
+        ck(cudaMemsetAsync(fg.words, 0, 32 * fg.n_sectors, s));
+        fg.patterns = ctx_patterns(c, prm, s);
+        fg.pat_mask = prm.n_patterns - 1;
+        st.filter_bytes = 32 * fg.n_sectors;
+    }
+    // Chunk size: 60% of the budget for one chunk's working set (candidates, the bucket sort's second
+    // buffer, per-candidate counts, the compacted chunk and its share of the merged array), the rest for
+    // the running array (held twice during a merge).
+    const double budget = prm.budget_mib ? (double)prm.budget_mib * (1 << 20) : 0.8 * device_room(c);
+    const double per_pos = 4.0 * sizeof(K) + 12.0;
+    const uint64_t all_tiles = (L.n_bases + 127) / 128;
+    uint64_t tiles = (uint64_t)(0.6 * budget / per_pos / 128.0);
+    if (tiles < 1) tiles = 1;
+    if (tiles > all_tiles) tiles = all_tiles;
+    const uint64_t cap = tiles * 128;  // windows of a chunk <= its positions
+    K *cand = (K *)ctx_alloc(c, sizeof(K) * cap, s);
+    uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
+    K *R = nullptr;
+    uint32_t *Rc = nullptr;
+    uint64_t nR = 0;
+    const int variant = prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile);
+    for (uint64_t t0 = 0; t0 < all_tiles; t0 += tiles) {
+        const uint64_t t1 = std::min(all_tiles, t0 + tiles);
+        ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
+        ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
+        int bits = 0;
+        const BucketGeom bg = bucket_geom((t1 - t0) * 128, 0u, 1u << PART_BITS, PART_BITS, k, &bits);
+        tm.start(TURTLE_STAGE_FILTER);
+        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cap, nullptr, ctr + C_FIRST, 0, hist,
+                        (bits + 7) / 8, 0, 0u, 1u << PART_BITS, nullptr, 0, nullptr, err, &bg, t0, t1);
+        tm.stop(TURTLE_STAGE_FILTER);
+        st.stage_launches[TURTLE_STAGE_FILTER] += 1;
+        read_back(c, s);
+        const uint64_t n_cand = c->h_ctr[C_CAND];
+        st.n_candidates += n_cand;
+        st.chunks += 1;
+        const size_t mark = c->scratch.size();
+        const PartOut po = bucketed_part<K>(c, lc, tm, st, 1, cand, n_cand, nullptr, 0, bg, bits, hist, false,
+                                            variant, prm.bucket_slots != 4096, s);
+        if (!R) {  // the first chunk's compacted keys start the running array
+            scratch_trim(c, mark, {po.keys, po.counts}, s);
+            R = (K *)po.keys;
+            Rc = po.counts;
+            nR = po.n;
+        } else if (po.n) {
+            const uint64_t n = nR + po.n, mt = merge_tiles(n);
+            K *Rn = (K *)ctx_alloc(c, sizeof(K) * n, s);
+            uint32_t *Rnc = (uint32_t *)ctx_alloc(c, 4 * n, s);
+            uint64_t *split = (uint64_t *)ctx_alloc(c, 8 * (mt + 1), s);
+            uint64_t *lb = (uint64_t *)ctx_alloc(c, 8 * mt, s);
+            uint32_t *tc = (uint32_t *)ctx_alloc(c, 16, s);
+            tm.start(TURTLE_STAGE_MERGE);
+            launch_merge_counts<K>(lc, R, Rc, nR, (const K *)po.keys, po.counts, po.n, Rn, Rnc, ctr + C_UNIQUE, split,
+                                   lb, tc, err);
+            tm.stop(TURTLE_STAGE_MERGE);
+            st.stage_launches[TURTLE_STAGE_MERGE] += 2;
+            read_back(c, s);
+            scratch_trim(c, mark, {Rn, Rnc}, s);
+            ctx_free(c, R, s);
+            ctx_free(c, Rc, s);
+            R = Rn;
+            Rc = Rnc;
+            nR = c->h_ctr[C_UNIQUE];
+        } else {
+            scratch_trim(c, mark, {}, s);
+        }
+        if (prm.timing) {  // accumulate this chunk's stage times (the events are reused per chunk)
+            ck(cudaStreamSynchronize(s));
+            for (int i = TURTLE_STAGE_FILTER; i < TURTLE_STAGE_COUNT; i++) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] += ms;
+                else cudaGetLastError();
+                ck(cudaEventRecord(c->ev[2 * i], s));
+                ck(cudaEventRecord(c->ev[2 * i + 1], s));
+            }
+        }
+    }
+    ctx_free(c, cand, s);
+    ctx_free(c, hist, s);
+    if (use_filter) ctx_free(c, fg.words, s);
+    st.n_unique = nR;
+    K *okeys = (K *)ctx_alloc(c, sizeof(K) * (nR ? nR : 1), s, true);
+    uint32_t *ocounts = (uint32_t *)ctx_alloc(c, 4 * (nR ? nR : 1), s, true);
+    uint64_t n_out = 0;
+    if (!use_filter) {  // every window was a candidate: the merged run lengths are the counts
+        if (nR) {
+            ck(cudaMemcpyAsync(okeys, R, sizeof(K) * nR, cudaMemcpyDeviceToDevice, s));
+            ck(cudaMemcpyAsync(ocounts, Rc, 4 * nR, cudaMemcpyDeviceToDevice, s));
+        }
+        n_out = nR;
+    } else if (nR) {
+        ctx_free(c, Rc, s);  // candidate run lengths: the second pass counts every window itself
+        Rc = nullptr;
+        const uint64_t lines = pow2_at_least((uint64_t)(nR / (0.4 * slots_per_line(KW))) + 1);
+        const TableGeom tg{lines - 1, nullptr, 0, 0};
+        void *table = ctx_alloc(c, 128 * lines, s);
+        st.table_bytes = 128 * lines;
+        c->h_ctr[C_N - 1] = nR;  // the insert kernel reads the key count from device memory
+        ck(cudaMemcpyAsync(ctr + C_UNIQUE, &c->h_ctr[C_N - 1], 8, cudaMemcpyHostToDevice, s));
+        tm.start(TURTLE_STAGE_TABLE);
+        launch_table_clear<K>(lc, table, lines);
+        launch_table_insert<K>(lc, R, nullptr, ctr + C_UNIQUE, nR, table, tg, nullptr, 0, err);
+        tm.stop(TURTLE_STAGE_TABLE);
+        tm.start(TURTLE_STAGE_RECOUNT);
+        launch_pass2<K>(lc, L, k, P, V, table, tg, W >= 0xfffffffeull, err);
+        tm.stop(TURTLE_STAGE_RECOUNT);
+        const uint64_t lw = sort_lookback_words(nR, KW);
+        uint64_t *lookback = (uint64_t *)ctx_alloc(c, 8 * lw, s);
+        uint32_t *tc = (uint32_t *)ctx_alloc(c, 16, s);
+        tm.start(TURTLE_STAGE_THRESHOLD);
+        launch_threshold<K>(lc, R, nR, table, tg, min_count, okeys, ocounts, ctr + C_OUT, lookback, tc, err);
+        tm.stop(TURTLE_STAGE_THRESHOLD);
+        st.stage_launches[TURTLE_STAGE_TABLE] += 1;
+        st.stage_launches[TURTLE_STAGE_RECOUNT] += 1;
+        st.stage_launches[TURTLE_STAGE_THRESHOLD] += 1;
+        read_back(c, s);
+        n_out = c->h_ctr[C_OUT];
+        if (prm.timing) {
+            ck(cudaStreamSynchronize(s));
+            for (int i : {(int)TURTLE_STAGE_TABLE, (int)TURTLE_STAGE_RECOUNT, (int)TURTLE_STAGE_THRESHOLD}) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] += ms;
+                else cudaGetLastError();
+            }
+        }
+    }
+    read_back(c, s);
+    out.keys = okeys;
+    out.counts = ocounts;
+    out.n = n_out;
+    st.n_out = n_out;
+    st.super_partitions = 1;
+    if (prm.timing)
+        for (int i = 0; i < TURTLE_STAGE_FILTER; i++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) st.stage_ms[i] = ms;
+            else cudaGetLastError();
+        }
+    for (int i = 0; i < TURTLE_STAGE_COUNT; i++) st.launches += st.stage_launches[i];
+    st.scratch_bytes = c->scratch_bytes;
+    c->stats = st;
+}
+
 template <class K>
 void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets, uint64_t n_reads,
                int k, uint32_t min_count, const turtle_params &prm, cudaStream_t s, DeviceOut &out,
@@ -637,6 +849,12 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         run_cturtle<K>(c, lc, tm, st, L, k, P, V, W, prm, s, out);
         return;
     }
+    if (prm.compact == 3 && !tag) {  // lazy sort-and-compact phases: the ambiguous-call and start bitmaps are done
+        ctx_free(c, B, s);
+        ctx_free(c, S, s);
+        run_lazy<K>(c, lc, tm, st, L, k, min_count, P, V, W, prm, s, out);
+        return;
+    }
     const bool use_filter = min_count >= 2;
     const bool hashed = prm.compact == 2;
     // batches and the hash-table form recount from first sightings
@@ -670,24 +888,39 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     cudaGetLastError();
     const double budget = prm.budget_mib ? (double)prm.budget_mib * (1 << 20) : 0.8 * (double)free_b;
     constexpr int PART_BITS = 6;
+    static_assert((1 << PART_BITS) == TURTLE_PARTS, "key-range parts");
     std::vector<std::pair<uint32_t, uint32_t>> groups;  // [part_lo, part_hi) of each super-partition
     std::vector<uint64_t> group_w;
-    if (tag || (double)W * bytes_per_window <= budget) {  // batches are sized by the caller: one range
+    const bool sharded = !tag && prm.shard_count > 1;
+    // this call's key range: the whole key space, or its shard's consecutive parts
+    uint32_t range_lo = 0, range_hi = 1u << PART_BITS;
+    uint64_t W_range = W;
+    if (tag || (!sharded && (double)W * bytes_per_window <= budget)) {  // batches are sized by the caller
         groups.push_back({0u, 1u << PART_BITS});
         group_w.push_back(W);
     } else {
         unsigned long long *pc = (unsigned long long *)ctx_alloc(c, 8 << PART_BITS, s);
         ck(cudaMemsetAsync(pc, 0, 8 << PART_BITS, s));
         launch_part_count<K>(lc, L, k, P, V, PART_BITS, pc);
+        st.stage_launches[TURTLE_STAGE_VALID] += 1;
         std::vector<unsigned long long> cnt(1 << PART_BITS);
         ck(cudaMemcpyAsync(cnt.data(), pc, 8 << PART_BITS, cudaMemcpyDeviceToHost, s));
         read_back(c, s);
-        // balanced groups: as many as the budget needs, each near the average size
-        const double n_groups = std::ceil((double)W * bytes_per_window / budget);
-        const double target = (double)W / n_groups;
-        uint32_t lo = 0;
+        if (sharded) {  // every shard sees the same part counts, so all agree on the bounds
+            std::vector<uint32_t> bounds(prm.shard_count + 1);
+            std::vector<uint64_t> w64(cnt.begin(), cnt.end());
+            shard_bounds(w64.data(), 1u << PART_BITS, prm.shard_count, bounds.data());
+            range_lo = bounds[prm.shard_index];
+            range_hi = bounds[prm.shard_index + 1];
+            W_range = 0;
+            for (uint32_t p = range_lo; p < range_hi; p++) W_range += cnt[p];
+        }
+        // balanced groups within the range: as many as the budget needs, each near the average size
+        const double n_groups = std::max(1.0, std::ceil((double)W_range * bytes_per_window / budget));
+        const double target = (double)W_range / n_groups;
+        uint32_t lo = range_lo;
         uint64_t acc = 0;
-        for (uint32_t p = 0; p < (1u << PART_BITS); p++) {
+        for (uint32_t p = range_lo; p < range_hi; p++) {
             const double next = (double)(acc + cnt[p]);
             if (p > lo && (next * bytes_per_window > budget || next > 1.02 * target)) {
                 groups.push_back({lo, p});
@@ -697,10 +930,12 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             }
             acc += cnt[p];
         }
-        groups.push_back({lo, 1u << PART_BITS});
-        group_w.push_back(acc);
+        if (range_hi > lo) {
+            groups.push_back({lo, range_hi});
+            group_w.push_back(acc);
+        }
     }
-    const bool parted = groups.size() > 1;
+    const bool parted = groups.size() > 1 || sharded;
     st.super_partitions = (uint32_t)groups.size();
 
     std::vector<PartOut> outs;
@@ -1108,6 +1343,7 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
         launch_pack_groups(lc, stage[b] - c0, d_off, reads->n_reads, L, g0, g1, pp.P, pp.B);
         ck(cudaEventRecord(c->ev_packed[b], s));
     }
+    ck(cudaEventRecord(c->ev_in[1], c->copy_stream));  // the last chunk has landed
     if (n_chunks == 0) launch_pack_groups(lc, nullptr, d_off, reads->n_reads, L, 0, L.pack_groups(), pp.P, pp.B);
     launch_mark_starts(lc, d_off, reads->n_reads, L, pp.S, c->d_err);
 }
@@ -1239,6 +1475,7 @@ void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, u
         if (t_ready > t_done) t_done = t_ready;
     }
     tm.stop(TURTLE_STAGE_FILTER);
+    ck(cudaEventRecord(c->ev_in[1], c->copy_stream));  // the last chunk of the reads has landed
     st.stage_launches[TURTLE_STAGE_PACK] = (uint32_t)n_chunks + 1;
     st.stage_launches[TURTLE_STAGE_VALID] = (uint32_t)n_chunks;
     st.stage_launches[TURTLE_STAGE_FILTER] = (uint32_t)n_chunks;
@@ -1286,7 +1523,7 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
     const uint32_t min_count = jobs[idx[0]].min_count;
     const int n_libs = (int)idx.size();
     const turtle_params prm = resolve(params);
-    if (!params_ok(prm)) return TURTLE_E_ARG;
+    if (!params_ok(prm) || prm.shard_count > 1) return TURTLE_E_ARG;
     std::vector<uint64_t> lib_starts(n_libs + 1, 0), entry_starts(n_libs + 1, 0);
     for (int l = 0; l < n_libs; l++) {
         const turtle_job &j = jobs[idx[l]];
@@ -1495,7 +1732,7 @@ const char *turtle_strerror(int code) {
 
 const char *turtle_stage_name(int stage) {
     static const char *names[TURTLE_STAGE_COUNT] = {"pack", "valid", "filter", "hist", "sort",
-                                                    "rle", "table", "recount", "threshold"};
+                                                    "rle", "table", "recount", "threshold", "merge"};
     return stage >= 0 && stage < TURTLE_STAGE_COUNT ? names[stage] : "?";
 }
 
@@ -1530,6 +1767,7 @@ int turtle_ctx_create(int device, turtle_ctx **out) {
         for (auto &e : c->ev) ck(cudaEventCreate(&e));
         for (auto &e : c->ev_h2d) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         for (auto &e : c->ev_packed) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &e : c->ev_in) ck(cudaEventCreate(&e));
         ck(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     } catch (Fail f) {
         turtle_ctx_destroy(c);
@@ -1558,10 +1796,18 @@ void turtle_ctx_destroy(turtle_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->ev_packed)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->ev_in)
+        if (e) cudaEventDestroy(e);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
+}
+
+int turtle_shard_bounds(const uint64_t *part_windows, uint32_t n_parts, uint32_t n_shards, uint32_t *bounds) {
+    if (!part_windows || !bounds || n_parts == 0 || n_shards == 0) return TURTLE_E_ARG;
+    shard_bounds(part_windows, n_parts, n_shards, bounds);
+    return TURTLE_OK;
 }
 
 int turtle_ctx_stats(const turtle_ctx *c, turtle_stats *st) {
@@ -1643,6 +1889,10 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     if (!reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64 || min_count < 1)
         return TURTLE_E_ARG;
     // every offsets pair is checked on the device while packing (TURTLE_E_ARG)
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<float, std::milli>(clk::now() - t).count(); };
+    const clk::time_point t_call = clk::now();
+    float host_ms[TURTLE_HOST_COUNT] = {};
     int rc = 0;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t n_bases = reads->offsets[reads->n_reads];
@@ -1659,7 +1909,7 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     // large host inputs, one key range, bucketed form: overlap the copy with pass 1
     bool overlapped = false;
     if (!streamed && !cturtle && prm.compact == 0 && (min_count == 1 || !prm.recount_windows) &&
-        n_bases >= OVERLAP_MIN && params_ok(prm)) {
+        prm.shard_count <= 1 && n_bases >= OVERLAP_MIN && params_ok(prm)) {
         size_t free_b = 0, total_b = 0;
         if (cudaSetDevice(c->device) == cudaSuccess && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
             const double kb = k <= 32 ? 8.0 : 16.0;
@@ -1674,14 +1924,18 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         ck(cudaSetDevice(c->device));
         if (!streamed) ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
         ck(cudaMallocFromPoolAsync((void **)&d_off, 8 * (reads->n_reads + 1), c->pool, s));
+        ck(cudaEventRecord(c->ev_in[0], s));  // the input copies start here
+        copy_to_device(c, d_off, reads->offsets, 8 * (reads->n_reads + 1), s);
         if (n_bases && !streamed && !overlapped)
             ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
-        copy_to_device(c, d_off, reads->offsets, 8 * (reads->n_reads + 1), s);
+        if (!streamed && !overlapped) ck(cudaEventRecord(c->ev_in[1], s));  // (streamed/overlapped: after the last chunk)
     } catch (Fail f) {
         if (d_bases) cudaFreeAsync(d_bases, s);
         if (d_off) cudaFreeAsync(d_off, s);
         return f.code;
     }
+    host_ms[TURTLE_HOST_INPUT] = ms_since(t_call);
+    const clk::time_point t_path = clk::now();
     DeviceOut o;
     if (overlapped) {
         try {
@@ -1706,6 +1960,7 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     if (d_bases) cudaFreeAsync(d_bases, s);
     cudaFreeAsync(d_off, s);
     if (rc) return rc;
+    host_ms[TURTLE_HOST_PATH] = ms_since(t_path);
     const int kw = k <= 32 ? 1 : 2;
     bool fk = true, fc = true;
     out->keys = (uint64_t *)result_alloc(8 * kw * (o.n ? o.n : 1), &fk);
@@ -1714,9 +1969,16 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         turtle_result_free(out);
         return TURTLE_E_NOMEM;
     }
+    const size_t key_bytes = 8 * kw * o.n, count_bytes = o.counts ? 4 * o.n : 0;
     try {
-        copy_to_host(c, out->keys, o.keys, 8 * kw * o.n, s, fk);
-        if (o.counts) copy_to_host(c, out->counts, o.counts, 4 * o.n, s, fc);
+        const clk::time_point t_touch = clk::now();  // fresh host pages are touched first (see first_touch)
+        if (fk && key_bytes) first_touch(out->keys, key_bytes);
+        if (fc && count_bytes) first_touch(out->counts, count_bytes);
+        host_ms[TURTLE_HOST_TOUCH] = ms_since(t_touch);
+        const clk::time_point t_out = clk::now();
+        copy_to_host(c, out->keys, o.keys, key_bytes, s, false);
+        if (o.counts) copy_to_host(c, out->counts, o.counts, count_bytes, s, false);
+        host_ms[TURTLE_HOST_OUTPUT] = ms_since(t_out);
     } catch (Fail f) {
         cudaGetLastError();
         turtle_result_free(out);
@@ -1725,6 +1987,15 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     out->k = k;
     out->n = o.n;
     out->n_windows = o.n_windows;
+    for (int i = 0; i < TURTLE_HOST_COUNT; i++) c->stats.host_ms[i] = host_ms[i];
+    float h2d = 0.f;
+    if (cudaEventElapsedTime(&h2d, c->ev_in[0], c->ev_in[1]) != cudaSuccess) {
+        cudaGetLastError();
+        h2d = 0.f;
+    }
+    c->stats.h2d_ms = h2d;
+    c->stats.h2d_bytes = n_bases + 8 * (reads->n_reads + 1);
+    c->stats.d2h_bytes = key_bytes + count_bytes;
     return TURTLE_OK;
 }
 
@@ -1741,6 +2012,16 @@ int turtle_count_ex(const turtle_reads *reads, int k, uint32_t min_count, const 
     int rc = 0;
     turtle_ctx *c = default_ctx(&rc);
     if (!c) return rc;
+    return count_host_impl(c, reads, k, min_count, params, stream, out, false);
+}
+
+int turtle_ctx_count(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t min_count, const turtle_params *params,
+                     void *stream, turtle_result *out) {
+    if (!out) return TURTLE_E_ARG;
+    memset(out, 0, sizeof(*out));
+    if (!c || !reads || !reads->offsets || (reads->n_reads && !reads->bases) || k < 1 || k > 64 || min_count < 1)
+        return TURTLE_E_ARG;
+    if (reads->offsets[reads->n_reads] < reads->offsets[0]) return TURTLE_E_ARG;  // the device checks every pair
     return count_host_impl(c, reads, k, min_count, params, stream, out, false);
 }
 

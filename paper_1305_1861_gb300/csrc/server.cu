@@ -1,14 +1,15 @@
 // Served form: a request loop that admits counting jobs by device-memory footprint as they
 // arrive and runs them with continuous batching.
 //
-// One executor thread owns the device work, in FIFO order. Whenever the GPU is free it takes
-// the oldest queued job plus every other queued job with the same k and min_count whose
-// footprint estimate still fits the HBM budget (up to max_batch jobs, and as many as the spare
-// key bits can tag), and runs them as one batched pipeline: each stage is one launch for all of
-// them. The run's results are split and copied to the host by a second thread while the next
-// run executes, so host-side work overlaps device work. A job whose estimate exceeds the whole
-// budget is refused at submit time (TURTLE_E_BUSY). Results are exactly those of turtle_count
-// on the same reads.
+// Several executor threads (default 2) share one queue and one HBM budget; each owns a context
+// (device scratch) and a stream, so the batches they run overlap on the device. Whenever an
+// executor is free it takes the oldest queued job whose footprint estimate fits what is left of
+// the budget, plus every other queued job with the same k and min_count that still fits (up to
+// max_batch jobs, and as many as the spare key bits can tag), and runs them as one batched
+// pipeline: each stage is one launch for all of them. A run's results are split and copied to
+// the host by the executor's copy-out thread while its next run executes. A job whose estimate
+// exceeds the whole budget is refused at submit time (TURTLE_E_BUSY). Results are exactly those
+// of turtle_count on the same reads.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -40,15 +41,21 @@ struct Ticket {
 
 }  // namespace
 
+// One executor: a context, a stream and a copy-out thread of its own.
+struct Executor {
+    turtle_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::unique_ptr<BatchOutput> out;
+    std::thread thread;
+};
+
 struct turtle_server {
     int device = 0;
     int max_batch = 1;
     uint64_t budget = 0, in_use = 0;
     turtle_params params{};
-    turtle_ctx *ctx = nullptr;
-    cudaStream_t stream = nullptr;
-    std::unique_ptr<BatchOutput> out;
-    std::thread executor;
+    std::vector<std::unique_ptr<Executor>> execs;
+    uint64_t running_batches = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
@@ -63,6 +70,7 @@ static void finish(turtle_server *sv, const std::vector<uint64_t> &ids, const st
                    turtle_result *outs, int rc) {
     std::lock_guard<std::mutex> g(sv->mu);
     const double t = now_ms();
+    sv->running_batches--;
     for (size_t i = 0; i < ids.size(); i++) {
         Ticket *tk = sv->tickets[ids[i]].get();
         if (rc == TURTLE_OK) {
@@ -83,7 +91,7 @@ static void finish(turtle_server *sv, const std::vector<uint64_t> &ids, const st
     sv->cv_work.notify_all();
 }
 
-static void executor_loop(turtle_server *sv) {
+static void executor_loop(turtle_server *sv, Executor *ex) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
@@ -120,6 +128,8 @@ static void executor_loop(turtle_server *sv) {
         }
         sv->stats.running += ids.size();
         sv->stats.batches++;
+        sv->running_batches++;
+        if (sv->running_batches > sv->stats.peak_running_batches) sv->stats.peak_running_batches = sv->running_batches;
         if (ids.size() > sv->stats.largest_batch) sv->stats.largest_batch = ids.size();
         if (sv->stats.running > sv->stats.peak_running) sv->stats.peak_running = sv->stats.running;
         if (sv->in_use > sv->stats.peak_admitted_bytes) sv->stats.peak_admitted_bytes = sv->in_use;
@@ -127,7 +137,7 @@ static void executor_loop(turtle_server *sv) {
         std::shared_ptr<std::vector<turtle_result>> outs = std::make_shared<std::vector<turtle_result>>(ids.size());
         std::vector<size_t> idx(ids.size());
         for (size_t i = 0; i < idx.size(); i++) idx[i] = i;
-        const int rc = batch_run_jobs(sv->ctx, jobs.data(), idx, &sv->params, sv->stream, outs->data(), *sv->out,
+        const int rc = batch_run_jobs(ex->ctx, jobs.data(), idx, &sv->params, ex->stream, outs->data(), *ex->out,
                                       [sv, ids, fps, outs](int r) { finish(sv, ids, fps, outs->data(), r); });
         if (rc) finish(sv, ids, fps, outs->data(), rc);  // nothing was posted
         lk.lock();
@@ -138,7 +148,12 @@ extern "C" {
 
 int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_batch, const turtle_params *params,
                          turtle_server **out) {
-    if (!out || max_batch < 1 || max_batch > 64) return TURTLE_E_ARG;
+    return turtle_server_create_ex(device, hbm_budget_bytes, max_batch, 2, params, out);
+}
+
+int turtle_server_create_ex(int device, uint64_t hbm_budget_bytes, int max_batch, int executors,
+                            const turtle_params *params, turtle_server **out) {
+    if (!out || max_batch < 1 || max_batch > 64 || executors < 1 || executors > 16) return TURTLE_E_ARG;
     *out = nullptr;
     turtle_server *sv = new (std::nothrow) turtle_server();
     if (!sv) return TURTLE_E_NOMEM;
@@ -160,18 +175,28 @@ int turtle_server_create(int device, uint64_t hbm_budget_bytes, int max_batch, c
     }
     sv->budget = hbm_budget_bytes;
     sv->stats.budget_bytes = hbm_budget_bytes;
-    int rc = turtle_ctx_create(device, &sv->ctx);
-    if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = TURTLE_E_CUDA;
-    if (!rc) {
-        sv->out.reset(new (std::nothrow) BatchOutput());
-        if (!sv->out || !sv->out->ok()) rc = TURTLE_E_CUDA;
+    sv->stats.executors = (uint64_t)executors;
+    int rc = TURTLE_OK;
+    for (int e = 0; e < executors && rc == TURTLE_OK; e++) {
+        std::unique_ptr<Executor> ex(new (std::nothrow) Executor());
+        if (!ex) {
+            rc = TURTLE_E_NOMEM;
+            break;
+        }
+        rc = turtle_ctx_create(device, &ex->ctx);
+        if (!rc && cudaStreamCreateWithFlags(&ex->stream, cudaStreamNonBlocking) != cudaSuccess) rc = TURTLE_E_CUDA;
+        if (!rc) {
+            ex->out.reset(new (std::nothrow) BatchOutput());
+            if (!ex->out || !ex->out->ok()) rc = TURTLE_E_CUDA;
+        }
+        sv->execs.push_back(std::move(ex));
     }
     if (rc) {
         cudaGetLastError();
         turtle_server_destroy(sv);
         return rc;
     }
-    sv->executor = std::thread(executor_loop, sv);
+    for (auto &ex : sv->execs) ex->thread = std::thread(executor_loop, sv, ex.get());
     *out = sv;
     return TURTLE_OK;
 }
@@ -215,6 +240,8 @@ int turtle_poll(turtle_server *sv, uint64_t ticket, int timeout_ms, turtle_resul
         times->queue_ms = t->t_start - t->t_submit;
         times->run_ms = t->t_end - t->t_start;
         times->total_ms = t->t_end - t->t_submit;
+        times->start_ms = t->t_start;
+        times->end_ms = t->t_end;
     }
     sv->tickets.erase(it);
     return rc;
@@ -236,12 +263,18 @@ void turtle_server_destroy(turtle_server *sv) {
         sv->stop = true;
     }
     sv->cv_work.notify_all();
-    if (sv->executor.joinable()) sv->executor.join();  // the running batch finishes first
-    if (sv->out) sv->out->drain();                       // and its copy-out
-    sv->out.reset();
+    for (auto &ex : sv->execs)
+        if (ex->thread.joinable()) ex->thread.join();  // running batches finish first
+    for (auto &ex : sv->execs) {
+        if (ex->out) ex->out->drain();  // and their copy-out
+        ex->out.reset();
+    }
     for (auto &kv : sv->tickets) turtle_result_free(&kv.second->res);
-    if (sv->ctx) turtle_ctx_destroy(sv->ctx);
-    if (sv->stream) cudaStreamDestroy(sv->stream);
+    for (auto &ex : sv->execs) {
+        if (ex->ctx) turtle_ctx_destroy(ex->ctx);
+        if (ex->stream) cudaStreamDestroy(ex->stream);
+    }
+    sv->execs.clear();
     cudaGetLastError();
     delete sv;
 }
