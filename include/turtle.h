@@ -379,7 +379,7 @@ typedef struct {
     uint64_t submitted, completed, failed, queued, running, peak_running, peak_queued;
     uint64_t batches, largest_batch;  /* batched runs started; most jobs in one run */
     uint64_t executors;               /* runs that can be on the device at once */
-    uint64_t peak_running_batches;    /* most runs that were on the device at the same time */
+    uint64_t peak_running_batches;    /* most runs whose device work was in progress at the same time */
 } turtle_server_stats;
 
 /* Start a server on `device` with 2 executors (turtle_server_create_ex). */

@@ -70,7 +70,6 @@ static void finish(turtle_server *sv, const std::vector<uint64_t> &ids, const st
                    turtle_result *outs, int rc) {
     std::lock_guard<std::mutex> g(sv->mu);
     const double t = now_ms();
-    sv->running_batches--;
     for (size_t i = 0; i < ids.size(); i++) {
         Ticket *tk = sv->tickets[ids[i]].get();
         if (rc == TURTLE_OK) {
@@ -141,6 +140,7 @@ static void executor_loop(turtle_server *sv, Executor *ex) {
                                       [sv, ids, fps, outs](int r) { finish(sv, ids, fps, outs->data(), r); });
         if (rc) finish(sv, ids, fps, outs->data(), rc);  // nothing was posted
         lk.lock();
+        sv->running_batches--;  // this run's device work is done (its copy-out may still be running)
     }
 }
 

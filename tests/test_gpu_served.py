@@ -68,3 +68,38 @@ def test_poll_times_out_then_completes(have_gpu):
         srv.poll(t_small, timeout_ms=0)  # already collected: unknown ticket
     assert e.value.code == -1
     srv.close()
+
+
+def test_runs_of_different_jobs_overlap_on_the_device(have_gpu):
+    """Jobs of different k cannot share a run; with two executors, two runs are in flight at once
+    (their [start, end) intervals intersect), and every result is still the oracle's."""
+    import paper_1305_1861_gb300 as pkg
+
+    libs = [synth.fly(seed=60 + i, scale=0.02) for i in range(6)]
+    ks = [31, 63, 31, 63, 25, 63]
+    srv = pkg.Server(0, hbm_budget_bytes=64 << 30, max_batch=1, executors=2)
+    tickets = [srv.submit(l.bases, l.offsets, k, 2) for l, k in zip(libs, ks)]
+    res = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["executors"] == 2 and st["peak_running_batches"] == 2 and st["failed"] == 0
+    spans = [(tm.start_ms, tm.end_ms) for _, _, _, tm in res]
+    overlap = [(i, j) for i in range(6) for j in range(i + 1, 6)
+               if ks[i] != ks[j] and spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1]]
+    assert overlap, spans
+    for l, k, (keys, counts, nw, _) in zip(libs, ks, res):
+        ok, oc, onw = oracle.count(l.bases, l.offsets, k, 2)
+        assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+
+
+def test_one_executor_runs_one_batch_at_a_time(have_gpu):
+    import paper_1305_1861_gb300 as pkg
+
+    libs = [synth.fly(seed=60 + i, scale=0.02) for i in range(4)]
+    srv = pkg.Server(0, hbm_budget_bytes=64 << 30, max_batch=1, executors=1)
+    tickets = [srv.submit(l.bases, l.offsets, k, 2) for l, k in zip(libs, [31, 63, 31, 63])]
+    for t in tickets:
+        srv.poll(t)
+    st = srv.stats()
+    srv.close()
+    assert st["executors"] == 1 and st["peak_running_batches"] == 1 and st["batches"] == 4
