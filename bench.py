@@ -62,7 +62,7 @@ def parse():
                     help="served: also submit this many jobs at once (no arrival gaps) to compare capacity")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--blocks", default="k64,batched,served",
+    ap.add_argument("--blocks", default="batched,served,k64",
                     help="default run: also measure these workloads as nested blocks of the same line "
                          "(k64, batched, served; 'none' for the headline alone)")
     ap.add_argument("--block-steps", type=int, default=3, help="timed steps of the k64 and batched blocks")

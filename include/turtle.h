@@ -280,6 +280,11 @@ typedef struct {
 /* Statistics of the context's last successful call. */
 int turtle_ctx_stats(const turtle_ctx *ctx, turtle_stats *st);
 
+/* Device memory of the context's pool: *used = bytes held by live buffers (the last call's device
+ * result, between calls), *reserved = bytes the pool keeps from the driver for later calls. After a
+ * failed call, used returns to what it was before the call. Either pointer may be NULL. */
+int turtle_ctx_pool_bytes(const turtle_ctx *ctx, uint64_t *used, uint64_t *reserved);
+
 /* Host-memory form on a caller-owned context: as turtle_count_ex (reads in host memory, result in
  * library-allocated host arrays owned by *out, free with turtle_result_free), run on `ctx`, whose
  * statistics then also hold the host-side phases (host_ms, h2d_ms, h2d_bytes, d2h_bytes). */

@@ -111,6 +111,8 @@ def load():
         "turtle_ctx_destroy": (None, [_p]),
         "turtle_ctx_stats": (ctypes.c_int, [_p, _p]),
         "turtle_shard_bounds": (ctypes.c_int, [_p, u32, u32, _p]),
+        "turtle_ctx_pool_bytes": (ctypes.c_int, [_p, _p, _p]),
+        "turtle_test_inject": (ctypes.c_int, [ctypes.c_int, u64]),
         "turtle_ctx_count": (ctypes.c_int, [_p, _p, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_count_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_frequent": (ctypes.c_int, [_p, ctypes.c_int, _p, _p, _p]),
@@ -440,6 +442,13 @@ class Context:
         st = Stats()
         _check(self._lib.turtle_ctx_stats(self._h, ctypes.byref(st)), "turtle_ctx_stats")
         return st.as_dict()
+
+    def pool_bytes(self):
+        """(bytes used by live buffers, bytes reserved) of this context's device memory pool."""
+        used, reserved = u64(), u64()
+        _check(self._lib.turtle_ctx_pool_bytes(self._h, ctypes.byref(used), ctypes.byref(reserved)),
+               "turtle_ctx_pool_bytes")
+        return int(used.value), int(reserved.value)
 
     # ------------------------------------------------------------ per-step entry points
     def turtle_extract(self, bases, offsets, k: int, stream=None):

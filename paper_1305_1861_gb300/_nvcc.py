@@ -43,7 +43,7 @@ def _stale(lib: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "turtle.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
     if not force and not _stale(LIB, srcs + headers + [__file__]):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

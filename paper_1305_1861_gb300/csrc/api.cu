@@ -21,6 +21,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <initializer_list>
 #include <chrono>
 #include <map>
@@ -30,6 +31,7 @@
 #include <vector>
 
 #include "turtle.h"
+#include "turtle_testing.h"
 #include "common.cuh"
 #include "host.h"
 #include "kernels.h"
@@ -112,6 +114,24 @@ struct Fail {
     int code;
 };
 
+// Failure injection (turtle_testing.h): armed by turtle_test_inject, each fires once.
+struct Injection {
+    std::atomic<int64_t> device_alloc{-1};  // allocations to let through before one fails (-1: off)
+    std::atomic<int64_t> host_alloc{-1};
+    std::atomic<uint32_t> lookback_spins{0};  // > 0: the next merge skips tile 0, waits run out after this many
+    std::atomic<uint64_t> cand_cap{0};        // > 0: pass 1's candidate capacity for the next call
+};
+Injection g_inject;
+
+// True when an armed countdown reaches its allocation (and disarms it).
+bool inject_fires(std::atomic<int64_t> &left) {
+    int64_t v = left.load();
+    while (v >= 0) {
+        if (left.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
 void ck(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) throw Fail{TURTLE_E_NOMEM};
     if (e != cudaSuccess) throw Fail{TURTLE_E_CUDA};
@@ -120,6 +140,7 @@ void ck(cudaError_t e) {
 void *ctx_alloc(turtle_ctx *c, size_t bytes, cudaStream_t s, bool is_result = false) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (inject_fires(g_inject.device_alloc)) throw Fail{TURTLE_E_NOMEM};
     cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -699,8 +720,9 @@ void run_lazy(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, c
             uint64_t *lb = (uint64_t *)ctx_alloc(c, 8 * mt, s);
             uint32_t *tc = (uint32_t *)ctx_alloc(c, 16, s);
             tm.start(TURTLE_STAGE_MERGE);
+            const uint32_t inj = g_inject.lookback_spins.exchange(0);
             launch_merge_counts<K>(lc, R, Rc, nR, (const K *)po.keys, po.counts, po.n, Rn, Rnc, ctr + C_UNIQUE, split,
-                                   lb, tc, err);
+                                   lb, tc, err, inj > 0, inj);
             tm.stop(TURTLE_STAGE_MERGE);
             st.stage_launches[TURTLE_STAGE_MERGE] += 2;
             read_back(c, s);
@@ -976,7 +998,9 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         const int hist_passes = bucketed ? (bucket_bits + 7) / 8 : hashed ? 0 : passes;
         ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
         tm.start(TURTLE_STAGE_FILTER);
-        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, Wg, firsts, ctr + C_FIRST, Wg, hist,
+        const uint64_t inj_cap = g_inject.cand_cap.exchange(0);  // failure injection: a smaller candidate room
+        const uint64_t cand_cap = inj_cap && inj_cap < Wg ? inj_cap : Wg;
+        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cand_cap, firsts, ctr + C_FIRST, Wg, hist,
                         hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
                         tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
                         bucketed ? &bg : nullptr);
@@ -1263,6 +1287,7 @@ constexpr size_t RBUF_MIN = (size_t)1 << 20;  // smaller buffers are not worth k
 
 // *fresh: the buffer's pages may not exist yet.
 void *result_alloc(size_t bytes, bool *fresh) {
+    if (inject_fires(g_inject.host_alloc)) return nullptr;
     {
         std::lock_guard<std::mutex> g(g_rbuf_mu);
         auto it = g_rbuf_idle.lower_bound(bytes);
@@ -1802,6 +1827,41 @@ void turtle_ctx_destroy(turtle_ctx *c) {
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
+}
+
+int turtle_ctx_pool_bytes(const turtle_ctx *c, uint64_t *used, uint64_t *reserved) {
+    if (!c) return TURTLE_E_ARG;
+    uint64_t u = 0, r = 0;
+    if (cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess ||
+        cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess) {
+        cudaGetLastError();
+        return TURTLE_E_CUDA;
+    }
+    if (used) *used = u;
+    if (reserved) *reserved = r;
+    return TURTLE_OK;
+}
+
+int turtle_test_inject(int what, uint64_t value) {
+    switch (what) {
+    case TURTLE_INJECT_NONE:
+        g_inject.device_alloc = -1;
+        g_inject.host_alloc = -1;
+        g_inject.lookback_spins = 0;
+        g_inject.cand_cap = 0;
+        return TURTLE_OK;
+    case TURTLE_INJECT_DEVICE_ALLOC: g_inject.device_alloc = (int64_t)value; return TURTLE_OK;
+    case TURTLE_INJECT_HOST_ALLOC: g_inject.host_alloc = (int64_t)value; return TURTLE_OK;
+    case TURTLE_INJECT_LOOKBACK:
+        if (value == 0 || value > 0xffffffffull) return TURTLE_E_ARG;
+        g_inject.lookback_spins = (uint32_t)value;
+        return TURTLE_OK;
+    case TURTLE_INJECT_CAND_CAP:
+        if (value == 0) return TURTLE_E_ARG;
+        g_inject.cand_cap = value;
+        return TURTLE_OK;
+    default: return TURTLE_E_ARG;
+    }
 }
 
 int turtle_shard_bounds(const uint64_t *part_windows, uint32_t n_parts, uint32_t n_shards, uint32_t *bounds) {

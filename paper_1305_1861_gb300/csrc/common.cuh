@@ -245,7 +245,8 @@ __device__ __forceinline__ uint64_t lookback_prefix(uint64_t *status, uint64_t s
 // predecessor tile-1-l, so one round trip covers 32 predecessors. Returns the exclusive
 // prefix in every lane and publishes the inclusive one. Bounded like lookback_prefix.
 __device__ __forceinline__ uint64_t lookback_prefix_warp(uint64_t *status, uint64_t tile, uint64_t aggregate,
-                                                         uint32_t epoch, uint32_t *err) {
+                                                         uint32_t epoch, uint32_t *err,
+                                                         uint32_t spin_limit = LB_SPIN_LIMIT) {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
         if (lane == 0) st_relaxed(status, lb_pack(LB_INC, epoch, aggregate));
@@ -270,7 +271,7 @@ __device__ __forceinline__ uint64_t lookback_prefix_warp(uint64_t *status, uint6
         const int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;  // nearest predecessor with a prefix
         const uint32_t need = first_inc >= 31 ? FULL : ((2u << first_inc) - 1u);
         if ((ready_mask & need) != need) {
-            if (++spins > LB_SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 if (lane == 0) atomicOr(err, ERR_LOOKBACK);
                 break;
             }

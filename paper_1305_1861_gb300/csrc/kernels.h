@@ -195,11 +195,14 @@ void launch_bucket_gather(const LaunchCfg &c, const K *tmp_keys, const uint32_t 
 // Merge the ascending runs of distinct keys A[0 .. na) and B[0 .. nb) (counts ca, cb) into out/cout, a key in
 // both inputs once with its counts added; *n_out <- the merged length. Scratch: split (merge_tiles(na + nb) + 1
 // words), lookback (merge_tiles(na + nb) words), tile_ctr (one word). out must not alias A or B.
+// skip_tile0 / spin_limit (failure-injection tests only): start the tile tickets at 1, so the look-back
+// waits of tiles 1.. run out after spin_limit rounds (0 = the default limit) and ERR_LOOKBACK is set.
 uint64_t merge_tiles(uint64_t n);
 template <class K>
 void launch_merge_counts(const LaunchCfg &c, const K *A, const uint32_t *ca, uint64_t na, const K *B,
                          const uint32_t *cb, uint64_t nb, K *out, uint32_t *cout, unsigned long long *n_out,
-                         uint64_t *split, uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err);
+                         uint64_t *split, uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err,
+                         bool skip_tile0 = false, uint32_t spin_limit = 0);
 
 // ---------------------------------------------------------------- hash-table counting (hashcount.cu)
 // Open-addressing table of 128-byte lines (8 slots of 16 B for 64-bit keys, 4 of 32 B for 128-bit),

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(M_BLOCK) k_merge_counts(const K *__restrict__ 
                                                           const uint32_t *__restrict__ cb, uint64_t nb,
                                                           const uint64_t *__restrict__ split, K *__restrict__ out,
                                                           uint32_t *__restrict__ cout, unsigned long long *n_out,
-                                                          uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err) {
+                                                          uint64_t *lookback, uint32_t *tile_ctr, uint64_t n_tiles,
+                                                          uint32_t spin_limit, uint32_t *err) {
     __shared__ K s_key[M_TILE];          // the tile's A part, then its B part; later the merged tile
     __shared__ uint32_t s_cnt[M_TILE];
     __shared__ uint32_t s_scan[M_BLOCK / WARP];
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(M_BLOCK) k_merge_counts(const K *__restrict__ 
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // tiles in ticket order: look-back never waits on a later one
     __syncthreads();
+    if (s_tile >= n_tiles) return;  // a ticket past the last tile (only when the counter did not start at 0)
     const uint64_t tile = s_tile, n = na + nb;
     const uint64_t d0 = tile * (uint64_t)M_TILE, d1 = d0 + M_TILE < n ? d0 + M_TILE : n;
     const uint64_t i0 = split[tile], i1 = split[tile + 1];
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(M_BLOCK) k_merge_counts(const K *__restrict__ 
     uint32_t total;
     const uint32_t before = block_exclusive_scan<M_BLOCK>(nkeep, s_scan, &total);
     if (tid < WARP) {
-        const uint64_t e = lookback_prefix_warp(lookback, tile, total, 1, err);
+        const uint64_t e = lookback_prefix_warp(lookback, tile, total, 1, err, spin_limit);
         if (tid == 0) s_excl = e;
     }
     __syncthreads();
@@ -167,25 +169,32 @@ __global__ void __launch_bounds__(M_BLOCK) k_merge_counts(const K *__restrict__ 
 template <class K>
 void launch_merge_counts(const LaunchCfg &c, const K *A, const uint32_t *ca, uint64_t na, const K *B,
                          const uint32_t *cb, uint64_t nb, K *out, uint32_t *cout, unsigned long long *n_out,
-                         uint64_t *split, uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err) {
+                         uint64_t *split, uint64_t *lookback, uint32_t *tile_ctr, uint32_t *err, bool skip_tile0,
+                         uint32_t spin_limit) {
     cudaMemsetAsync(n_out, 0, sizeof(unsigned long long), c.stream);
     const uint64_t n = na + nb;
     if (n == 0) return;
     const uint64_t tiles = (n + M_TILE - 1) / M_TILE;
     k_merge_splits<K><<<(int)((tiles + 1 + 255) / 256), 256, 0, c.stream>>>(A, na, B, nb, tiles, split);
     cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t), c.stream);
+    // failure injection: tickets start at 1, so tile 0 never runs and its successors' look-back waits
+    // run out (the ticket past the last tile returns at once)
+    if (skip_tile0) cudaMemsetAsync(tile_ctr, 1, 1, c.stream);
     cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * tiles, c.stream);
     k_merge_counts<K><<<(int)tiles, M_BLOCK, 0, c.stream>>>(A, ca, na, B, cb, nb, split, out, cout, n_out, lookback,
-                                                             tile_ctr, err);
+                                                             tile_ctr, tiles, spin_limit ? spin_limit : LB_SPIN_LIMIT,
+                                                             err);
 }
 
 uint64_t merge_tiles(uint64_t n) { return (n + M_TILE - 1) / M_TILE; }
 
 template void launch_merge_counts<uint64_t>(const LaunchCfg &, const uint64_t *, const uint32_t *, uint64_t,
                                             const uint64_t *, const uint32_t *, uint64_t, uint64_t *, uint32_t *,
-                                            unsigned long long *, uint64_t *, uint64_t *, uint32_t *, uint32_t *);
+                                            unsigned long long *, uint64_t *, uint64_t *, uint32_t *, uint32_t *, bool,
+                                            uint32_t);
 template void launch_merge_counts<Key128>(const LaunchCfg &, const Key128 *, const uint32_t *, uint64_t,
                                           const Key128 *, const uint32_t *, uint64_t, Key128 *, uint32_t *,
-                                          unsigned long long *, uint64_t *, uint64_t *, uint32_t *, uint32_t *);
+                                          unsigned long long *, uint64_t *, uint64_t *, uint32_t *, uint32_t *, bool,
+                                          uint32_t);
 
 }  // namespace turtle
