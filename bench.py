@@ -79,6 +79,8 @@ def parse():
                          "3 = lazy sort-and-compact phases (memory-capped, chunked)")
     ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
     ap.add_argument("--pattern-bits", type=int, default=0, help="Bloom pattern bits (0 = library default)")
+    ap.add_argument("--probe-order", type=int, default=-1,
+                    help="pass 1 probes: 0 = by filter block (binned), 1 = in window order (-1 = default)")
     ap.add_argument("--micro", action="store_true",
                     help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()
@@ -324,6 +326,8 @@ def make_params(pkg, args, **kw):
         prm.budget_mib = args.budget_mib
     if args.pattern_bits:
         prm.pattern_bits = args.pattern_bits
+    if args.probe_order >= 0:
+        prm.probe_order = args.probe_order
     return prm
 
 

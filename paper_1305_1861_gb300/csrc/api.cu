@@ -226,7 +226,7 @@ bool params_ok(const turtle_params &p) {
            p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 3 && p.hash_slots_log2 <= 40 &&
            (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192) &&
            p.shard_count <= TURTLE_PARTS && p.shard_index < (p.shard_count ? p.shard_count : 1) &&
-           !(p.shard_count > 1 && p.compact == 3);
+           !(p.shard_count > 1 && p.compact == 3) && p.probe_order <= 1;
 }
 
 // Shard s of n takes the key-range parts [bounds[s], bounds[s+1]): bounds[s] is the first part at which
@@ -349,7 +349,8 @@ int batch_bucket_bits(const std::vector<unsigned long long> &lib_w, std::vector<
 template <class K>
 PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, uint32_t min_count,
                       K *cand, uint64_t n_cand, K *first_keys, uint64_t n_first, const BucketGeom &bg, int bits,
-                      uint64_t *hist, bool result_buffers, int variant, bool large_table, cudaStream_t s) {
+                      uint64_t *hist, bool result_buffers, int variant, bool large_table, cudaStream_t s,
+                      K *alt_pre = nullptr) {
     constexpr int KW = sizeof(K) / 8;
     uint32_t *err = c->d_err;
     unsigned long long *ctr = c->d_ctr;
@@ -360,7 +361,7 @@ PartOut bucketed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stat
     unsigned long long *nrep = (unsigned long long *)ctx_alloc(c, 8 * (uint64_t)B, s);
     unsigned long long *out_off = (unsigned long long *)ctx_alloc(c, 8 * ((uint64_t)B + 1), s);
     uint32_t *ticket = (uint32_t *)ctx_alloc(c, 16, s);
-    K *alt = (K *)ctx_alloc(c, sizeof(K) * (n_all ? n_all : 1), s);
+    K *alt = alt_pre ? alt_pre : (K *)ctx_alloc(c, sizeof(K) * (n_all ? n_all : 1), s);  // room for n_all keys
     uint32_t *tmp_counts = (uint32_t *)ctx_alloc(c, 4 * (n_cand ? n_cand : 1), s);
     const int passes_all = (bits + 7) / 8;
     SortScratch ss{};
@@ -1000,10 +1001,23 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         tm.start(TURTLE_STAGE_FILTER);
         const uint64_t inj_cap = g_inject.cand_cap.exchange(0);  // failure injection: a smaller candidate room
         const uint64_t cand_cap = inj_cap && inj_cap < Wg ? inj_cap : Wg;
-        launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cand_cap, firsts, ctr + C_FIRST, Wg, hist,
-                        hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
-                        tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
-                        bucketed ? &bg : nullptr);
+        // filter-blocked pass 1: the windows' keys are binned into what becomes the bucket sort's second
+        // buffer (the bins are dead once probed), so it costs no memory
+        const bool binned = bucketed && !tag && use_filter && firsts_mode && prm.probe_order == 0;
+        K *bin_keys = nullptr;
+        if (binned) {
+            bin_keys = (K *)ctx_alloc(c, sizeof(K) * Wg, s);
+            unsigned long long *bin_words = (unsigned long long *)ctx_alloc(c, 8 * pass1_bin_words(), s);
+            launch_pass1_binned<K>(lc, L, k, P, V, fg, bin_keys, Wg, bin_words, cand, ctr + C_CAND, cand_cap, firsts,
+                                   ctr + C_FIRST, Wg, hist, hist_passes, parted ? PART_BITS : 0, groups[g].first,
+                                   groups[g].second, err, &bg);
+            st.stage_launches[TURTLE_STAGE_FILTER] += 3;  // + the bin-offset scan, counted with the filter stage
+        } else {
+            launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cand_cap, firsts, ctr + C_FIRST, Wg,
+                            hist, hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
+                            tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
+                            bucketed ? &bg : nullptr);
+        }
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;
         if (!bucketed && !hashed) ck(cudaMemcpyAsync(c->h_hist, hist, 8 * 256 * passes, cudaMemcpyDeviceToHost, s));
@@ -1019,7 +1033,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, const_cast<K *>(first_keys), n_first, bg,
                                   bucket_bits, hist, !parted,
                                   prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
-                                  prm.bucket_slots != 4096, s);
+                                  prm.bucket_slots != 4096, s, bin_keys);
         } else if (hashed) {
             po = hashed_part<K>(c, lc, tm, st, min_count, cand, n_cand, first_keys, n_first, key_bits,
                                 W >= 0xfffffffeull, !parted, prm, s);

@@ -15,6 +15,8 @@
 // key seen twice emits at least one candidate (no false negatives, for any
 // interleaving). A plain load that already shows every pattern bit set proves
 // "seen" without the atomic, because bits are never cleared.
+#include <algorithm>
+
 #include "bucket.cuh"
 
 namespace turtle {
@@ -434,5 +436,268 @@ template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, 
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,
                                          uint8_t *);
+
+// ---------------------------------------------------------------- pass 1, filter-blocked (binned) form
+// The filter is far larger than L2, and in window order every probe lands on a random sector: most
+// probes miss L2 and move a whole DRAM line. The Turtle filter is designed for caches (Sec. 2.1.3:
+// one block per k-mer, so a probe touches one cache line); here the probes are also ORDERED so
+// that the cache holds the blocks being probed. Window keys are first binned by the top 8 bits of
+// their hash -- the top bits of their filter sector, so bin b holds exactly the keys whose blocks
+// lie in the b-th 1/256 of the filter -- and then probed bin after bin by all warps together: at
+// any moment the whole GPU works inside one or two bins, a few MiB of filter that stay in L2. The
+// order in which windows test-and-set the filter does not change the result: every valid window
+// still leaves as exactly one candidate or first sighting, and at most one occurrence of a key can
+// be a first sighting (see above).
+//   k_bin_count   extract + hash every valid (in-range) window, count it in its bin
+//   (scan)        exact bin offsets
+//   k_bin_scatter extract + hash again, rank inside the CTA's tile per bin, reserve each bin's run
+//                 of slots with one atomic per bin and tile, write the keys
+//   k_probe_bins  stream the binned keys in order: filter test-and-set and candidate / first-sighting
+//                 emission exactly as in k_pass1 (same staging, same bucket-index histograms)
+constexpr int BIN_BITS = 8;
+constexpr int N_BINS = 1 << BIN_BITS;
+constexpr int BT_THREADS = 256;
+constexpr int BT_ITEMS = 16;                   // positions per thread per tile
+constexpr int BT_POS = BT_THREADS * BT_ITEMS;  // 4096 positions per tile: 64 validity words
+static_assert(BT_THREADS == N_BINS, "one thread per bin in the scatter's reservation step");
+
+__device__ __forceinline__ uint32_t bin_of(uint64_t h) { return (uint32_t)(h >> (64 - BIN_BITS)); }
+
+// Validity words of the tile starting at position `base` into s_v (words past the bitmap read as 0).
+__device__ __forceinline__ void load_tile_valid(const uint64_t *__restrict__ V, uint64_t base, uint64_t n_vwords,
+                                                uint64_t *s_v) {
+    if (threadIdx.x < BT_POS / 64) {
+        const uint64_t w = base / 64 + threadIdx.x;
+        s_v[threadIdx.x] = w < n_vwords ? V[w] : 0ull;
+    }
+}
+
+template <class K, bool PARTED>
+__global__ void __launch_bounds__(BT_THREADS) k_bin_count(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                          uint64_t n_pos, int k, int part_bits, uint32_t part_lo,
+                                                          uint32_t part_hi, unsigned long long *bin_count) {
+    __shared__ uint32_t s_hist[N_BINS];
+    __shared__ uint64_t s_v[BT_POS / 64];
+    const int tid = threadIdx.x;
+    s_hist[tid] = 0;
+    const uint64_t tiles = (n_pos + BT_POS - 1) / BT_POS, n_vwords = (n_pos + 63) / 64;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t base = t * BT_POS;
+        __syncthreads();
+        load_tile_valid(V, base, n_vwords, s_v);
+        __syncthreads();
+#pragma unroll 4
+        for (int i = 0; i < BT_ITEMS; i++) {
+            const int r = tid + BT_THREADS * i;
+            const uint64_t s = base + r;
+            if (s >= n_pos || !((s_v[r >> 6] >> (r & 63)) & 1)) continue;
+            const K key = canonical<K>(P, s, k);
+            if (PARTED) {
+                const uint32_t pt = key_part(key, k, part_bits);
+                if (pt < part_lo || pt >= part_hi) continue;
+            }
+            atomicAdd(&s_hist[bin_of(key_hash(key))], 1u);
+        }
+    }
+    __syncthreads();
+    if (s_hist[tid]) atomicAdd(&bin_count[tid], (unsigned long long)s_hist[tid]);
+}
+
+template <class K, bool PARTED>
+__global__ void __launch_bounds__(BT_THREADS) k_bin_scatter(const uint64_t *__restrict__ P,
+                                                            const uint64_t *__restrict__ V, uint64_t n_pos, int k,
+                                                            int part_bits, uint32_t part_lo, uint32_t part_hi,
+                                                            unsigned long long *cursor,
+                                                            const unsigned long long *__restrict__ bin_off,
+                                                            K *__restrict__ out, uint64_t out_cap, uint32_t *err) {
+    __shared__ uint32_t s_cnt[N_BINS];
+    __shared__ unsigned long long s_base[N_BINS];
+    __shared__ uint64_t s_v[BT_POS / 64];
+    const int tid = threadIdx.x;
+    const uint64_t tiles = (n_pos + BT_POS - 1) / BT_POS, n_vwords = (n_pos + 63) / 64;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t base = t * BT_POS;
+        __syncthreads();
+        s_cnt[tid] = 0;
+        load_tile_valid(V, base, n_vwords, s_v);
+        __syncthreads();
+        K key[BT_ITEMS];
+        uint32_t slot[BT_ITEMS];  // bin | rank << 8 inside the tile's run of that bin; ~0 = no key
+#pragma unroll
+        for (int i = 0; i < BT_ITEMS; i++) {
+            const int r = tid + BT_THREADS * i;
+            const uint64_t s = base + r;
+            slot[i] = ~0u;
+            if (s >= n_pos || !((s_v[r >> 6] >> (r & 63)) & 1)) continue;
+            key[i] = canonical<K>(P, s, k);
+            if (PARTED) {
+                const uint32_t pt = key_part(key[i], k, part_bits);
+                if (pt < part_lo || pt >= part_hi) continue;
+            }
+            const uint32_t b = bin_of(key_hash(key[i]));
+            slot[i] = b | (atomicAdd(&s_cnt[b], 1u) << BIN_BITS);
+        }
+        __syncthreads();
+        if (s_cnt[tid]) s_base[tid] = atomicAdd(&cursor[tid], (unsigned long long)s_cnt[tid]);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < BT_ITEMS; i++) {
+            if (slot[i] == ~0u) continue;
+            const uint32_t b = slot[i] & (N_BINS - 1);
+            const unsigned long long o = s_base[b] + (slot[i] >> BIN_BITS);
+            if (o < bin_off[b + 1] && o < out_cap) store_key(out + o, key[i]);  // the counting pass sized every bin
+            else atomicOr(err, ERR_CAND_OVERFLOW);
+        }
+    }
+}
+
+template <class K, bool EMIT_FIRSTS, bool BY_BUCKET>
+__global__ void __launch_bounds__(P1_BLOCK) k_probe_bins(const K *__restrict__ keys, const unsigned long long *n_keys,
+                                                         uint64_t *filter, int sector_shift,
+                                                         const uint64_t *__restrict__ patterns, uint32_t pat_mask,
+                                                         K *cand, unsigned long long *cand_count, uint64_t cand_cap,
+                                                         K *firsts, unsigned long long *first_count,
+                                                         uint64_t first_cap, uint64_t *hist, int hist_passes,
+                                                         BucketGeom bg, uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
+    const int n_hist = 256 * hist_passes * (BY_BUCKET && EMIT_FIRSTS ? 2 : 1);
+    K *s_buf = reinterpret_cast<K *>(smem);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
+    uint32_t *s_fhist = s_hist + 256 * hist_passes;
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
+    for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
+    for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK) s_hist[i] = 0;
+    __syncthreads();
+    const uint64_t n = *n_keys;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    K *wbuf = s_buf + warp * P1_BUF * NBUF;
+    K *fbuf = wbuf + P1_BUF;
+    int nbuf = 0, nfirst = 0;
+    // every warp of the grid takes the next 128 keys: together they sweep the bins front to back
+    for (uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp; t * P1_TILE < n; t += (uint64_t)gridDim.x * P1_WARPS) {
+        const uint64_t base = t * P1_TILE;
+        bool ok[P1_ILP];
+        K key[P1_ILP];
+        uint64_t *addr[P1_ILP];
+        uint64_t mask[P1_ILP];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const uint64_t j = base + lane + WARP * i;
+            ok[i] = j < n;
+            if (ok[i]) {
+                key[i] = load_stream(keys + j);
+                const uint64_t h = key_hash(key[i]);
+                const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
+                addr[i] = filter + sector * 4 + ((h >> 16) & 3);
+                mask[i] = s_pat[h & pat_mask];
+            }
+        }
+        uint64_t w[P1_ILP];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) w[i] = ok[i] ? __ldcg(addr[i]) : 0;
+        bool seen[P1_ILP];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            seen[i] = ok[i];
+            if (ok[i] && (w[i] & mask[i]) != mask[i]) {
+                const uint64_t old = atomicOr((unsigned long long *)addr[i], (unsigned long long)mask[i]);
+                seen[i] = (old & mask[i]) == mask[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const uint32_t b = __ballot_sync(FULL, seen[i]);
+            if (seen[i]) wbuf[nbuf + __popc(b & lt)] = key[i];
+            nbuf += __popc(b);
+            if (nbuf >= P1_STAGE) {
+                __syncwarp();
+                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane, bg, BY_BUCKET);
+                flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+            }
+            if (EMIT_FIRSTS) {
+                const bool f = ok[i] && !seen[i];
+                const uint32_t bf = __ballot_sync(FULL, f);
+                if (f) fbuf[nfirst + __popc(bf & lt)] = key[i];
+                nfirst += __popc(bf);
+                if (nfirst >= P1_STAGE) {
+                    if (BY_BUCKET) {
+                        __syncwarp();
+                        hist_keys(fbuf, P1_STAGE, s_fhist, hist_passes, lane, bg, true);
+                    }
+                    flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane, bg, BY_BUCKET);
+    flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+    if (EMIT_FIRSTS) {
+        if (BY_BUCKET) hist_keys(fbuf, nfirst, s_fhist, hist_passes, lane, bg, true);
+        flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK)
+        if (s_hist[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)s_hist[i]);
+}
+
+uint64_t pass1_bin_words() { return 3 * (N_BINS + 1); }
+
+template <class K>
+void launch_pass1_binned(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                         const FilterGeom &f, K *bin_keys, uint64_t bin_cap, unsigned long long *bin_words, K *cand,
+                         unsigned long long *cand_count, uint64_t cand_cap, K *firsts,
+                         unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
+                         int part_bits, uint32_t part_lo, uint32_t part_hi, uint32_t *err, const BucketGeom *bucket) {
+    unsigned long long *count = bin_words, *off = bin_words + (N_BINS + 1), *cursor = bin_words + 2 * (N_BINS + 1);
+    cudaMemsetAsync(count, 0, sizeof(unsigned long long) * N_BINS, c.stream);
+    const uint64_t tiles = (L.n_bases + BT_POS - 1) / BT_POS;
+    if (tiles) {
+        auto kc = part_bits ? k_bin_count<K, true> : k_bin_count<K, false>;
+        auto ks = part_bits ? k_bin_scatter<K, true> : k_bin_scatter<K, false>;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks, BT_THREADS, 0);
+        if (per_sm < 1) per_sm = 1;
+        const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)c.sms * per_sm);
+        kc<<<grid, BT_THREADS, 0, c.stream>>>(P, V, L.n_bases, k, part_bits, part_lo, part_hi, count);
+        launch_scan_u64(c, count, N_BINS, off);
+        cudaMemcpyAsync(cursor, off, sizeof(unsigned long long) * N_BINS, cudaMemcpyDeviceToDevice, c.stream);
+        ks<<<grid, BT_THREADS, 0, c.stream>>>(P, V, L.n_bases, k, part_bits, part_lo, part_hi, cursor, off, bin_keys,
+                                              bin_cap, err);
+    } else {
+        cudaMemsetAsync(off, 0, sizeof(unsigned long long) * (N_BINS + 1), c.stream);
+    }
+    const bool emit_firsts = firsts != nullptr;
+    if (!hist) hist_passes = 0;
+    const BucketGeom bg = bucket ? *bucket : BucketGeom{};
+    const bool by_bucket = bucket != nullptr;
+    const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
+                        4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) + sizeof(uint64_t) * (f.pat_mask + 1);
+    auto kp = emit_firsts ? (by_bucket ? k_probe_bins<K, true, true> : k_probe_bins<K, true, false>)
+                          : (by_bucket ? k_probe_bins<K, false, true> : k_probe_bins<K, false, false>);
+    cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp, P1_BLOCK, smem);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t need = (L.n_bases / P1_TILE + P1_WARPS) / P1_WARPS;  // keys <= positions
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)c.sms * per_sm));
+    kp<<<grid, P1_BLOCK, smem, c.stream>>>(bin_keys, off + N_BINS, f.words, f.sector_shift, f.patterns, f.pat_mask, cand,
+                                           cand_count, cand_cap, firsts, first_count, first_cap, hist, hist_passes, bg,
+                                           err);
+}
+
+template void launch_pass1_binned<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
+                                            const uint64_t *, const FilterGeom &, uint64_t *, uint64_t,
+                                            unsigned long long *, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
+                                            unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
+                                            uint32_t *, const BucketGeom *);
+template void launch_pass1_binned<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
+                                          const uint64_t *, const FilterGeom &, Key128 *, uint64_t,
+                                          unsigned long long *, Key128 *, unsigned long long *, uint64_t, Key128 *,
+                                          unsigned long long *,
+                                          uint64_t, uint64_t *, int, int, uint32_t, uint32_t, uint32_t *,
+                                          const BucketGeom *);
 
 }  // namespace turtle

@@ -82,6 +82,17 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr, uint64_t t_begin = 0,
                   uint64_t t_end = ~0ull);
+// a2+a3, filter-blocked form of pass 1 (one library, bucketed sort-and-compact): the valid windows (of
+// parts [part_lo, part_hi) when part_bits > 0) are binned by the top 8 bits of their hash into bin_keys
+// (room for every such window), then probed bin after bin, so the filter blocks being probed stay in L2;
+// outputs as launch_pass1. bin_words: pass1_bin_words() device words of scratch.
+uint64_t pass1_bin_words();
+template <class K>
+void launch_pass1_binned(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                         const FilterGeom &f, K *bin_keys, uint64_t bin_cap, unsigned long long *bin_words, K *cand,
+                         unsigned long long *cand_count, uint64_t cand_cap, K *firsts,
+                         unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
+                         int part_bits, uint32_t part_lo, uint32_t part_hi, uint32_t *err, const BucketGeom *bucket);
 // Valid windows of each library of a batch (counts: n_libs zeroed counters).
 void launch_lib_windows(const LaunchCfg &c, const PackLayout &L, const uint64_t *V, const uint64_t *lib_starts,
                         int n_libs, unsigned long long *counts);
