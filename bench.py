@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
     ap.add_argument("--pattern-bits", type=int, default=0, help="Bloom pattern bits (0 = library default)")
     ap.add_argument("--probe-order", type=int, default=-1,
-                    help="pass 1 probes: 0 = by filter block (binned), 1 = in window order (-1 = default)")
+                    help="pass 1 probes: 0 = in window order, 1 = by filter block (binned) (-1 = default)")
     ap.add_argument("--micro", action="store_true",
                     help="measure the random 32-byte-sector read / atomic ceiling with torch gathers instead")
     return ap.parse_args()

@@ -129,11 +129,12 @@ typedef struct {
                                       concatenating shards 0 .. n-1 in order gives the whole result. Not
                                       with compact = 3 or the batched form (TURTLE_E_ARG). */
     uint32_t shard_index;          /* 0 .. shard_count - 1 */
-    uint32_t probe_order;          /* pass 1 with a filter, bucketed form (compact = 0), one library: 0 = by filter
-                                      block (default): the windows are first binned by the top 8 bits of their
-                                      hash, i.e. by the 1/256 of the filter their block lies in, and then probed
-                                      bin after bin, so the blocks being probed stay in L2; 1 = in window order.
-                                      The result is the same either way. */
+    uint32_t probe_order;          /* pass 1 with a filter, bucketed form (compact = 0), one library: 0 = in window
+                                      order (default); 1 = by filter block: the windows are first binned by the
+                                      top 8 bits of their hash, i.e. by the 1/256 of the filter their block lies
+                                      in, and then probed bin after bin, so the blocks being probed stay in L2.
+                                      The result is the same either way; on GB300 the window order is faster
+                                      (the binning passes cost more than the DRAM misses they save). */
 } turtle_params;
 
 /* Fill *p with the defaults above. */

@@ -1003,7 +1003,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         const uint64_t cand_cap = inj_cap && inj_cap < Wg ? inj_cap : Wg;
         // filter-blocked pass 1: the windows' keys are binned into what becomes the bucket sort's second
         // buffer (the bins are dead once probed), so it costs no memory
-        const bool binned = bucketed && !tag && use_filter && firsts_mode && prm.probe_order == 0;
+        const bool binned = bucketed && !tag && use_filter && firsts_mode && prm.probe_order == 1;
         K *bin_keys = nullptr;
         if (binned) {
             bin_keys = (K *)ctx_alloc(c, sizeof(K) * Wg, s);

@@ -503,6 +503,9 @@ __global__ void __launch_bounds__(BT_THREADS) k_bin_count(const uint64_t *__rest
     if (s_hist[tid]) atomicAdd(&bin_count[tid], (unsigned long long)s_hist[tid]);
 }
 
+// The tile's keys are first placed in shared memory grouped by bin (bin-major, each bin's keys in one
+// run), so that the writes of one bin's run are consecutive addresses: a warp's stores coalesce into
+// a few requests instead of one request per key.
 template <class K, bool PARTED>
 __global__ void __launch_bounds__(BT_THREADS) k_bin_scatter(const uint64_t *__restrict__ P,
                                                             const uint64_t *__restrict__ V, uint64_t n_pos, int k,
@@ -510,9 +513,13 @@ __global__ void __launch_bounds__(BT_THREADS) k_bin_scatter(const uint64_t *__re
                                                             unsigned long long *cursor,
                                                             const unsigned long long *__restrict__ bin_off,
                                                             K *__restrict__ out, uint64_t out_cap, uint32_t *err) {
-    __shared__ uint32_t s_cnt[N_BINS];
+    extern __shared__ __align__(16) unsigned char bs_smem[];
+    K *s_key = reinterpret_cast<K *>(bs_smem);                            // BT_POS keys, grouped by bin
+    uint8_t *s_bin = reinterpret_cast<uint8_t *>(s_key + BT_POS);         // bin of each staged key
+    __shared__ uint32_t s_cnt[N_BINS], s_start[N_BINS], s_scan[BT_THREADS / WARP];
     __shared__ unsigned long long s_base[N_BINS];
     __shared__ uint64_t s_v[BT_POS / 64];
+    __shared__ uint32_t s_total;
     const int tid = threadIdx.x;
     const uint64_t tiles = (n_pos + BT_POS - 1) / BT_POS, n_vwords = (n_pos + 63) / 64;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
@@ -538,21 +545,34 @@ __global__ void __launch_bounds__(BT_THREADS) k_bin_scatter(const uint64_t *__re
             slot[i] = b | (atomicAdd(&s_cnt[b], 1u) << BIN_BITS);
         }
         __syncthreads();
-        if (s_cnt[tid]) s_base[tid] = atomicAdd(&cursor[tid], (unsigned long long)s_cnt[tid]);
+        // thread b: the start of bin b's run in the staging area, and its slots in the output
+        const uint32_t cnt = s_cnt[tid];
+        uint32_t total;
+        const uint32_t st = block_exclusive_scan<BT_THREADS>(cnt, s_scan, &total);
+        s_start[tid] = st;
+        if (cnt) s_base[tid] = atomicAdd(&cursor[tid], (unsigned long long)cnt);
+        if (tid == 0) s_total = total;
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < BT_ITEMS; i++) {
             if (slot[i] == ~0u) continue;
-            const uint32_t b = slot[i] & (N_BINS - 1);
-            const unsigned long long o = s_base[b] + (slot[i] >> BIN_BITS);
-            if (o < bin_off[b + 1] && o < out_cap) store_key(out + o, key[i]);  // the counting pass sized every bin
+            const uint32_t b = slot[i] & (N_BINS - 1), j = s_start[b] + (slot[i] >> BIN_BITS);
+            s_key[j] = key[i];
+            s_bin[j] = (uint8_t)b;
+        }
+        __syncthreads();
+        // consecutive staged keys of one bin go to consecutive output slots
+        for (uint32_t j = tid; j < s_total; j += BT_THREADS) {
+            const uint32_t b = s_bin[j];
+            const unsigned long long o = s_base[b] + (j - s_start[b]);
+            if (o < bin_off[b + 1] && o < out_cap) store_key(out + o, s_key[j]);  // the counting pass sized every bin
             else atomicOr(err, ERR_CAND_OVERFLOW);
         }
     }
 }
 
 template <class K, bool EMIT_FIRSTS, bool BY_BUCKET>
-__global__ void __launch_bounds__(P1_BLOCK) k_probe_bins(const K *__restrict__ keys, const unsigned long long *n_keys,
+__global__ void __launch_bounds__(P1_BLOCK, sizeof(K) == 8 ? 4 : 2) k_probe_bins(const K *__restrict__ keys, const unsigned long long *n_keys,
                                                          uint64_t *filter, int sector_shift,
                                                          const uint64_t *__restrict__ patterns, uint32_t pat_mask,
                                                          K *cand, unsigned long long *cand_count, uint64_t cand_cap,
@@ -575,37 +595,43 @@ __global__ void __launch_bounds__(P1_BLOCK) k_probe_bins(const K *__restrict__ k
     K *wbuf = s_buf + warp * P1_BUF * NBUF;
     K *fbuf = wbuf + P1_BUF;
     int nbuf = 0, nfirst = 0;
-    // every warp of the grid takes the next 128 keys: together they sweep the bins front to back
-    for (uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp; t * P1_TILE < n; t += (uint64_t)gridDim.x * P1_WARPS) {
+    // every warp of the grid takes the next 128 keys: together they sweep the bins front to back. The
+    // keys of a warp's next chunk are loaded while the current chunk is probed.
+    const uint64_t stride = (uint64_t)gridDim.x * P1_WARPS;
+    uint64_t t = (uint64_t)blockIdx.x * P1_WARPS + warp;
+    K next[P1_ILP];
+#pragma unroll
+    for (int i = 0; i < P1_ILP; i++) {
+        const uint64_t j = t * P1_TILE + lane + WARP * i;
+        if (j < n) next[i] = load_stream(keys + j);
+    }
+    for (; t * P1_TILE < n; t += stride) {
         const uint64_t base = t * P1_TILE;
         bool ok[P1_ILP];
         K key[P1_ILP];
-        uint64_t *addr[P1_ILP];
-        uint64_t mask[P1_ILP];
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
-            const uint64_t j = base + lane + WARP * i;
-            ok[i] = j < n;
+            ok[i] = base + lane + WARP * i < n;
+            key[i] = next[i];
+            const uint64_t j = base + stride * P1_TILE + lane + WARP * i;
+            if (j < n) next[i] = load_stream(keys + j);
+        }
+        // the probed blocks are in L2 (the bins are swept in order), so the test-and-set goes straight to
+        // the atomic: its old value says whether every pattern bit was already set
+        bool seen[P1_ILP];
+        uint64_t old[P1_ILP], mask[P1_ILP];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
             if (ok[i]) {
-                key[i] = load_stream(keys + j);
                 const uint64_t h = key_hash(key[i]);
                 const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
-                addr[i] = filter + sector * 4 + ((h >> 16) & 3);
                 mask[i] = s_pat[h & pat_mask];
+                old[i] = atomicOr((unsigned long long *)(filter + sector * 4 + ((h >> 16) & 3)),
+                                  (unsigned long long)mask[i]);
             }
         }
-        uint64_t w[P1_ILP];
 #pragma unroll
-        for (int i = 0; i < P1_ILP; i++) w[i] = ok[i] ? __ldcg(addr[i]) : 0;
-        bool seen[P1_ILP];
-#pragma unroll
-        for (int i = 0; i < P1_ILP; i++) {
-            seen[i] = ok[i];
-            if (ok[i] && (w[i] & mask[i]) != mask[i]) {
-                const uint64_t old = atomicOr((unsigned long long *)addr[i], (unsigned long long)mask[i]);
-                seen[i] = (old & mask[i]) == mask[i];
-            }
-        }
+        for (int i = 0; i < P1_ILP; i++) seen[i] = ok[i] && (old[i] & mask[i]) == mask[i];
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
             const uint32_t b = __ballot_sync(FULL, seen[i]);
@@ -657,15 +683,18 @@ void launch_pass1_binned(const LaunchCfg &c, const PackLayout &L, int k, const u
     if (tiles) {
         auto kc = part_bits ? k_bin_count<K, true> : k_bin_count<K, false>;
         auto ks = part_bits ? k_bin_scatter<K, true> : k_bin_scatter<K, false>;
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks, BT_THREADS, 0);
-        if (per_sm < 1) per_sm = 1;
-        const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)c.sms * per_sm);
-        kc<<<grid, BT_THREADS, 0, c.stream>>>(P, V, L.n_bases, k, part_bits, part_lo, part_hi, count);
+        const size_t smem = (sizeof(K) + 1) * BT_POS;
+        cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm_c = 0, per_sm_s = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kc, BT_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, ks, BT_THREADS, smem);
+        const int grid_c = (int)std::min<uint64_t>(tiles, (uint64_t)c.sms * std::max(per_sm_c, 1));
+        const int grid_s = (int)std::min<uint64_t>(tiles, (uint64_t)c.sms * std::max(per_sm_s, 1));
+        kc<<<grid_c, BT_THREADS, 0, c.stream>>>(P, V, L.n_bases, k, part_bits, part_lo, part_hi, count);
         launch_scan_u64(c, count, N_BINS, off);
         cudaMemcpyAsync(cursor, off, sizeof(unsigned long long) * N_BINS, cudaMemcpyDeviceToDevice, c.stream);
-        ks<<<grid, BT_THREADS, 0, c.stream>>>(P, V, L.n_bases, k, part_bits, part_lo, part_hi, cursor, off, bin_keys,
-                                              bin_cap, err);
+        ks<<<grid_s, BT_THREADS, smem, c.stream>>>(P, V, L.n_bases, k, part_bits, part_lo, part_hi, cursor, off,
+                                                   bin_keys, bin_cap, err);
     } else {
         cudaMemsetAsync(off, 0, sizeof(unsigned long long) * (N_BINS + 1), c.stream);
     }

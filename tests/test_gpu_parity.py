@@ -321,3 +321,19 @@ def test_host_form_streamed_through_pinned_chunks(have_gpu, k, chunk_mib):
     keys, counts, nw = pkg.turtle_count(b, o, k, 2, pkg.Params.default(stream_chunk_mib=chunk_mib))
     ok, oc, onw = oracle.count(b, o, k, 2)
     assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+
+
+@pytest.mark.parametrize("k", [15, 31, 32, 33, 64])
+@pytest.mark.parametrize("budget", [0, 1])
+def test_count_with_probes_ordered_by_filter_block(ctx, k, budget):
+    """Pass 1 with its windows binned by filter block before the probes (probe_order = 1): same output,
+    in one key range and in several (a small budget)."""
+    import paper_1305_1861_gb300 as pkg
+
+    s = synth.longk(seed=30 + k, scale=0.001, k=k)
+    b, o = s.chunk(0, s.n_reads)
+    st = _check_count(ctx, b, o, k, 2, pkg.Params.default(probe_order=1, budget_mib=budget))
+    assert st["stage_launches"]["filter"] >= 3 * st["super_partitions"]
+    reads = ["A" * 100] * 1200 + ["ACGT" * 25] * 3  # one key fills one bin
+    bases, offs = brute.pack(reads)
+    _check_count(ctx, bases, offs, k, 2, pkg.Params.default(probe_order=1))
