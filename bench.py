@@ -62,7 +62,7 @@ def parse():
                     help="served: also submit this many jobs at once (no arrival gaps) to compare capacity")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--blocks", default="batched,served,k64",
+    ap.add_argument("--blocks", default="tuned,batched,served,k64",
                     help="default run: also measure these workloads as nested blocks of the same line "
                          "(k64, batched, served; 'none' for the headline alone)")
     ap.add_argument("--block-steps", type=int, default=3, help="timed steps of the k64 and batched blocks")
@@ -483,6 +483,50 @@ def run_ours(args, rank, world):
     return out
 
 
+KNOBS = ("filter_bits_per_window", "pattern_bits", "sort_tile", "bucket_slots", "bucket_windows")
+
+
+def run_tuned_block(args):
+    """Autotuner A/B on the fly-shaped library, device-resident: turtle_autotune chooses the knobs, then the
+    default and the tuned params alternate step by step (CUDA events on the launching stream)."""
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    lib, desc = workload("fly", 1.0, 0)
+    pkg.load().turtle_tune_cache_clear()
+    ctx = pkg.Context(0)
+    b = torch.from_numpy(lib.bases).cuda()
+    o = torch.from_numpy(lib.offsets.astype(np.int64)).cuda()
+    base = make_params(pkg, args)
+    base.timing = 0
+    t0 = time.perf_counter()
+    best, rep = ctx.autotune(b, o, lib.k, lib.min_count, base)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    times = {"default": [], "tuned": []}
+    for p in (base, best):
+        ctx.turtle_count_device(b, o, lib.k, lib.min_count, p, stream)
+    for step in range(2 * max(1, min(args.steps, 10))):
+        name, p = (("default", base), ("tuned", best))[step % 2]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.turtle_count_device(b, o, lib.k, lib.min_count, p, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[name].append(e0.elapsed_time(e1))
+    W = ctx.stats()["n_windows"]
+    ctx.close()
+    del b, o
+    torch.cuda.empty_cache()
+    d, t = float(np.median(times["default"])), float(np.median(times["tuned"]))
+    return {"metric": "autotuned vs default knobs, fly-shaped k=31, device-resident", "unit": METRIC,
+            "default_ms": d, "tuned_ms": t, "speedup_vs_default": d / t, "value": W / (t / 1e3),
+            "knobs_default": {k: getattr(base, k) for k in KNOBS}, "knobs_tuned": {k: getattr(best, k) for k in KNOBS},
+            "evaluations": rep.evaluations, "tune_wall_s": round(tune_s, 2),
+            "tuner_ms": {"start": rep.default_ms, "best": rep.best_ms}, "steps_each": len(times["tuned"])}
+
+
 def run_k64_block(args):
     """The long-k workload (k = 64, 128-bit keys) at full size, device-resident, with its own roofline, its
     end to end streamed through two device staging buffers in 1 GiB chunks, and its oracle baseline."""
@@ -701,14 +745,18 @@ def run_batched(args):
            "config": {"workload": "batched: 64 libraries, genome log-uniform %.3g-%.3g Mbp, coverage U(10,60), "
                                   "R in {100,150}, 1%% substitutions, k in {21,31,55}, min_count 2; %.2f Gbase"
                                   % (0.1 * args.scale, 20 * args.scale, n_bases / 1e9)},
-           "batched": res["batched"], "plain": res["plain_64_calls"],
+           "batched": res["batched"], "plain": res["plain_64_calls"], "batched_autotune": res["batched_autotune"],
            "speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched"]["s_per_batch"],
+           "autotune_speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched_autotune"]["s_per_batch"],
            "identical_results": ok}
     if args.scale == 1.0:  # the same recipe at 1/50 scale: small libraries, where per-call costs dominate
         res_s, ok_s, nb_s = compare(0.02)
         out["small_libraries"] = {"bases": nb_s, "batched": res_s["batched"], "plain": res_s["plain_64_calls"],
+                                  "batched_autotune": res_s["batched_autotune"],
                                   "speedup_vs_plain": res_s["plain_64_calls"]["s_per_batch"]
-                                  / res_s["batched"]["s_per_batch"], "identical_results": ok_s}
+                                  / res_s["batched"]["s_per_batch"],
+                                  "autotune_speedup_vs_plain": res_s["plain_64_calls"]["s_per_batch"]
+                                  / res_s["batched_autotune"]["s_per_batch"], "identical_results": ok_s}
     return out
 
 
@@ -722,9 +770,16 @@ def batched_vs_plain(pkg, jobs, args):
     def batched():
         return pkg.turtle_count_batch(jobs)
 
-    # The two forms alternate step by step and each reports its median, so a drift in the host's
-    # speed during the run (boxes differ and vary by up to 2x on the host side) hits both alike.
-    fns = (("plain_64_calls", plain), ("batched", batched))
+    tuned_params = pkg.Params.default(autotune=1)
+
+    def batched_tuned():
+        return pkg.turtle_count_batch(jobs, tuned_params)
+
+    # The forms alternate step by step and each reports its median, so a drift in the host's speed
+    # during the run (boxes differ and vary by up to 2x on the host side) hits all alike. The autotuned
+    # batch tunes each group's class in its warm-up call; the timed calls reuse the cached knobs.
+    pkg.load().turtle_tune_cache_clear()
+    fns = (("plain_64_calls", plain), ("batched", batched), ("batched_autotune", batched_tuned))
     for _ in range(max(1, args.warmup)):
         for _, fn in fns:
             out = fn()
@@ -743,7 +798,8 @@ def batched_vs_plain(pkg, jobs, args):
         dt = float(np.median(times[name]))
         res[name] = {"s_per_batch": dt, "kmers_per_s": W / dt, "windows": W,
                      "s_per_batch_all": [round(t, 4) for t in times[name]]}
-    ok = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(plain(), batched()))
+    ok = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[0], c[0])
+             and np.array_equal(a[1], c[1]) for a, b, c in zip(plain(), batched(), batched_tuned()))
     return res, ok
 
 
@@ -817,6 +873,8 @@ def run_blocks(args, out):
             a = copy.copy(args)
             a.scale, a.steps, a.warmup = 1.0, max(1, min(args.steps, args.block_steps)), 1
             res = run_batched(a)
+        elif name == "tuned":
+            res = run_tuned_block(args)
         elif name == "served":
             a = copy.copy(args)
             a.scale, a.jobs, a.saturate_jobs = 1.0, min(args.jobs, 400), min(args.saturate_jobs, 150)

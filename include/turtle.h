@@ -135,6 +135,11 @@ typedef struct {
                                       in, and then probed bin after bin, so the blocks being probed stay in L2.
                                       The result is the same either way; on GB300 the window order is faster
                                       (the binning passes cost more than the DRAM misses they save). */
+    uint32_t bucket_windows;       /* bucketed form: windows per key-range bucket, about (sets how many bucket-
+                                      index digits the radix passes sort by); 0 = 16384, else 1024 .. 2^20 */
+    uint32_t autotune;             /* turtle_count_batch: 1 = run each group of libraries (same k and min_count)
+                                      with knobs chosen by turtle_autotune on its largest library (tuned once
+                                      per class of input, then cached); 0 = as given */
 } turtle_params;
 
 /* Fill *p with the defaults above. */
@@ -415,6 +420,44 @@ int turtle_poll(turtle_server *server, uint64_t ticket, int timeout_ms, turtle_r
 int turtle_server_stats_get(turtle_server *server, turtle_server_stats *stats);
 /* Stop accepting work, let running jobs finish, drop queued ones, free everything. */
 void turtle_server_destroy(turtle_server *server);
+
+/* ------------------------------------------------------------------ autotuner
+ * Chooses the knobs that change speed but not the result -- filter bits per window and pattern bits
+ * (the filter block's fill), the onesweep tile shape (sort_tile), the bucket kernel's table size
+ * (bucket_slots) and the windows per bucket (bucket_windows: how many bucket-index radix digits are
+ * sorted) -- by coordinate descent: each knob in turn takes each of its candidate values with the
+ * others held; a value is kept when its measured time beats the best so far by more than 2%. The
+ * result is therefore never slower than the starting params on the measured runs.
+ */
+typedef struct {
+    uint32_t evaluations;  /* configurations timed (0 when taken from the cache) */
+    uint32_t cached;       /* 1: the class was tuned before; its knobs were reused, nothing was timed */
+    float default_ms;      /* time of the starting params */
+    float best_ms;         /* time of the chosen params */
+    uint64_t sample_bases; /* bases of the library the times were measured on */
+} turtle_tune_report;
+
+/* Timer of one configuration: milliseconds, or a negative value when the configuration cannot run. */
+typedef double (*turtle_tune_timer)(const turtle_params *p, void *user);
+
+/* The selection alone (host only): coordinate descent from *base with `timer`; *best receives the
+ * chosen params, *rep (may be NULL) the evaluations and times. TURTLE_E_DEVICE when the timer fails
+ * on *base itself; TURTLE_E_ARG for NULL pointers or a base without struct_size set. */
+int turtle_tune_select(const turtle_params *base, turtle_tune_timer timer, void *user, turtle_params *best,
+                       turtle_tune_report *rep);
+
+/* Device form: tune on a device-resident library (arguments as turtle_count_device; base may be NULL =
+ * defaults), timing turtle_count_device on `ctx` and `stream` with CUDA events (one warm-up, median of
+ * three runs per configuration). *best = base with the tuned knobs. Results are cached per class of
+ * input -- key width, filter used (min_count >= 2), base->compact and floor(log2(n_bases)) -- and a
+ * later call of the same class returns the cached knobs at once (rep->cached = 1). The context's
+ * last device result is invalidated. */
+int turtle_autotune(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
+                    uint64_t n_reads, int k, uint32_t min_count, const turtle_params *base, void *stream,
+                    turtle_params *best, turtle_tune_report *rep);
+
+/* Forget every cached tuning. */
+void turtle_tune_cache_clear(void);
 
 /*
  * Allocation-free variant of turtle_sort_compact (no counterpart in the paper:

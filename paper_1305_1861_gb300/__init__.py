@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
                 ("stream_chunk_mib", u32), ("sort_tile", u32),
                 ("compact", u32), ("bucket_slots", u32),
                 ("cturtle_bits_per_window", u32), ("hash_slots_log2", u32), ("shard_count", u32),
-                ("shard_index", u32), ("probe_order", u32)]
+                ("shard_index", u32), ("probe_order", u32), ("bucket_windows", u32), ("autotune", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":
@@ -56,6 +56,14 @@ class Params(ctypes.Structure):
         for k, v in kw.items():
             setattr(p, k, v)
         return p
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("evaluations", u32), ("cached", u32), ("default_ms", ctypes.c_float), ("best_ms", ctypes.c_float),
+                ("sample_bases", u64)]
+
+
+TUNE_TIMER = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class _Reads(ctypes.Structure):
@@ -113,6 +121,9 @@ def load():
         "turtle_shard_bounds": (ctypes.c_int, [_p, u32, u32, _p]),
         "turtle_ctx_pool_bytes": (ctypes.c_int, [_p, _p, _p]),
         "turtle_test_inject": (ctypes.c_int, [ctypes.c_int, u64]),
+        "turtle_tune_select": (ctypes.c_int, [_p, _p, _p, _p, _p]),
+        "turtle_autotune": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p, _p]),
+        "turtle_tune_cache_clear": (None, []),
         "turtle_ctx_count": (ctypes.c_int, [_p, _p, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_count_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_frequent": (ctypes.c_int, [_p, ctypes.c_int, _p, _p, _p]),
@@ -442,6 +453,15 @@ class Context:
         st = Stats()
         _check(self._lib.turtle_ctx_stats(self._h, ctypes.byref(st)), "turtle_ctx_stats")
         return st.as_dict()
+
+    def autotune(self, bases, offsets, k: int, min_count: int = 2, params: Params | None = None, stream=None):
+        """turtle_autotune on device-resident reads: (tuned Params, TuneReport)."""
+        best, rep = Params(), TuneReport()
+        rc = self._lib.turtle_autotune(self._h, _dptr(bases), bases.numel(), _dptr(offsets), offsets.numel() - 1, k,
+                                       min_count, ctypes.byref(params) if params else None, _stream_ptr(stream),
+                                       ctypes.byref(best), ctypes.byref(rep))
+        _check(rc, "turtle_autotune")
+        return best, rep
 
     def pool_bytes(self):
         """(bytes used by live buffers, bytes reserved) of this context's device memory pool."""

@@ -226,7 +226,8 @@ bool params_ok(const turtle_params &p) {
            p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 3 && p.hash_slots_log2 <= 40 &&
            (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192) &&
            p.shard_count <= TURTLE_PARTS && p.shard_index < (p.shard_count ? p.shard_count : 1) &&
-           !(p.shard_count > 1 && p.compact == 3) && p.probe_order <= 1;
+           !(p.shard_count > 1 && p.compact == 3) && p.probe_order <= 1 &&
+           (p.bucket_windows == 0 || (p.bucket_windows >= 1024 && p.bucket_windows <= (1u << 20)));
 }
 
 // Shard s of n takes the key-range parts [bounds[s], bounds[s+1]): bounds[s] is the first part at which
@@ -293,7 +294,9 @@ struct PartOut {
 // Bucketed sort-and-compact: stable radix sort of the candidates and of the first sightings by
 // bucket index, bucket bounds, then per bucket merge + first-sighting recount + threshold + sort,
 // then a dense gather (bucketed_part below).
-constexpr uint64_t BUCKET_WINDOWS = 16384;  // candidates + first sightings per bucket, about
+constexpr uint64_t BUCKET_WINDOWS = 16384;  // candidates + first sightings per bucket, about (default)
+
+uint64_t bucket_windows_of(const turtle_params &p) { return p.bucket_windows ? p.bucket_windows : BUCKET_WINDOWS; }
 
 // Bucket-index bits actually used, given the bits wanted: 8 per sort pass, and up to three bits
 // beyond a multiple of 8 are dropped rather than paid for with a whole extra pass (buckets up to
@@ -304,9 +307,10 @@ int bucket_bits_for(int want) {
 }
 
 // Buckets for n_all windows of the key range [part_lo, part_hi) of 2^part_bits parts; *bits = index bits.
-BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int part_bits, int k, int *bits) {
+BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int part_bits, int k, int *bits,
+                       uint64_t per_bucket = BUCKET_WINDOWS) {
     int b = 0;
-    while (b < 24 && (n_all >> b) > BUCKET_WINDOWS) b++;
+    while (b < 24 && (n_all >> b) > per_bucket) b++;
     b = bucket_bits_for(b);
     BucketGeom bg{};
     bg.k = k;
@@ -321,12 +325,13 @@ BucketGeom bucket_geom(uint64_t n_all, uint32_t part_lo, uint32_t part_hi, int p
 
 // Batch: library l gets 2^b[l] buckets for its lib_w[l] windows; the total is capped the same way
 // (the largest libraries give up bits first). Returns the index bits of the total.
-int batch_bucket_bits(const std::vector<unsigned long long> &lib_w, std::vector<int> &b) {
+int batch_bucket_bits(const std::vector<unsigned long long> &lib_w, std::vector<int> &b,
+                      uint64_t per_bucket = BUCKET_WINDOWS) {
     const size_t n = lib_w.size();
     b.assign(n, 0);
     uint64_t total = 0;
     for (size_t l = 0; l < n; l++) {
-        while (b[l] < 20 && (lib_w[l] >> b[l]) > BUCKET_WINDOWS) b[l]++;
+        while (b[l] < 20 && (lib_w[l] >> b[l]) > per_bucket) b[l]++;
         total += (uint64_t)1 << b[l];
     }
     int want = 0;
@@ -534,9 +539,9 @@ uint64_t lib_filter_regions(turtle_ctx *c, const std::vector<unsigned long long>
 
 // Batch: each library its own range of buckets, sized by its windows (lib_w); *bits = index bits.
 BucketGeom lib_buckets(turtle_ctx *c, const std::vector<unsigned long long> &lib_w, int k, int *bits,
-                       cudaStream_t s) {
+                       cudaStream_t s, uint64_t per_bucket = BUCKET_WINDOWS) {
     std::vector<int> lb;
-    *bits = batch_bucket_bits(lib_w, lb);
+    *bits = batch_bucket_bits(lib_w, lb, per_bucket);
     std::vector<uint4> lg(lib_w.size());
     uint32_t at = 0;
     for (size_t l = 0; l < lib_w.size(); l++) {
@@ -695,7 +700,8 @@ void run_lazy(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, c
         ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
         ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
         int bits = 0;
-        const BucketGeom bg = bucket_geom((t1 - t0) * 128, 0u, 1u << PART_BITS, PART_BITS, k, &bits);
+        const BucketGeom bg = bucket_geom((t1 - t0) * 128, 0u, 1u << PART_BITS, PART_BITS, k, &bits,
+                                          bucket_windows_of(prm));
         tm.start(TURTLE_STAGE_FILTER);
         launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cap, nullptr, ctr + C_FIRST, 0, hist,
                         (bits + 7) / 8, 0, 0u, 1u << PART_BITS, nullptr, 0, nullptr, err, &bg, t0, t1);
@@ -991,10 +997,10 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         int bucket_bits = 0;
         BucketGeom bg{};
         if (bucketed && tag) {  // batch: each library its own range of buckets, sized by its windows
-            bg = lib_buckets(c, lib_w, k, &bucket_bits, s);
+            bg = lib_buckets(c, lib_w, k, &bucket_bits, s, bucket_windows_of(prm));
         } else if (bucketed) {  // every window of the range becomes a candidate or a first sighting: Wg of them
             bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
-                             PART_BITS, k, &bucket_bits);
+                             PART_BITS, k, &bucket_bits, bucket_windows_of(prm));
         }
         const int hist_passes = bucketed ? (bucket_bits + 7) / 8 : hashed ? 0 : passes;
         ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
@@ -1473,8 +1479,9 @@ void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, u
     }
     constexpr int PART_BITS = 6;
     int bucket_bits = 0;
-    const BucketGeom bg = tag ? lib_buckets(c, *lib_w_est, k, &bucket_bits, s)
-                              : bucket_geom(West, 0u, 1u << PART_BITS, PART_BITS, k, &bucket_bits);
+    const BucketGeom bg = tag ? lib_buckets(c, *lib_w_est, k, &bucket_bits, s, bucket_windows_of(prm))
+                              : bucket_geom(West, 0u, 1u << PART_BITS, PART_BITS, k, &bucket_bits,
+                                            bucket_windows_of(prm));
     const int hist_passes = (bucket_bits + 7) / 8;
     uint64_t *hist = (uint64_t *)ctx_alloc(c, 8 * 256 * 16, s);
     ck(cudaMemsetAsync(hist, 0, 8 * 256 * 16, s));
@@ -1664,6 +1671,37 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
 
 std::mutex g_default_mu;
 turtle_ctx *g_default[64] = {};
+
+// Batched form with params.autotune: the knobs of a group (same k and min_count) come from
+// turtle_autotune on the group's largest library, copied to the device for the purpose (tuned once
+// per class of input; later groups of the class reuse the cached knobs without a copy).
+int tune_group(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, const turtle_params &prm,
+               cudaStream_t s, turtle_params *out) {
+    size_t big = idx[0];
+    for (size_t i : idx)
+        if (jobs[i].offsets[jobs[i].n_reads] - jobs[i].offsets[0] > jobs[big].offsets[jobs[big].n_reads] - jobs[big].offsets[0])
+            big = i;
+    const turtle_job &j = jobs[big];
+    const uint64_t nb = j.offsets[j.n_reads] - j.offsets[0];
+    std::vector<uint64_t> off(j.offsets, j.offsets + j.n_reads + 1);
+    for (uint64_t &o : off) o -= j.offsets[0];
+    turtle_params base = prm;
+    base.autotune = 0;
+    uint8_t *d_b = nullptr;
+    uint64_t *d_o = nullptr;
+    int rc = TURTLE_OK;
+    if (cudaMalloc(&d_b, nb ? nb : 16) != cudaSuccess || cudaMalloc(&d_o, 8 * off.size()) != cudaSuccess) rc = TURTLE_E_NOMEM;
+    if (!rc && ((nb && cudaMemcpyAsync(d_b, j.bases + j.offsets[0], nb, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+                cudaMemcpyAsync(d_o, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, s) != cudaSuccess))
+        rc = TURTLE_E_CUDA;
+    if (!rc) rc = turtle_autotune(c, d_b, nb, d_o, j.n_reads, j.k, j.min_count, &base, s, out, nullptr);
+    cudaStreamSynchronize(s);
+    if (d_b) cudaFree(d_b);
+    if (d_o) cudaFree(d_o);
+    cudaGetLastError();
+    out->autotune = 0;
+    return rc;
+}
 
 }  // namespace
 
@@ -2131,12 +2169,15 @@ int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_param
     // group by (k, min_count); a run holds as many libraries as the spare key bits can tag (<= 64)
     std::map<std::pair<int, uint32_t>, std::vector<size_t>> groups;
     for (size_t i = 0; i < n_jobs; i++) groups[{jobs[i].k, jobs[i].min_count}].push_back(i);
+    const turtle_params prm = resolve(params);
     for (auto &kv : groups) {
         const size_t per_run = batch_capacity(kv.first.first);
         const std::vector<size_t> &all = kv.second;
+        turtle_params gp = prm;
+        if (prm.autotune && rc == TURTLE_OK) rc = tune_group(c, jobs, all, prm, s, &gp);
         for (size_t a = 0; a < all.size() && rc == TURTLE_OK; a += per_run) {
             std::vector<size_t> idx(all.begin() + a, all.begin() + std::min(all.size(), a + per_run));
-            rc = batch_run_jobs(c, jobs, idx, params, s, outs, bo, nullptr);
+            rc = batch_run_jobs(c, jobs, idx, &gp, s, outs, bo, nullptr);
         }
     }
     const int rc_out = bo.drain();

@@ -1,0 +1,47 @@
+"""Autotuner on the GPU: the tuned params count exactly like the defaults, a class is tuned once and
+then served from the cache, and the batched form with params.autotune matches the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_device_form_and_cache(have_gpu):
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    pkg.build()
+    lib = pkg.load()
+    lib.turtle_tune_cache_clear()
+    ctx = pkg.Context(0)
+    s = synth.fly(seed=44, scale=0.02)
+    b, o = torch.from_numpy(s.bases).cuda(), torch.from_numpy(s.offsets.astype(np.int64)).cuda()
+    best, rep = ctx.autotune(b, o, 31, 2)
+    assert rep.cached == 0 and rep.evaluations == 10 and rep.best_ms <= rep.default_ms
+    assert best.struct_size == pkg.Params.default().struct_size
+    keys, counts, nw = ctx.turtle_count_device(b, o, 31, 2, best)
+    ok, oc, onw = oracle.count(s.bases, s.offsets, 31, 2)
+    assert nw == onw and np.array_equal(keys.cpu().numpy().astype(np.uint64), ok)
+    assert np.array_equal(counts.cpu().numpy().astype(np.uint64), oc)
+    best2, rep2 = ctx.autotune(b, o, 31, 2)
+    assert rep2.cached == 1 and rep2.evaluations == 0
+    for f in ("filter_bits_per_window", "pattern_bits", "sort_tile", "bucket_slots", "bucket_windows"):
+        assert getattr(best2, f) == getattr(best, f)
+    ctx.close()
+
+
+def test_batched_form_with_autotune_matches_oracle(have_gpu):
+    import paper_1305_1861_gb300 as pkg
+
+    pkg.load().turtle_tune_cache_clear()
+    specs = synth.batched_specs(seed=4, n_libs=12, scale=0.01)
+    libs = [synth.library_from_spec(sp) for sp in specs]
+    jobs = [(l.bases, l.offsets, l.k, l.min_count) for l in libs]
+    res = pkg.turtle_count_batch(jobs, pkg.Params.default(autotune=1))
+    for (b, o, k, m), (keys, counts, nw) in zip(jobs, res):
+        ok, oc, onw = oracle.count(b, o, k, m)
+        assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
