@@ -145,7 +145,11 @@ int turtle_autotune(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, con
         auto it = g_cache.find(key);
         if (it != g_cache.end()) {
             *best = start;  // the caller's other settings, with the tuned knobs of this class
-            for (const Knob &kn : knobs()) kn.set(*best, kn.get(it->second));
+            best->filter_bits_per_window = it->second.filter_bits_per_window;
+            best->pattern_bits = it->second.pattern_bits;
+            best->sort_tile = it->second.sort_tile;
+            best->bucket_slots = it->second.bucket_slots;
+            best->bucket_windows = it->second.bucket_windows;
             if (rep) {
                 memset(rep, 0, sizeof(*rep));
                 rep->cached = 1;
