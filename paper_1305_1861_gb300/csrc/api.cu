@@ -1683,6 +1683,9 @@ int tune_group(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> 
             big = i;
     const turtle_job &j = jobs[big];
     const uint64_t nb = j.offsets[j.n_reads] - j.offsets[0];
+    turtle_params base0 = prm;
+    base0.autotune = 0;
+    if (tune_cache_lookup(j.k, j.min_count, base0, nb, out)) return TURTLE_OK;  // tuned before: no copy
     std::vector<uint64_t> off(j.offsets, j.offsets + j.n_reads + 1);
     for (uint64_t &o : off) o -= j.offsets[0];
     turtle_params base = prm;

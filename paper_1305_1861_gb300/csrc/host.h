@@ -52,3 +52,7 @@ size_t batch_capacity(int k);
 // on an error nothing is posted and done is not called.
 int batch_run_jobs(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, const turtle_params *params,
                    cudaStream_t s, turtle_result *outs, BatchOutput &bo, std::function<void(int)> done);
+
+// Autotuner cache: the tuned knobs of (k's key width, min_count >= 2, start.compact, log2 n_bases) merged into
+// *best = start, if that class was tuned before.
+bool tune_cache_lookup(int k, uint32_t min_count, const turtle_params &start, uint64_t n_bases, turtle_params *best);

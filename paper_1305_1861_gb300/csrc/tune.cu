@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "turtle.h"
+#include "host.h"
 
 namespace {
 
@@ -48,6 +49,7 @@ const std::vector<Knob> &knobs() {
 }
 
 constexpr double KEEP_GAIN = 0.98;  // a candidate must beat the best time so far by 2%
+constexpr int CONFIRM = 3;          // interleaved re-timings of the start and the choice
 
 std::mutex g_cache_mu;
 // (key words, filter on, compact form, log2 bases) -> tuned params
@@ -103,7 +105,7 @@ int turtle_tune_select(const turtle_params *base, turtle_tune_timer timer, void 
     if (!base || !timer || !best || base->struct_size != sizeof(turtle_params)) return TURTLE_E_ARG;
     turtle_tune_report r{};
     turtle_params cur = *base;
-    const double t0 = timer(&cur, user);
+    double t0 = timer(&cur, user);
     r.evaluations = 1;
     if (t0 < 0) return TURTLE_E_DEVICE;
     double best_t = t0;
@@ -121,12 +123,54 @@ int turtle_tune_select(const turtle_params *base, turtle_tune_timer timer, void 
             }
         }
     }
+    // A changed choice is confirmed against the start by interleaved re-timings (start, choice, start,
+    // choice, ...): it is kept only if its median still wins by the same margin, so one lucky timing
+    // during the sweep cannot select it.
+    bool changed = false;
+    for (const Knob &kn : knobs()) changed |= kn.get(cur) != kn.get(*base);
+    if (changed) {
+        double ts[CONFIRM], tc[CONFIRM];
+        for (int i = 0; i < CONFIRM; i++) {
+            ts[i] = timer(base, user);
+            tc[i] = timer(&cur, user);
+            r.evaluations += 2;
+        }
+        std::sort(ts, ts + CONFIRM);
+        std::sort(tc, tc + CONFIRM);
+        const double ms = ts[CONFIRM / 2], mc = tc[CONFIRM / 2];
+        if (mc >= 0 && ms >= 0 && mc < ms * KEEP_GAIN) {
+            best_t = mc;
+            t0 = ms;
+        } else {
+            cur = *base;
+            best_t = t0 = ms >= 0 ? ms : t0;
+        }
+    }
     *best = cur;
     r.default_ms = (float)t0;
     r.best_ms = (float)best_t;
     if (rep) *rep = r;
     return TURTLE_OK;
 }
+
+}  // extern "C"
+
+bool tune_cache_lookup(int k, uint32_t min_count, const turtle_params &start, uint64_t n_bases, turtle_params *best) {
+    const auto key = std::make_tuple(k <= 32 ? 1 : 2, min_count >= 2 ? 1 : 0, start.compact,
+                                     log2_floor(n_bases ? n_bases : 1));
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) return false;
+    *best = start;  // the caller's other settings, with the tuned knobs of this class
+    best->filter_bits_per_window = it->second.filter_bits_per_window;
+    best->pattern_bits = it->second.pattern_bits;
+    best->sort_tile = it->second.sort_tile;
+    best->bucket_slots = it->second.bucket_slots;
+    best->bucket_windows = it->second.bucket_windows;
+    return true;
+}
+
+extern "C" {
 
 int turtle_autotune(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, const uint64_t *offsets,
                     uint64_t n_reads, int k, uint32_t min_count, const turtle_params *base, void *stream,
@@ -140,22 +184,12 @@ int turtle_autotune(turtle_ctx *ctx, const uint8_t *bases, uint64_t n_bases, con
     }
     const auto key = std::make_tuple(k <= 32 ? 1 : 2, min_count >= 2 ? 1 : 0, start.compact,
                                      log2_floor(n_bases ? n_bases : 1));
-    {
-        std::lock_guard<std::mutex> g(g_cache_mu);
-        auto it = g_cache.find(key);
-        if (it != g_cache.end()) {
-            *best = start;  // the caller's other settings, with the tuned knobs of this class
-            best->filter_bits_per_window = it->second.filter_bits_per_window;
-            best->pattern_bits = it->second.pattern_bits;
-            best->sort_tile = it->second.sort_tile;
-            best->bucket_slots = it->second.bucket_slots;
-            best->bucket_windows = it->second.bucket_windows;
-            if (rep) {
-                memset(rep, 0, sizeof(*rep));
-                rep->cached = 1;
-            }
-            return TURTLE_OK;
+    if (tune_cache_lookup(k, min_count, start, n_bases, best)) {
+        if (rep) {
+            memset(rep, 0, sizeof(*rep));
+            rep->cached = 1;
         }
+        return TURTLE_OK;
     }
     DeviceRun run{ctx, bases, n_bases, offsets, n_reads, k, min_count, (cudaStream_t)stream, {nullptr, nullptr}};
     if (cudaEventCreate(&run.ev[0]) != cudaSuccess || cudaEventCreate(&run.ev[1]) != cudaSuccess) {

@@ -56,7 +56,8 @@ def test_separable_cost_reaches_its_optimum_in_one_sweep(pkg):
 
     rc, best, rep, calls = _select(pkg, cost)
     assert rc == 0 and best == pref
-    assert rep.evaluations == len(calls) == 1 + sum(len(v) - 1 for v in KNOBS.values())
+    sweep = 1 + sum(len(v) - 1 for v in KNOBS.values())
+    assert rep.evaluations == len(calls) == sweep + 2 * 3  # the sweep, then 3 interleaved confirmations
     assert rep.best_ms == pytest.approx(100.0) and rep.default_ms == pytest.approx(100.0 + 5 * 5)
 
 
@@ -87,3 +88,19 @@ def test_failing_start_is_an_error(pkg):
     best = pkg.Params()
     assert pkg.load().turtle_tune_select(ctypes.byref(bad), pkg.TUNE_TIMER(lambda p, u: 1.0), None,
                                          ctypes.byref(best), None) == -1
+
+
+def test_one_lucky_timing_is_not_kept(pkg):
+    """A candidate that measured fast once (noise) but not in the interleaved confirmation is dropped."""
+    default = {n: v[0] for n, v in KNOBS.items()}
+    seen = set()
+
+    def cost(c):
+        key = tuple(sorted(c.items()))
+        if c["sort_tile"] == 2 and key not in seen:
+            seen.add(key)
+            return 40.0  # the first timing of this configuration is lucky
+        return 50.0
+
+    rc, best, rep, calls = _select(pkg, cost)
+    assert rc == 0 and best == default and rep.best_ms == pytest.approx(50.0)
