@@ -657,7 +657,7 @@ double device_room(turtle_ctx *c) {
 // candidates: the compacted prefix is never sorted again. A key seen twice has at least one
 // candidate (the filter has no false negatives), so the running array holds every key that can
 // reach min_count >= 2; the exact count of each is then taken by the second pass, which re-extracts
-// every window and counts it in a table of the running array's keys (the benchmark spec (d)); the keys are
+// every window and counts it in a table of the running array's keys (the exact recount); the keys are
 // kept in the array's order when count >= min_count. With min_count = 1 every window is a
 // candidate and the merged run lengths are the counts.
 template <class K>
