@@ -192,6 +192,7 @@ void read_back(turtle_ctx *c, cudaStream_t s) {
     if (e & ERR_BAD_OFFSETS) throw Fail{TURTLE_E_ARG};
     if (e & ERR_COUNT_OVERFLOW) throw Fail{TURTLE_E_OVERFLOW};
     if (e & ERR_CAND_OVERFLOW) throw Fail{TURTLE_E_CAPACITY};  // an output larger than the room given to it
+    if (e & ERR_PART_MISMATCH) throw Fail{TURTLE_E_DEVICE};    // a key-range test disagreed with the key
     if (e) throw Fail{TURTLE_E_DEVICE};
 }
 

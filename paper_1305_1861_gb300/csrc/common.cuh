@@ -13,6 +13,7 @@ enum : uint32_t {
     ERR_COUNT_OVERFLOW = 8u,  // a uint32 count reached 2^32-1
     ERR_BAD_OFFSETS = 16u,    // offsets not monotone or past n_bases
     ERR_NOT_FOUND = 32u,      // threshold lookup missed a key that was inserted
+    ERR_PART_MISMATCH = 64u,  // a window's key-range test disagreed with its canonical key's range
 };
 
 constexpr int WARP = 32;

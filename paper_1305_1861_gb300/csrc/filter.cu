@@ -362,6 +362,170 @@ __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys,
     }
 }
 
+// ---------------------------------------------------------------- pass 1 for one key range (super-partitions, shards)
+// A key range holds a fraction of the windows. Testing each window where it is and probing the filter
+// only for those in range would leave most lanes of a warp idle during the probe round trips, which
+// are what pass 1 waits on. Instead, each warp first tests a tile of 128 windows for the range and
+// appends the positions of those in range to a queue in shared memory; whenever the queue holds 128
+// positions, the warp extracts their keys and probes them four per lane, as pass 1 does for a full
+// tile. The range test needs only the top 31 bits of the canonical key, which are the smaller of
+// the top 31 bits of the forward encoding and of the reverse complement (if those differ, the
+// smaller one belongs to the smaller key; if they are equal, both keys share them). For 128-bit keys
+// those come from the window's first 32 bases and from its last 32 bases, without building either
+// full key; the probe phase checks every key against the range once more.
+constexpr int PQ_CAP = 2 * P1_TILE;  // queue of in-range positions per warp: one tile's worth beyond a full batch
+
+template <class K>
+__device__ __forceinline__ uint32_t window_part(const uint64_t *__restrict__ P, uint64_t s, int k, int part_bits);
+template <>
+__device__ __forceinline__ uint32_t window_part<uint64_t>(const uint64_t *__restrict__ P, uint64_t s, int k,
+                                                          int part_bits) {
+    return key_part(canonical_at(P, s, k), k, part_bits);
+}
+template <>
+__device__ __forceinline__ uint32_t window_part<Key128>(const uint64_t *__restrict__ P, uint64_t s, int k,
+                                                        int part_bits) {
+    const uint64_t e = s + (uint64_t)k - 32;  // k >= 33: the window's last 32 bases start at e >= s
+    const uint64_t a = stream_bits(__ldg(P + (s >> 5)), __ldg(P + (s >> 5) + 1), (int)(s & 31) << 1);
+    const uint64_t b = stream_bits(__ldg(P + (e >> 5)), __ldg(P + (e >> 5) + 1), (int)(e & 31) << 1);
+    const uint64_t vf = a >> 33, vr = (~rev2(b)) >> 33;  // top 31 bits of forward / reverse complement
+    const uint64_t v = vf < vr ? vf : vr;
+    return (uint32_t)((v * ((1ull << 32) - v)) >> (62 - part_bits));
+}
+
+template <class K, bool EMIT_FIRSTS, bool BY_BUCKET>
+__global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                          uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
+                                                          const uint64_t *__restrict__ patterns, uint32_t pat_mask,
+                                                          K *cand, unsigned long long *cand_count, uint64_t cand_cap,
+                                                          K *firsts, unsigned long long *first_count,
+                                                          uint64_t first_cap, uint64_t *hist, int hist_passes,
+                                                          int part_bits, uint32_t part_lo, uint32_t part_hi,
+                                                          BucketGeom bg, uint64_t t_begin, uint64_t t_end,
+                                                          uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NBUF = EMIT_FIRSTS ? 2 : 1;
+    const int n_hist = 256 * hist_passes * (BY_BUCKET && EMIT_FIRSTS ? 2 : 1);
+    K *s_buf = reinterpret_cast<K *>(smem);
+    uint64_t *s_queue = reinterpret_cast<uint64_t *>(smem + sizeof(K) * P1_BUF * P1_WARPS * NBUF);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_queue + PQ_CAP * P1_WARPS);
+    uint32_t *s_fhist = s_hist + 256 * hist_passes;
+    uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
+    for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
+    for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK) s_hist[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    K *wbuf = s_buf + warp * P1_BUF * NBUF;
+    K *fbuf = wbuf + P1_BUF;
+    uint64_t *q = s_queue + warp * PQ_CAP;
+    int nbuf = 0, nfirst = 0, nq = 0;
+    // extract, test-and-set and emit the first `count` queued positions (count <= P1_TILE)
+    auto probe = [&](int count) {
+        bool ok[P1_ILP], seen[P1_ILP];
+        K key[P1_ILP];
+        uint64_t *addr[P1_ILP];
+        uint64_t mask[P1_ILP], w[P1_ILP];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const int j = lane + WARP * i;
+            ok[i] = j < count;
+            if (ok[i]) {
+                key[i] = canonical<K>(P, q[j], k);
+                const uint32_t pt = key_part(key[i], k, part_bits);
+                if (pt < part_lo || pt >= part_hi) {  // cannot happen: the range test is exact
+                    atomicOr(err, ERR_PART_MISMATCH);
+                    ok[i] = false;
+                }
+            }
+            if (ok[i]) {
+                const uint64_t h = key_hash(key[i]);
+                const uint64_t sector = sector_shift < 64 ? (h >> sector_shift) : 0;
+                addr[i] = filter + sector * 4 + ((h >> 16) & 3);
+                mask[i] = s_pat[h & pat_mask];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) w[i] = ok[i] ? __ldcg(addr[i]) : 0;
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            seen[i] = ok[i];
+            if (ok[i] && (w[i] & mask[i]) != mask[i]) {
+                const uint64_t old = atomicOr((unsigned long long *)addr[i], (unsigned long long)mask[i]);
+                seen[i] = (old & mask[i]) == mask[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const uint32_t b = __ballot_sync(FULL, seen[i]);
+            if (seen[i]) wbuf[nbuf + __popc(b & lt)] = key[i];
+            nbuf += __popc(b);
+            if (nbuf >= P1_STAGE) {
+                __syncwarp();
+                hist_keys(wbuf, P1_STAGE, s_hist, hist_passes, lane, bg, BY_BUCKET);
+                flush_full(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+            }
+            if (EMIT_FIRSTS) {
+                const bool f = ok[i] && !seen[i];
+                const uint32_t bf = __ballot_sync(FULL, f);
+                if (f) fbuf[nfirst + __popc(bf & lt)] = key[i];
+                nfirst += __popc(bf);
+                if (nfirst >= P1_STAGE) {
+                    if (BY_BUCKET) {
+                        __syncwarp();
+                        hist_keys(fbuf, P1_STAGE, s_fhist, hist_passes, lane, bg, true);
+                    }
+                    flush_full(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+                }
+            }
+        }
+    };
+    for (uint64_t t = t_begin + (uint64_t)blockIdx.x * P1_WARPS + warp; t < t_end; t += (uint64_t)gridDim.x * P1_WARPS) {
+        const uint64_t base = t * P1_TILE;
+        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const int r = lane + WARP * i;
+            const uint64_t s = base + r;
+            bool in = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
+            if (in) {
+                const uint32_t pt = window_part<K>(P, s, k, part_bits);
+                in = pt >= part_lo && pt < part_hi;
+            }
+            const uint32_t m = __ballot_sync(FULL, in);
+            if (in) q[nq + __popc(m & lt)] = s;
+            nq += __popc(m);
+        }
+        __syncwarp();
+        if (nq >= P1_TILE) {
+            probe(P1_TILE);
+            __syncwarp();
+            const int rest = nq - P1_TILE;  // < P1_TILE: move the remainder to the front
+            uint64_t tail[P1_ILP];
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++)
+                if (lane + WARP * i < rest) tail[i] = q[P1_TILE + lane + WARP * i];
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++)
+                if (lane + WARP * i < rest) q[lane + WARP * i] = tail[i];
+            __syncwarp();
+            nq = rest;
+        }
+    }
+    if (nq > 0) probe(nq);
+    __syncwarp();
+    hist_keys(wbuf, nbuf, s_hist, hist_passes, lane, bg, BY_BUCKET);
+    flush_rest(wbuf, nbuf, cand, cand_count, cand_cap, err, lane);
+    if (EMIT_FIRSTS) {
+        if (BY_BUCKET) hist_keys(fbuf, nfirst, s_fhist, hist_passes, lane, bg, true);
+        flush_rest(fbuf, nfirst, firsts, first_count, first_cap, err, lane, true);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK)
+        if (s_hist[i]) atomicAdd((unsigned long long *)&hist[i], (unsigned long long)s_hist[i]);
+}
+
 template <class K, bool F, bool E>
 static auto pass1_by_mode(int mode) -> decltype(&k_pass1<K, F, E, 0>) {
     switch (mode) {  // the combinations the pipeline uses (batches are never split into key ranges)
@@ -400,6 +564,22 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     const size_t smem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) +
                         4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) +
                         (use_filter ? sizeof(uint64_t) * (f.pat_mask + 1) : 0);
+    if (part_bits && !n_libs && use_filter) {  // one key range of a library: the compacting form
+        const size_t rsmem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) + 8 * PQ_CAP * P1_WARPS +
+                             4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) +
+                             sizeof(uint64_t) * (f.pat_mask + 1);
+        auto rk = emit_firsts ? (by_bucket ? k_pass1_range<K, true, true> : k_pass1_range<K, true, false>)
+                              : (by_bucket ? k_pass1_range<K, false, true> : k_pass1_range<K, false, false>);
+        cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk, P1_BLOCK, rsmem);
+        if (per_sm < 1) per_sm = 1;
+        const uint64_t need = (tiles + P1_WARPS - 1) / P1_WARPS, cap = (uint64_t)c.sms * per_sm;
+        rk<<<(int)(need < cap ? (need ? need : 1) : cap), P1_BLOCK, rsmem, c.stream>>>(
+            P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask, cand, cand_count, cand_cap, firsts,
+            first_count, first_cap, hist, hist_passes, part_bits, part_lo, part_hi, bg, t_begin, t_end, err);
+        return;
+    }
     const int mode = (n_libs ? P1_BATCHED : 0) | (part_bits ? P1_PARTED : 0) | (by_bucket ? P1_BY_BUCKET : 0);
     auto kern = pass1_kernel<K>(use_filter, emit_firsts, mode);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
