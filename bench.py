@@ -40,7 +40,10 @@ HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/s
 # fly-shaped library at 1/10 scale (profiles/); scaled to a full launch by the units it processes.
 # A kernel is left out (traffic null) until it has been captured again after a change.
 NCU_BYTES_PER_UNIT = {"k_pass1": 98.95, "k_onesweep": 16.16, "k_bucket_count": 8.66, "k_hash_insert": 221.8}
-NCU_BYTES_PER_UNIT_U128 = {}  # long-k (k = 64): filled from its own captures
+# long-k (k = 64, 128-bit keys, four key ranges), from a capture at 1/50 scale whose ranges have the full-size
+# 1 GiB filter (profiles/k_pass1_range_longk_scale0.02.md): k_pass1_range per library window per launch (every
+# launch tests every window for its range), k_bucket_count per key of its range (the range's keys taken as W/4)
+NCU_BYTES_PER_UNIT_U128 = {"k_pass1_range": 17.46, "k_bucket_count": 17.09}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -425,12 +428,17 @@ def roofline_of(lib, prm, st, avg, args):
                                     if hashed else stage_bytes(dom, st, lib, bucketed))
     ach = total_bytes / (avg[dom] / 1e3) / 1e9  # = bytes per launch / average launch time
     kern = kernels[dom]
+    if kern == "k_pass1" and st["super_partitions"] > 1 and not lazy:
+        kern = "k_pass1_range"  # one key range per launch: the compacting form of pass 1
     table = NCU_BYTES_PER_UNIT if lib.k <= 32 else NCU_BYTES_PER_UNIT_U128
     # per-unit DRAM bytes were captured on the fly-shaped (k = 31) and long-k (k = 64) libraries at
     # default parameters only
     per_unit = (table.get(kern) if lib.name in ("fly", "longk") and (bucketed or hashed) and not lazy
                 and args.filter_bits <= 0 and args.scale == 1.0 and not args.budget_mib else None)
-    traffic = per_unit * units / n_launch if per_unit else None
+    if per_unit and kern == "k_pass1_range":
+        traffic = per_unit * st["n_windows"]  # every range's launch tests every window
+    else:
+        traffic = per_unit * units / n_launch if per_unit else None
     return {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
             "bytes_per_launch": total_bytes / n_launch, "launches_per_step": n_launch,

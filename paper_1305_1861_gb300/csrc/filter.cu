@@ -316,28 +316,67 @@ template void launch_cturtle<Key128>(const LaunchCfg &, const PackLayout &, int,
                                      const FilterGeom &, uint64_t, Key128 *, unsigned long long *, uint64_t,
                                      uint32_t *);
 
-// Number of valid windows in each of the 2^part_bits key-range parts (sizes the super-partitions).
+// Part (of 2^part_bits) of the canonical key of the window at s, exactly as key_part of that key. The top 31
+// bits of the canonical key are the smaller of the top 31 bits of the forward encoding and of the reverse
+// complement (if those differ, the smaller belongs to the smaller key; if equal, both keys share them); for
+// 128-bit keys they come from the window's first 32 bases and its last 32 bases, without building the keys.
+template <class K>
+__device__ __forceinline__ uint32_t window_part(const uint64_t *__restrict__ P, uint64_t s, int k, int part_bits);
+template <>
+__device__ __forceinline__ uint32_t window_part<uint64_t>(const uint64_t *__restrict__ P, uint64_t s, int k,
+                                                          int part_bits) {
+    return key_part(canonical_at(P, s, k), k, part_bits);
+}
+template <>
+__device__ __forceinline__ uint32_t window_part<Key128>(const uint64_t *__restrict__ P, uint64_t s, int k,
+                                                        int part_bits) {
+    const uint64_t e = s + (uint64_t)k - 32;  // k >= 33: the window's last 32 bases start at e >= s
+    const uint64_t a = stream_bits(__ldg(P + (s >> 5)), __ldg(P + (s >> 5) + 1), (int)(s & 31) << 1);
+    const uint64_t b = stream_bits(__ldg(P + (e >> 5)), __ldg(P + (e >> 5) + 1), (int)(e & 31) << 1);
+    const uint64_t vf = a >> 33, vr = (~rev2(b)) >> 33;  // top 31 bits of forward / reverse complement
+    const uint64_t v = vf < vr ? vf : vr;
+    return (uint32_t)((v * ((1ull << 32) - v)) >> (62 - part_bits));
+}
+
+// Number of valid windows in each of the 2^part_bits key-range parts (sizes the super-partitions and the
+// shards). Warp tiles of 128 positions read their two validity words once; the part comes from the exact
+// end-bases test of window_part (no full 128-bit key is built); each warp counts into its own shared
+// histogram, so lanes of different warps never contend for a bin.
 template <class K>
 __global__ void __launch_bounds__(256) k_part_count(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
                                                     uint64_t n_pos, int k, int part_bits,
                                                     unsigned long long *counts) {
-    extern __shared__ uint32_t s_cnt[];
+    extern __shared__ uint32_t s_cnt[];  // 8 warps x 2^part_bits
     const int nparts = 1 << part_bits;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s_cnt[i] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * nparts; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
-    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_pos; s += (uint64_t)gridDim.x * blockDim.x)
-        if ((V[s >> 6] >> (s & 63)) & 1) atomicAdd(&s_cnt[key_part(canonical<K>(P, s, k), k, part_bits)], 1u);
+    uint32_t *mine = s_cnt + warp * nparts;
+    const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
+    for (uint64_t t = (uint64_t)blockIdx.x * 8 + warp; t < tiles; t += (uint64_t)gridDim.x * 8) {
+        const uint64_t base = t * P1_TILE;
+        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const int r = lane + WARP * i;
+            const uint64_t s = base + r;
+            if (s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1)) atomicAdd(&mine[window_part<K>(P, s, k, part_bits)], 1u);
+        }
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
-        if (s_cnt[i]) atomicAdd(&counts[i], (unsigned long long)s_cnt[i]);
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        uint32_t c = 0;
+        for (int w = 0; w < 8; w++) c += s_cnt[w * nparts + i];
+        if (c) atomicAdd(&counts[i], (unsigned long long)c);
+    }
 }
 
 template <class K>
 void launch_part_count(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                        int part_bits, unsigned long long *counts) {
-    uint64_t need = (L.n_bases + 255) / 256;
-    const uint64_t cap = (uint64_t)c.sms * 8;
-    k_part_count<K><<<(int)(need < cap ? (need ? need : 1) : cap), 256, 4u << part_bits, c.stream>>>(
+    const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
+    const uint64_t need = (tiles + 7) / 8, cap = (uint64_t)c.sms * 8;
+    k_part_count<K><<<(int)(need < cap ? (need ? need : 1) : cap), 256, 32u << part_bits, c.stream>>>(
         P, V, L.n_bases, k, part_bits, counts);
 }
 template void launch_part_count<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
@@ -374,24 +413,6 @@ __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys,
 // those come from the window's first 32 bases and from its last 32 bases, without building either
 // full key; the probe phase checks every key against the range once more.
 constexpr int PQ_CAP = 2 * P1_TILE;  // queue of in-range positions per warp: one tile's worth beyond a full batch
-
-template <class K>
-__device__ __forceinline__ uint32_t window_part(const uint64_t *__restrict__ P, uint64_t s, int k, int part_bits);
-template <>
-__device__ __forceinline__ uint32_t window_part<uint64_t>(const uint64_t *__restrict__ P, uint64_t s, int k,
-                                                          int part_bits) {
-    return key_part(canonical_at(P, s, k), k, part_bits);
-}
-template <>
-__device__ __forceinline__ uint32_t window_part<Key128>(const uint64_t *__restrict__ P, uint64_t s, int k,
-                                                        int part_bits) {
-    const uint64_t e = s + (uint64_t)k - 32;  // k >= 33: the window's last 32 bases start at e >= s
-    const uint64_t a = stream_bits(__ldg(P + (s >> 5)), __ldg(P + (s >> 5) + 1), (int)(s & 31) << 1);
-    const uint64_t b = stream_bits(__ldg(P + (e >> 5)), __ldg(P + (e >> 5) + 1), (int)(e & 31) << 1);
-    const uint64_t vf = a >> 33, vr = (~rev2(b)) >> 33;  // top 31 bits of forward / reverse complement
-    const uint64_t v = vf < vr ? vf : vr;
-    return (uint32_t)((v * ((1ull << 32) - v)) >> (62 - part_bits));
-}
 
 template <class K, bool EMIT_FIRSTS, bool BY_BUCKET>
 __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
