@@ -140,6 +140,13 @@ typedef struct {
     uint32_t autotune;             /* turtle_count_batch: 1 = run each group of libraries (same k and min_count)
                                       with knobs chosen by turtle_autotune on its largest library (tuned once
                                       per class of input, then cached); 0 = as given */
+    uint32_t host_transfer;        /* host-memory calls: how the caller's reads and the result arrays move
+                                      between host and device. 0 = automatic: each context measures once how
+                                      fast a pageable copy runs against page-locking the memory first
+                                      (cudaHostRegister) and copying then, and takes the faster for the call's
+                                      sizes (on Grace the two differ from box to box by up to 20x);
+                                      1 = page-lock the caller's read arrays and the result arrays for the
+                                      duration of their copies; 2 = copy pageable memory directly. */
 } turtle_params;
 
 /* Fill *p with the defaults above. */

@@ -25,6 +25,7 @@
 #include <initializer_list>
 #include <chrono>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -106,6 +107,9 @@ struct turtle_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_packed[2] = {};
     cudaEvent_t ev_in[2] = {};  // host-memory calls: first byte of the reads queued, last byte landed
+    // host transfers, measured once per context: GB/s of a pageable copy, of page-locking (registering)
+    // host memory, and of a copy from registered memory (0 = not measured yet)
+    double gbs_pageable = 0, gbs_register = 0, gbs_registered = 0;
 };
 
 namespace {
@@ -228,7 +232,8 @@ bool params_ok(const turtle_params &p) {
            (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192) &&
            p.shard_count <= TURTLE_PARTS && p.shard_index < (p.shard_count ? p.shard_count : 1) &&
            !(p.shard_count > 1 && p.compact == 3) && p.probe_order <= 1 &&
-           (p.bucket_windows == 0 || (p.bucket_windows >= 1024 && p.bucket_windows <= (1u << 20)));
+           (p.bucket_windows == 0 || (p.bucket_windows >= 1024 && p.bucket_windows <= (1u << 20))) &&
+           p.host_transfer <= 2;
 }
 
 // Shard s of n takes the key-range parts [bounds[s], bounds[s+1]): bounds[s] is the first part at which
@@ -1354,6 +1359,72 @@ void result_release(void *p) {
     }
 }
 
+// Host transfers on Grace: the copy engines reach pageable memory through the CPU's page tables, and
+// on most boxes that runs as fast as page-locked memory (~200 GB/s); on some it runs at ~10 GB/s, and
+// page-locking the memory first (cudaHostRegister, milliseconds per GB) restores the full rate. Each
+// context measures the three rates once on 64 MiB and the host form then page-locks the caller's
+// arrays for a call only when that is predicted to be faster.
+void calibrate_transfers(turtle_ctx *c, cudaStream_t s) {
+    if (c->gbs_pageable > 0) return;
+    const size_t n = (size_t)64 << 20;
+    std::vector<unsigned char> host(n, 1);  // touched pageable memory
+    void *dev = nullptr;
+    c->gbs_pageable = 200.0;  // if anything below fails: assume the common fast case
+    c->gbs_register = c->gbs_registered = 0.0;
+    if (cudaMallocFromPoolAsync(&dev, n, c->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    using clk = std::chrono::steady_clock;
+    auto secs = [](clk::time_point t) { return std::chrono::duration<double>(clk::now() - t).count(); };
+    auto copy_gbs = [&]() {
+        double best = 1e30;
+        for (int r = 0; r < 2; r++) {
+            const clk::time_point t0 = clk::now();
+            if (cudaMemcpyAsync(dev, host.data(), n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return 0.0;
+            best = std::min(best, secs(t0));
+        }
+        return n / best / 1e9;
+    };
+    const double p = copy_gbs();
+    if (p > 0) c->gbs_pageable = p;
+    const clk::time_point t0 = clk::now();
+    if (cudaHostRegister(host.data(), n, cudaHostRegisterDefault) == cudaSuccess) {
+        c->gbs_register = n / std::max(secs(t0), 1e-9) / 1e9;
+        c->gbs_registered = copy_gbs();
+        cudaHostUnregister(host.data());
+    }
+    cudaFreeAsync(dev, s);
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+}
+
+// Page-lock a caller's host range for the duration of a transfer when the measured rates say it pays;
+// the destructor unlocks what this object locked (memory the caller had locked is left alone).
+struct HostLock {
+    void *base = nullptr;
+    explicit HostLock(turtle_ctx *c, const void *p, size_t bytes, uint32_t mode) {
+        if (!p || bytes < ((size_t)16 << 20) || mode == 2) return;
+        if (mode == 0) {
+            const double gb = bytes / 1e9;
+            if (!(c->gbs_register > 0 && c->gbs_registered > 0)) return;
+            const double direct = gb / c->gbs_pageable, locked = gb / c->gbs_register + gb / c->gbs_registered;
+            if (!(locked < 0.8 * direct)) return;
+        }
+        const size_t page = (size_t)sysconf(_SC_PAGESIZE);
+        const uintptr_t a = (uintptr_t)p & ~(uintptr_t)(page - 1);
+        const uintptr_t e = ((uintptr_t)p + bytes + page - 1) & ~(uintptr_t)(page - 1);
+        if (cudaHostRegister((void *)a, e - a, cudaHostRegisterDefault) == cudaSuccess) base = (void *)a;
+        else cudaGetLastError();  // already locked by the caller, or not lockable: copy as it is
+    }
+    ~HostLock() {
+        if (base) cudaHostUnregister(base);
+        cudaGetLastError();
+    }
+};
+
 // Into a host result buffer (first touched when fresh). Synchronises s.
 void copy_to_host(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s, bool fresh = true) {
     if (bytes) {
@@ -1580,6 +1651,14 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
     const uint64_t n_bases = lib_starts[n_libs], n_reads = entry_starts[n_libs];
     std::vector<unsigned long long> lib_windows(n_libs, 0);
     DeviceOut o;
+    if (prm.host_transfer == 0 && cudaSetDevice(c->device) == cudaSuccess) calibrate_transfers(c, s);
+    cudaGetLastError();
+    std::vector<std::unique_ptr<HostLock>> locks;  // the libraries' arrays, page-locked while they are copied
+    for (int l = 0; l < n_libs; l++) {
+        const turtle_job &j = jobs[idx[l]];
+        locks.emplace_back(new HostLock(c, j.bases + j.offsets[0], j.offsets[j.n_reads] - j.offsets[0], prm.host_transfer));
+        locks.emplace_back(new HostLock(c, j.offsets, 8 * (j.n_reads + 1), prm.host_transfer));
+    }
     try {
         ctx_begin(c, s);
         const LaunchCfg lc{c->sms, s};
@@ -1630,6 +1709,7 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         ctx_end(c, s);
         std::vector<size_t> lib_idx = idx;
         const int dev = c->device;
+        const uint32_t transfer = prm.host_transfer;
         cudaStream_t os = bo.stream();
         bo.post([=, &bo]() {
             const int kw = sizeof(K) / 8;
@@ -1649,8 +1729,11 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
                 }
                 if (r.n) {
                     try {
-                        copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os, fk);
-                        copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, os, fc);
+                        if (fk) first_touch(r.keys, 8 * kw * r.n);
+                        if (fc) first_touch(r.counts, 4 * r.n);
+                        const HostLock lk(c, r.keys, 8 * kw * r.n, transfer), lc(c, r.counts, 4 * r.n, transfer);
+                        copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os, false);
+                        copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, os, false);
                     } catch (Fail f) {
                         rc = f.code;
                     }
@@ -2036,6 +2119,14 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     }
     uint8_t *d_bases = nullptr;
     uint64_t *d_off = nullptr;
+    if (cudaSetDevice(c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return TURTLE_E_CUDA;
+    }
+    if (prm.host_transfer == 0) calibrate_transfers(c, s);
+    // the caller's arrays, page-locked for this call when that is faster (see calibrate_transfers)
+    const HostLock lock_bases(c, reads->bases, n_bases, prm.host_transfer);
+    const HostLock lock_offsets(c, reads->offsets, 8 * (reads->n_reads + 1), prm.host_transfer);
     try {
         ck(cudaSetDevice(c->device));
         if (!streamed) ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
@@ -2092,8 +2183,12 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         if (fc && count_bytes) first_touch(out->counts, count_bytes);
         host_ms[TURTLE_HOST_TOUCH] = ms_since(t_touch);
         const clk::time_point t_out = clk::now();
-        copy_to_host(c, out->keys, o.keys, key_bytes, s, false);
-        if (o.counts) copy_to_host(c, out->counts, o.counts, count_bytes, s, false);
+        {
+            const HostLock lock_keys(c, out->keys, key_bytes, prm.host_transfer);
+            const HostLock lock_counts(c, out->counts, count_bytes, prm.host_transfer);
+            copy_to_host(c, out->keys, o.keys, key_bytes, s, false);
+            if (o.counts) copy_to_host(c, out->counts, o.counts, count_bytes, s, false);
+        }
         host_ms[TURTLE_HOST_OUTPUT] = ms_since(t_out);
     } catch (Fail f) {
         cudaGetLastError();

@@ -337,3 +337,22 @@ def test_count_with_probes_ordered_by_filter_block(ctx, k, budget):
     reads = ["A" * 100] * 1200 + ["ACGT" * 25] * 3  # one key fills one bin
     bases, offs = brute.pack(reads)
     _check_count(ctx, bases, offs, k, 2, pkg.Params.default(probe_order=1))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_host_transfer_modes(have_gpu, mode):
+    """Host arrays copied directly (2), page-locked for their copies (1) or as the context's measured
+    rates decide (0): the same results, in the single-library, overlapped-copy and batched forms."""
+    import paper_1305_1861_gb300 as pkg
+
+    p = pkg.Params.default(host_transfer=mode)
+    lib = synth.fly(seed=12, scale=0.034)  # ~100 Mbase: the copy overlaps pass 1
+    keys, counts, nw = pkg.turtle_count(lib.bases, lib.offsets, 31, 2, p)
+    ok, oc, onw = oracle.count(lib.bases, lib.offsets, 31, 2)
+    assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+    specs = synth.batched_specs(seed=4, n_libs=6, scale=0.05)
+    libs = [synth.library_from_spec(sp) for sp in specs]
+    jobs = [(l.bases, l.offsets, l.k, l.min_count) for l in libs]
+    for (b, o, k, m), (keys, counts, nw) in zip(jobs, pkg.turtle_count_batch(jobs, p)):
+        ok, oc, onw = oracle.count(b, o, k, m)
+        assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
