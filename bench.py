@@ -391,7 +391,7 @@ def time_e2e(pkg, lib, prm, steps, W_all, world=1, dev=0):
     keys_n = len(counts)
     del keys, counts
     phases = {p: [] for p in pkg.HOST_PHASES}
-    h2d = []
+    h2d, locked = [], 0
     t0 = time.perf_counter()
     for _ in range(steps):
         keys, counts, nw = ctx.turtle_count(lib.bases, lib.offsets, lib.k, lib.min_count, prm_e2e)
@@ -401,6 +401,7 @@ def time_e2e(pkg, lib, prm, steps, W_all, world=1, dev=0):
         for p in pkg.HOST_PHASES:
             phases[p].append(st["host_ms"][p])
         h2d.append(st["h2d_ms"])
+        locked += st["host_locked"]
     e2e_s = (time.perf_counter() - t0) / steps
     ctx.close()
     torch.cuda.empty_cache()
@@ -411,6 +412,7 @@ def time_e2e(pkg, lib, prm, steps, W_all, world=1, dev=0):
             "host": "pageable NumPy arrays (the caller's own memory), turtle_ctx_count",
             "stages_ms": {p: round(float(np.mean(v)), 3) for p, v in phases.items()},
             "h2d_copy_span_ms": round(float(np.mean(h2d)), 3),
+            "transfer_gbs_measured": st["transfer_gbs"], "calls_page_locked": locked,
             "stages_note": "input: device buffers + offsets copy + queueing the reads' copy; path: device path until "
                            "the result is in HBM (an overlapped or streamed copy of the reads runs inside it); "
                            "touch: first touch of fresh host result pages; output: result copy to host"}

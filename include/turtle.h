@@ -292,6 +292,11 @@ typedef struct {
     uint64_t h2d_bytes, d2h_bytes;              /* host-memory calls: bytes copied in and out */
     uint32_t chunks;                            /* lazy form (compact = 3): read chunks merged into the
                                                    running set (0 in the other forms) */
+    uint32_t host_locked;                       /* host-memory calls: 1 if the call page-locked the caller's
+                                                   reads for their copy (params.host_transfer) */
+    float transfer_gbs[3];                      /* this context's measured host transfer rates (GB/s): pageable
+                                                   copy, page-locking, copy from page-locked memory (0 = not
+                                                   measured) */
     uint32_t pad_;
 } turtle_stats;
 

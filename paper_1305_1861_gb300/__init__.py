@@ -86,10 +86,13 @@ class Stats(ctypes.Structure):
                 ("filter_bytes", u64), ("table_bytes", u64), ("scratch_bytes", u64), ("sort_passes", u32),
                 ("super_partitions", u32), ("launches", u32), ("stage_launches", u32 * 10), ("stage_ms", ctypes.c_float * 10),
                 ("host_ms", ctypes.c_float * 4), ("h2d_ms", ctypes.c_float), ("h2d_bytes", u64), ("d2h_bytes", u64),
-                ("chunks", u32), ("pad_", u32)]
+                ("chunks", u32), ("host_locked", u32), ("transfer_gbs", ctypes.c_float * 3), ("pad_", u32)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_launches", "stage_ms", "host_ms", "pad_")}
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("stage_launches", "stage_ms", "host_ms", "pad_", "transfer_gbs")}
+        d["transfer_gbs"] = {n: round(float(self.transfer_gbs[i]), 1)
+                             for i, n in enumerate(("pageable", "page_locking", "page_locked_copy"))}
         d["stage_launches"] = {STAGES[i]: int(self.stage_launches[i]) for i in range(len(STAGES))}
         d["stage_ms"] = {STAGES[i]: float(self.stage_ms[i]) for i in range(len(STAGES))}
         d["host_ms"] = {HOST_PHASES[i]: float(self.host_ms[i]) for i in range(4)}

@@ -2207,6 +2207,10 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     c->stats.h2d_ms = h2d;
     c->stats.h2d_bytes = n_bases + 8 * (reads->n_reads + 1);
     c->stats.d2h_bytes = key_bytes + count_bytes;
+    c->stats.host_locked = lock_bases.base ? 1u : 0u;
+    c->stats.transfer_gbs[0] = (float)c->gbs_pageable;
+    c->stats.transfer_gbs[1] = (float)c->gbs_register;
+    c->stats.transfer_gbs[2] = (float)c->gbs_registered;
     return TURTLE_OK;
 }
 
