@@ -82,6 +82,8 @@ def parse():
                          "3 = lazy sort-and-compact phases (memory-capped, chunked)")
     ap.add_argument("--budget-mib", type=int, default=0, help="device-memory budget per key range (0 = automatic)")
     ap.add_argument("--pattern-bits", type=int, default=0, help="Bloom pattern bits (0 = library default)")
+    ap.add_argument("--host-transfer", type=int, default=-1,
+                    help="host copies: 0 = measured choice, 1 = page-lock the arrays, 2 = pageable (-1 = default)")
     ap.add_argument("--probe-order", type=int, default=-1,
                     help="pass 1 probes: 0 = in window order, 1 = by filter block (binned) (-1 = default)")
     ap.add_argument("--micro", action="store_true",
@@ -331,6 +333,8 @@ def make_params(pkg, args, **kw):
         prm.pattern_bits = args.pattern_bits
     if args.probe_order >= 0:
         prm.probe_order = args.probe_order
+    if args.host_transfer >= 0:
+        prm.host_transfer = args.host_transfer
     return prm
 
 

@@ -1273,15 +1273,12 @@ int count_device_impl(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, con
     }
 }
 
-// Host <-> device copies go straight from and to host memory, pageable or not: on a Grace-based
-// GPU the copy engines reach pageable memory through the CPU's page tables at about the rate of
-// page-locked memory (~200 GB/s over NVLink-C2C), faster than staging through a page-locked
-// buffer with host copies. Host pages that do not exist yet are the exception: the copy engine
-// would fault each one in, an order of magnitude slower, so a result buffer is first touched
-// page by page from several host threads.
-void copy_to_device(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s) {
-    if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
-}
+// Host <-> device copies go straight from and to the caller's memory: on a Grace-based GPU the copy
+// engines reach pageable memory through the CPU's page tables, on most boxes at about the rate of
+// page-locked memory (~200 GB/s over NVLink-C2C), faster than staging through a page-locked buffer
+// with host copies; where they do not, the memory is page-locked for the copy (HostLocks below).
+// Host pages that do not exist yet are the exception: the copy engine would fault each one in, an
+// order of magnitude slower, so a result buffer is first touched page by page from several threads.
 
 void first_touch(void *p, size_t bytes) {
     const size_t page = (size_t)sysconf(_SC_PAGESIZE);
@@ -1401,35 +1398,82 @@ void calibrate_transfers(turtle_ctx *c, cudaStream_t s) {
     cudaGetLastError();
 }
 
-// Page-lock a caller's host range for the duration of a transfer when the measured rates say it pays;
-// the destructor unlocks what this object locked (memory the caller had locked is left alone).
-struct HostLock {
-    void *base = nullptr;
-    explicit HostLock(turtle_ctx *c, const void *p, size_t bytes, uint32_t mode) {
-        if (!p || bytes < ((size_t)16 << 20) || mode == 2) return;
-        if (mode == 0) {
-            const double gb = bytes / 1e9;
-            if (!(c->gbs_register > 0 && c->gbs_registered > 0)) return;
-            const double direct = gb / c->gbs_pageable, locked = gb / c->gbs_register + gb / c->gbs_registered;
-            if (!(locked < 0.8 * direct)) return;
-        }
-        const size_t page = (size_t)sysconf(_SC_PAGESIZE);
-        const uintptr_t a = (uintptr_t)p & ~(uintptr_t)(page - 1);
-        const uintptr_t e = ((uintptr_t)p + bytes + page - 1) & ~(uintptr_t)(page - 1);
-        if (cudaHostRegister((void *)a, e - a, cudaHostRegisterDefault) == cudaSuccess) base = (void *)a;
-        else cudaGetLastError();  // already locked by the caller, or not lockable: copy as it is
-    }
-    ~HostLock() {
-        if (base) cudaHostUnregister(base);
+// Page-locked parts of a call's host arrays. Only the whole pages inside an array are locked: a page at
+// either end may be shared with another allocation (another array of the call, or memory of the caller's
+// that is locked already), and locking it twice, or copying a range that starts inside one locked range
+// and runs past its end, is an error. Copies therefore go through copy(), which splits them at the locked
+// ranges' bounds so that every piece lies wholly inside or wholly outside one locked range. The
+// destructor unlocks everything this object locked.
+class HostLocks {
+public:
+    HostLocks(turtle_ctx *c, uint32_t mode) : c_(c), mode_(mode) {}
+    HostLocks(const HostLocks &) = delete;
+    HostLocks &operator=(const HostLocks &) = delete;
+    ~HostLocks() {
+        for (auto &r : ranges_) cudaHostUnregister((void *)r.first);
         cudaGetLastError();
     }
+    // Lock [p, p + bytes) (its whole pages) when that is predicted to be faster for a copy of this size
+    // (mode 0: the context's measured rates), always (mode 1) or never (mode 2). Arrays below 16 MiB are
+    // copied as they are.
+    void add(const void *p, size_t bytes) {
+        if (!p || bytes < ((size_t)16 << 20) || mode_ == 2) return;
+        if (mode_ == 0) {
+            const double gb = bytes / 1e9;
+            if (!(c_->gbs_register > 0 && c_->gbs_registered > 0)) return;
+            const double direct = gb / c_->gbs_pageable, locked = gb / c_->gbs_register + gb / c_->gbs_registered;
+            if (!(locked < 0.8 * direct)) return;
+        }
+        const uintptr_t page = (uintptr_t)sysconf(_SC_PAGESIZE);
+        const uintptr_t a = ((uintptr_t)p + page - 1) & ~(page - 1);
+        const uintptr_t e = ((uintptr_t)p + bytes) & ~(page - 1);
+        if (e <= a) return;
+        for (auto &r : ranges_)
+            if (a < r.second && r.first < e) return;  // cannot happen for distinct arrays; keep ranges disjoint
+        if (cudaHostRegister((void *)a, e - a, cudaHostRegisterDefault) != cudaSuccess) {
+            cudaGetLastError();  // e.g. the caller locked it already: copied as it is
+            return;
+        }
+        ranges_.insert(std::upper_bound(ranges_.begin(), ranges_.end(), std::make_pair(a, e)), std::make_pair(a, e));
+    }
+    bool locked(const void *p) const {
+        for (auto &r : ranges_)
+            if ((uintptr_t)p >= r.first && (uintptr_t)p < r.second) return true;
+        return false;
+    }
+    // cudaMemcpyAsync of n bytes between host and device (kind H2D: src is host; D2H: dst is host), split at
+    // the locked ranges' bounds.
+    void copy(void *dst, const void *src, size_t n, cudaMemcpyKind kind, cudaStream_t s) const {
+        const bool h2d = kind == cudaMemcpyHostToDevice;
+        const uintptr_t h0 = (uintptr_t)(h2d ? src : dst), h1 = h0 + n;
+        uintptr_t pos = h0;
+        auto piece = [&](uintptr_t x, uintptr_t y) {
+            if (y <= x) return;
+            const size_t off = x - h0;
+            if (h2d) ck(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, y - x, kind, s));
+            else ck(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, y - x, kind, s));
+        };
+        for (auto &r : ranges_) {
+            if (r.second <= pos || r.first >= h1) continue;
+            piece(pos, std::min(h1, r.first));
+            piece(std::max(pos, r.first), std::min(h1, r.second));
+            pos = std::min(h1, r.second);
+        }
+        piece(pos, h1);
+    }
+
+private:
+    turtle_ctx *c_;
+    uint32_t mode_;
+    std::vector<std::pair<uintptr_t, uintptr_t>> ranges_;  // locked [first, second), ascending, disjoint
 };
 
-// Into a host result buffer (first touched when fresh). Synchronises s.
-void copy_to_host(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaStream_t s, bool fresh = true) {
+// Into a host result buffer (first touched when fresh), split at the locked ranges of `locks`.
+// Synchronises s.
+void copy_to_host(const HostLocks &locks, void *dst, const void *src, size_t bytes, cudaStream_t s, bool fresh) {
     if (bytes) {
         if (fresh) first_touch(dst, bytes);
-        ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        locks.copy(dst, src, bytes, cudaMemcpyDeviceToHost, s);
     }
     ck(cudaStreamSynchronize(s));
 }
@@ -1438,7 +1482,7 @@ void copy_to_host(turtle_ctx *, void *dst, const void *src, size_t bytes, cudaSt
 // while chunk i-1 is packed on `s` (two device staging buffers). Only the 2-bit codes and bitmaps
 // stay on the device; the ASCII is never resident as a whole.
 void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off,
-                   size_t chunk, cudaStream_t s, PrePacked &pp, const LaunchCfg &lc) {
+                   size_t chunk, cudaStream_t s, PrePacked &pp, const LaunchCfg &lc, const HostLocks &locks) {
     const PackLayout L = PackLayout::of(n_bases);
     pp.P = (uint64_t *)ctx_alloc(c, 8 * L.p_words, s);
     pp.B = (uint64_t *)ctx_alloc(c, 8 * L.b_words, s);
@@ -1453,7 +1497,7 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
         const int b = (int)(i & 1);
         const uint64_t c0 = i * chunk, c1 = c0 + chunk < n_bases ? c0 + chunk : n_bases;
         ck(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0));  // its staging buffer was packed
-        ck(cudaMemcpyAsync(stage[b], reads->bases + c0, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream));
+        locks.copy(stage[b], reads->bases + c0, c1 - c0, cudaMemcpyHostToDevice, c->copy_stream);
         ck(cudaEventRecord(c->ev_h2d[b], c->copy_stream));
         ck(cudaStreamWaitEvent(s, c->ev_h2d[b], 0));
         const uint64_t g0 = c0 / 32, g1 = i + 1 == n_chunks ? L.pack_groups() : c1 / 32;
@@ -1468,7 +1512,7 @@ void pack_streamed(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, c
 // Host-memory input streamed through two device staging buffers, then the path on the packed reads.
 int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bases, const uint64_t *d_off, int k,
                         uint32_t min_count, const turtle_params *params, size_t chunk, cudaStream_t s,
-                        DeviceOut &o, bool cturtle = false) {
+                        DeviceOut &o, const HostLocks &locks, bool cturtle = false) {
     const turtle_params prm = resolve(params);
     if (!params_ok(prm)) return TURTLE_E_ARG;
     try {
@@ -1476,7 +1520,7 @@ int count_streamed_impl(turtle_ctx *c, const turtle_reads *reads, uint64_t n_bas
         L2Fetch l2(prm.l2_fetch_bytes);
         const LaunchCfg lc{c->sms, s};
         PrePacked pp{};
-        pack_streamed(c, reads, n_bases, d_off, chunk, s, pp, lc);
+        pack_streamed(c, reads, n_bases, d_off, chunk, s, pp, lc, locks);
         if (k <= 32)
             run_count<uint64_t>(c, nullptr, n_bases, d_off, reads->n_reads, k, min_count, prm, s, o, &pp, nullptr,
                                 cturtle);
@@ -1512,8 +1556,8 @@ struct HostPiece {  // bases [start, start + len) of the concatenated positions 
 template <class K>
 void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, uint64_t n_bases, uint64_t n_reads,
                           uint8_t *d_bases, const uint64_t *d_off, int k, uint32_t min_count,
-                          const turtle_params &prm, cudaStream_t s, DeviceOut &out, const BatchTag *tag = nullptr,
-                          const std::vector<unsigned long long> *lib_w_est = nullptr) {
+                          const turtle_params &prm, cudaStream_t s, DeviceOut &out, const HostLocks &locks,
+                          const BatchTag *tag = nullptr, const std::vector<unsigned long long> *lib_w_est = nullptr) {
     const LaunchCfg lc{c->sms, s};
     turtle_stats st{};
     Timer tm{c, s, prm.timing != 0};
@@ -1576,8 +1620,8 @@ void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, u
         for (size_t q = pi; q < pieces.size() && pieces[q].start < c1; q++) {
             const uint64_t a = std::max(c0, pieces[q].start), b = std::min(c1, pieces[q].start + pieces[q].len);
             if (b > a)
-                ck(cudaMemcpyAsync(d_bases + a, pieces[q].src + (a - pieces[q].start), b - a, cudaMemcpyHostToDevice,
-                                   c->copy_stream));
+                locks.copy(d_bases + a, pieces[q].src + (a - pieces[q].start), b - a, cudaMemcpyHostToDevice,
+                           c->copy_stream);
         }
         ck(cudaEventRecord(c->ev_h2d[0], c->copy_stream));
         ck(cudaStreamWaitEvent(s, c->ev_h2d[0], 0));
@@ -1653,11 +1697,11 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
     DeviceOut o;
     if (prm.host_transfer == 0 && cudaSetDevice(c->device) == cudaSuccess) calibrate_transfers(c, s);
     cudaGetLastError();
-    std::vector<std::unique_ptr<HostLock>> locks;  // the libraries' arrays, page-locked while they are copied
+    HostLocks locks(c, prm.host_transfer);  // the libraries' arrays, page-locked while they are copied
     for (int l = 0; l < n_libs; l++) {
         const turtle_job &j = jobs[idx[l]];
-        locks.emplace_back(new HostLock(c, j.bases + j.offsets[0], j.offsets[j.n_reads] - j.offsets[0], prm.host_transfer));
-        locks.emplace_back(new HostLock(c, j.offsets, 8 * (j.n_reads + 1), prm.host_transfer));
+        locks.add(j.bases + j.offsets[0], j.offsets[j.n_reads] - j.offsets[0]);
+        locks.add(j.offsets, 8 * (j.n_reads + 1));
     }
     try {
         ctx_begin(c, s);
@@ -1677,8 +1721,8 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
             const uint64_t lost = j.n_reads * (uint64_t)(k - 1);
             w_est[l] = std::max<uint64_t>(nb > lost ? nb - lost : 0, nb / 4);
             if (overlapped) pieces.push_back(HostPiece{lib_starts[l], nb, j.bases + j.offsets[0]});
-            else copy_to_device(c, d_bases + lib_starts[l], j.bases + j.offsets[0], nb, s);
-            copy_to_device(c, d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), s);
+            else if (nb) locks.copy(d_bases + lib_starts[l], j.bases + j.offsets[0], nb, cudaMemcpyHostToDevice, s);
+            locks.copy(d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), cudaMemcpyHostToDevice, s);
         }
         ck(cudaMemcpyAsync(d_tab, lib_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
         ck(cudaMemcpyAsync(d_tab + n_libs + 1, entry_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
@@ -1686,7 +1730,8 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         BatchTag tag{d_tab, n_libs, tag_bits, d_lw};
         L2Fetch l2(prm.l2_fetch_bytes);
         if (overlapped)
-            run_count_overlapped<K>(c, pieces, n_bases, n_reads, d_bases, d_off, k, min_count, prm, s, o, &tag, &w_est);
+            run_count_overlapped<K>(c, pieces, n_bases, n_reads, d_bases, d_off, k, min_count, prm, s, o, locks, &tag,
+                                    &w_est);
         else run_count<K>(c, d_bases, n_bases, d_off, n_reads, k, min_count, prm, s, o, nullptr, &tag);
         // split on the device: library boundaries + tag bits cleared, then one copy per library
         std::vector<uint64_t> starts(n_libs + 1, ~0ull);
@@ -1731,9 +1776,11 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
                     try {
                         if (fk) first_touch(r.keys, 8 * kw * r.n);
                         if (fc) first_touch(r.counts, 4 * r.n);
-                        const HostLock lk(c, r.keys, 8 * kw * r.n, transfer), lc(c, r.counts, 4 * r.n, transfer);
-                        copy_to_host(c, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os, false);
-                        copy_to_host(c, r.counts, o.counts + starts[l], 4 * r.n, os, false);
+                        HostLocks rl(c, transfer);
+                        rl.add(r.keys, 8 * kw * r.n);
+                        rl.add(r.counts, 4 * r.n);
+                        copy_to_host(rl, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os, false);
+                        copy_to_host(rl, r.counts, o.counts + starts[l], 4 * r.n, os, false);
                     } catch (Fail f) {
                         rc = f.code;
                     }
@@ -2125,16 +2172,16 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     }
     if (prm.host_transfer == 0) calibrate_transfers(c, s);
     // the caller's arrays, page-locked for this call when that is faster (see calibrate_transfers)
-    const HostLock lock_bases(c, reads->bases, n_bases, prm.host_transfer);
-    const HostLock lock_offsets(c, reads->offsets, 8 * (reads->n_reads + 1), prm.host_transfer);
+    HostLocks locks(c, prm.host_transfer);
+    locks.add(reads->bases, n_bases);
+    locks.add(reads->offsets, 8 * (reads->n_reads + 1));
     try {
         ck(cudaSetDevice(c->device));
         if (!streamed) ck(cudaMallocFromPoolAsync((void **)&d_bases, n_bases ? n_bases : 16, c->pool, s));
         ck(cudaMallocFromPoolAsync((void **)&d_off, 8 * (reads->n_reads + 1), c->pool, s));
         ck(cudaEventRecord(c->ev_in[0], s));  // the input copies start here
-        copy_to_device(c, d_off, reads->offsets, 8 * (reads->n_reads + 1), s);
-        if (n_bases && !streamed && !overlapped)
-            ck(cudaMemcpyAsync(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s));
+        locks.copy(d_off, reads->offsets, 8 * (reads->n_reads + 1), cudaMemcpyHostToDevice, s);
+        if (n_bases && !streamed && !overlapped) locks.copy(d_bases, reads->bases, n_bases, cudaMemcpyHostToDevice, s);
         if (!streamed && !overlapped) ck(cudaEventRecord(c->ev_in[1], s));  // (streamed/overlapped: after the last chunk)
     } catch (Fail f) {
         if (d_bases) cudaFreeAsync(d_bases, s);
@@ -2151,8 +2198,9 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
             const std::vector<HostPiece> pieces{HostPiece{0, n_bases, reads->bases}};
             if (k <= 32)
                 run_count_overlapped<uint64_t>(c, pieces, n_bases, reads->n_reads, d_bases, d_off, k, min_count, prm, s,
-                                               o);
-            else run_count_overlapped<Key128>(c, pieces, n_bases, reads->n_reads, d_bases, d_off, k, min_count, prm, s, o);
+                                               o, locks);
+            else run_count_overlapped<Key128>(c, pieces, n_bases, reads->n_reads, d_bases, d_off, k, min_count, prm, s, o,
+                                              locks);
             ctx_end(c, s);
         } catch (Fail f) {
             rc = fail_code(s, c, f.code);
@@ -2160,7 +2208,7 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
             rc = fail_code(s, c, TURTLE_E_NOMEM);
         }
     } else if (streamed) {
-        rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o, cturtle);
+        rc = count_streamed_impl(c, reads, n_bases, d_off, k, min_count, params, chunk, s, o, locks, cturtle);
     } else {
         rc = count_device_impl(c, d_bases, n_bases, d_off, reads->n_reads, k, min_count, params, s, o, cturtle);
     }
@@ -2184,10 +2232,11 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
         host_ms[TURTLE_HOST_TOUCH] = ms_since(t_touch);
         const clk::time_point t_out = clk::now();
         {
-            const HostLock lock_keys(c, out->keys, key_bytes, prm.host_transfer);
-            const HostLock lock_counts(c, out->counts, count_bytes, prm.host_transfer);
-            copy_to_host(c, out->keys, o.keys, key_bytes, s, false);
-            if (o.counts) copy_to_host(c, out->counts, o.counts, count_bytes, s, false);
+            HostLocks rl(c, prm.host_transfer);
+            rl.add(out->keys, key_bytes);
+            rl.add(out->counts, count_bytes);
+            copy_to_host(rl, out->keys, o.keys, key_bytes, s, false);
+            if (o.counts) copy_to_host(rl, out->counts, o.counts, count_bytes, s, false);
         }
         host_ms[TURTLE_HOST_OUTPUT] = ms_since(t_out);
     } catch (Fail f) {
@@ -2207,7 +2256,7 @@ int count_host_impl(turtle_ctx *c, const turtle_reads *reads, int k, uint32_t mi
     c->stats.h2d_ms = h2d;
     c->stats.h2d_bytes = n_bases + 8 * (reads->n_reads + 1);
     c->stats.d2h_bytes = key_bytes + count_bytes;
-    c->stats.host_locked = lock_bases.base ? 1u : 0u;
+    c->stats.host_locked = locks.locked(reads->bases + n_bases / 2) ? 1u : 0u;
     c->stats.transfer_gbs[0] = (float)c->gbs_pageable;
     c->stats.transfer_gbs[1] = (float)c->gbs_register;
     c->stats.transfer_gbs[2] = (float)c->gbs_registered;
