@@ -140,13 +140,14 @@ typedef struct {
     uint32_t autotune;             /* turtle_count_batch: 1 = run each group of libraries (same k and min_count)
                                       with knobs chosen by turtle_autotune on its largest library (tuned once
                                       per class of input, then cached); 0 = as given */
-    uint32_t host_transfer;        /* host-memory calls: how the caller's reads and the result arrays move
-                                      between host and device. 0 = automatic: each context measures once how
-                                      fast a pageable copy runs against page-locking the memory first
-                                      (cudaHostRegister) and copying then, and takes the faster for the call's
-                                      sizes (on Grace the two differ from box to box by up to 20x);
-                                      1 = page-lock the caller's read arrays and the result arrays for the
-                                      duration of their copies; 2 = copy pageable memory directly. */
+    uint32_t host_transfer;        /* host-memory calls: how the caller's reads and the result arrays (those
+                                      of 16 MiB or more) move between host and device. 0 = automatic: each
+                                      context measures once how fast page-locking (cudaHostRegister) runs, and
+                                      when it costs little (100 GB/s or more, as on Grace) the arrays' whole
+                                      pages are page-locked for their copies: pageable copies of large arrays
+                                      vary from run to run and box to box (8 to 190 GB/s measured), locked ones
+                                      run at 170-210 GB/s; 1 = always page-lock them; 2 = copy pageable
+                                      memory directly. Memory the caller locked already is used as it is. */
 } turtle_params;
 
 /* Fill *p with the defaults above. */

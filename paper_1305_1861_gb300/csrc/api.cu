@@ -1356,11 +1356,13 @@ void result_release(void *p) {
     }
 }
 
-// Host transfers on Grace: the copy engines reach pageable memory through the CPU's page tables, and
-// on most boxes that runs as fast as page-locked memory (~200 GB/s); on some it runs at ~10 GB/s, and
-// page-locking the memory first (cudaHostRegister, milliseconds per GB) restores the full rate. Each
-// context measures the three rates once on 64 MiB and the host form then page-locks the caller's
-// arrays for a call only when that is predicted to be faster.
+// Host transfers on Grace: the copy engines reach pageable memory through the CPU's page tables. For
+// large arrays the rate of such copies varies from run to run and box to box (8 to 190 GB/s measured,
+// even on a box where a fresh 64 MiB buffer copies at 180 GB/s), while copies from page-locked memory
+// run at 170-210 GB/s and page-locking (cudaHostRegister) costs 2-3 ms per GB. So the host form
+// page-locks its large host arrays for their copies whenever locking is cheap; each context measures
+// the rates once on 64 MiB (reported in its statistics).
+constexpr double LOCK_MIN_GBS = 100.0;  // page-locking at least this fast: lock large arrays for copies
 void calibrate_transfers(turtle_ctx *c, cudaStream_t s) {
     if (c->gbs_pageable > 0) return;
     const size_t n = (size_t)64 << 20;
@@ -1413,17 +1415,12 @@ public:
         for (auto &r : ranges_) cudaHostUnregister((void *)r.first);
         cudaGetLastError();
     }
-    // Lock [p, p + bytes) (its whole pages) when that is predicted to be faster for a copy of this size
-    // (mode 0: the context's measured rates), always (mode 1) or never (mode 2). Arrays below 16 MiB are
-    // copied as they are.
+    // Lock [p, p + bytes) (its whole pages) when locking is cheap on this machine (mode 0: the context
+    // measured page-locking at LOCK_MIN_GBS or more), always (mode 1) or never (mode 2). Arrays below
+    // 16 MiB are copied as they are.
     void add(const void *p, size_t bytes) {
         if (!p || bytes < ((size_t)16 << 20) || mode_ == 2) return;
-        if (mode_ == 0) {
-            const double gb = bytes / 1e9;
-            if (!(c_->gbs_register > 0 && c_->gbs_registered > 0)) return;
-            const double direct = gb / c_->gbs_pageable, locked = gb / c_->gbs_register + gb / c_->gbs_registered;
-            if (!(locked < 0.8 * direct)) return;
-        }
+        if (mode_ == 0 && !(c_->gbs_register >= LOCK_MIN_GBS && c_->gbs_registered > 0)) return;
         const uintptr_t page = (uintptr_t)sysconf(_SC_PAGESIZE);
         const uintptr_t a = ((uintptr_t)p + page - 1) & ~(page - 1);
         const uintptr_t e = ((uintptr_t)p + bytes) & ~(page - 1);
