@@ -877,8 +877,11 @@ def run_blocks(args, out):
 
     import torch
 
+    import paper_1305_1861_gb300 as pkg
+
     blocks = [b for b in args.blocks.split(",") if b and b != "none"]
     for name in blocks:
+        pkg.turtle_trim()  # each block starts with the device memory earlier blocks' calls kept given back
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
         if name == "k64":

@@ -206,6 +206,12 @@ void turtle_result_free(turtle_result *r);
 /* Static description of an error code. */
 const char *turtle_strerror(int code);
 
+/* Give back what the library keeps between calls of its host-memory and batched forms: the device
+ * memory that the internal per-device contexts' pools hold unused, and the recycled host result
+ * arrays. Later calls allocate again as needed. Waits for those contexts' work. Contexts created
+ * with turtle_ctx_create are not touched (turtle_ctx_destroy releases theirs). */
+void turtle_trim(void);
+
 /* ------------------------------------------------------------------ contexts and the device form */
 /* A context owns device scratch (grown on demand, kept between calls), the
  * device result of its last call, an error word and timing events. */

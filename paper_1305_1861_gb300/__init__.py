@@ -15,7 +15,7 @@ import numpy as np
 
 __all__ = [
     "TurtleError", "Params", "Context", "Server", "load", "build", "turtle_count", "turtle_count_batch",
-    "turtle_strerror", "STAGES",
+    "turtle_strerror", "turtle_trim", "STAGES",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -128,6 +128,7 @@ def load():
         "turtle_tune_select": (ctypes.c_int, [_p, _p, _p, _p, _p]),
         "turtle_autotune": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p, _p]),
         "turtle_tune_cache_clear": (None, []),
+        "turtle_trim": (None, []),
         "turtle_ctx_count": (ctypes.c_int, [_p, _p, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_count_device": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p]),
         "turtle_frequent": (ctypes.c_int, [_p, ctypes.c_int, _p, _p, _p]),
@@ -150,6 +151,11 @@ def load():
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def turtle_trim():
+    """Give back the device memory the library's internal contexts keep unused, and recycled host results."""
+    load().turtle_trim()
 
 
 def turtle_strerror(code: int) -> str:

@@ -2336,6 +2336,28 @@ int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_param
     return rc;
 }
 
+void turtle_trim(void) {
+    {
+        std::lock_guard<std::mutex> g(g_default_mu);
+        for (turtle_ctx *c : g_default) {
+            if (!c) continue;
+            if (cudaSetDevice(c->device) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+            free_list(c->result, c->last_stream);  // the last device result of the host forms is never handed out
+            cudaDeviceSynchronize();
+            cudaMemPoolTrimTo(c->pool, 0);
+            cudaGetLastError();
+        }
+    }
+    std::lock_guard<std::mutex> g(g_rbuf_mu);
+    for (auto &kv : g_rbuf_idle) free(kv.second);
+    g_rbuf_idle.clear();
+    g_rbuf_idle_bytes = 0;
+}
+
 int turtle_count(const turtle_reads *reads, int k, uint32_t min_count, turtle_result *out) {
     return turtle_count_ex(reads, k, min_count, nullptr, nullptr, out);
 }

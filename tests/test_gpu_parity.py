@@ -356,3 +356,21 @@ def test_host_transfer_modes(have_gpu, mode):
     for (b, o, k, m), (keys, counts, nw) in zip(jobs, pkg.turtle_count_batch(jobs, p)):
         ok, oc, onw = oracle.count(b, o, k, m)
         assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+
+
+def test_trim_gives_back_cached_memory_and_calls_still_work(have_gpu):
+    import torch
+
+    import paper_1305_1861_gb300 as pkg
+
+    lib = synth.fly(seed=13, scale=0.034)
+    ok, oc, _ = oracle.count(lib.bases, lib.offsets, 31, 2)
+    keys, counts, _ = pkg.turtle_count(lib.bases, lib.offsets, 31, 2)
+    del keys, counts
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    pkg.turtle_trim()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after > free_before + (1 << 30)  # the internal context's pool held gigabytes between calls
+    keys, counts, _ = pkg.turtle_count(lib.bases, lib.offsets, 31, 2)
+    assert np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
