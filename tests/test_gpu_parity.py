@@ -371,6 +371,6 @@ def test_trim_gives_back_cached_memory_and_calls_still_work(have_gpu):
     free_before, _ = torch.cuda.mem_get_info()
     pkg.turtle_trim()
     free_after, _ = torch.cuda.mem_get_info()
-    assert free_after > free_before + (1 << 30)  # the internal context's pool held gigabytes between calls
+    assert free_after > free_before + (256 << 20)  # the internal context's pool held its scratch between calls
     keys, counts, _ = pkg.turtle_count(lib.bases, lib.offsets, 31, 2)
     assert np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
