@@ -880,13 +880,15 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         return;
     }
 
+    // the ambiguous-call and read-start bitmaps are only needed for the validity bitmap: give their
+    // memory back before the key-range budget is taken
+    ctx_free(c, B, s);
+    ctx_free(c, S, s);
     if (cturtle) {
         run_cturtle<K>(c, lc, tm, st, L, k, P, V, W, prm, s, out);
         return;
     }
-    if (prm.compact == 3 && !tag) {  // lazy sort-and-compact phases: the ambiguous-call and start bitmaps are done
-        ctx_free(c, B, s);
-        ctx_free(c, S, s);
+    if (prm.compact == 3 && !tag) {  // lazy sort-and-compact phases
         run_lazy<K>(c, lc, tm, st, L, k, min_count, P, V, W, prm, s, out);
         return;
     }
@@ -972,6 +974,19 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     }
     const bool parted = groups.size() > 1 || sharded;
     st.super_partitions = (uint32_t)groups.size();
+    // With two to four key ranges, one pass writes each window's range id (two bits per position) and
+    // each range's pass 1 selects its windows from those bits; with more, each pass 1 tests every window.
+    uint64_t *rid = nullptr;
+    if (groups.size() >= 2 && groups.size() <= 4 && use_filter) {
+        std::vector<uint8_t> pg(1u << PART_BITS, 0);
+        for (size_t g = 0; g < groups.size(); g++)
+            for (uint32_t p = groups[g].first; p < groups[g].second; p++) pg[p] = (uint8_t)g;
+        uint8_t *d_pg = (uint8_t *)ctx_alloc(c, pg.size(), s);
+        ck(cudaMemcpyAsync(d_pg, pg.data(), pg.size(), cudaMemcpyHostToDevice, s));
+        rid = (uint64_t *)ctx_alloc(c, 8 * range_id_words(n_bases), s);
+        launch_range_ids<K>(lc, L, k, P, V, PART_BITS, d_pg, rid);
+        st.stage_launches[TURTLE_STAGE_VALID] += 1;
+    }
 
     std::vector<PartOut> outs;
     for (size_t g = 0; g < groups.size(); g++) {
@@ -1028,7 +1043,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cand_cap, firsts, ctr + C_FIRST, Wg,
                             hist, hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
                             tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
-                            bucketed ? &bg : nullptr);
+                            bucketed ? &bg : nullptr, 0, ~0ull, rid, (uint32_t)g);
         }
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;

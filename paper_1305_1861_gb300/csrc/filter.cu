@@ -384,6 +384,59 @@ template void launch_part_count<uint64_t>(const LaunchCfg &, const PackLayout &,
 template void launch_part_count<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
                                         const uint64_t *, int, unsigned long long *);
 
+// Key range of every window, two bits per position (bits 2j+1..2j of word w for position 32w + j), for up
+// to four ranges: range id = group[part of the window's key]. Each range's pass 1 then selects its
+// windows from these words and the validity bitmap, without computing any other window's key.
+constexpr int MAX_PARTS = 64;  // key-range parts of a library (part_bits <= 6)
+
+__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {  // bit j of x -> bit 2j
+    uint64_t v = x;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_range_ids(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
+                                                   uint64_t n_pos, int k, int part_bits,
+                                                   const uint8_t *__restrict__ part_group, uint64_t *rid) {
+    __shared__ uint8_t s_pg[MAX_PARTS];
+    for (int i = threadIdx.x; i < (1 << part_bits); i += blockDim.x) s_pg[i] = part_group[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
+    for (uint64_t t = (uint64_t)blockIdx.x * 8 + warp; t < tiles; t += (uint64_t)gridDim.x * 8) {
+        const uint64_t base = t * P1_TILE;
+        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const int r = lane + WARP * i;
+            const uint64_t s = base + r;
+            uint32_t g = 0;
+            if (s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1)) g = s_pg[window_part<K>(P, s, k, part_bits)];
+            const uint32_t lo = __ballot_sync(FULL, g & 1u), hi = __ballot_sync(FULL, (g >> 1) & 1u);
+            if (lane == 0) rid[4 * t + i] = spread_bits(lo) | (spread_bits(hi) << 1);
+        }
+    }
+}
+
+template <class K>
+void launch_range_ids(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                      int part_bits, const uint8_t *part_group, uint64_t *rid) {
+    const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
+    const uint64_t need = (tiles + 7) / 8, cap = (uint64_t)c.sms * 8;
+    k_range_ids<K><<<(int)(need < cap ? (need ? need : 1) : cap), 256, 0, c.stream>>>(P, V, L.n_bases, k, part_bits,
+                                                                                   part_group, rid);
+}
+template void launch_range_ids<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
+                                         const uint64_t *, int, const uint8_t *, uint64_t *);
+template void launch_range_ids<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
+                                       int, const uint8_t *, uint64_t *);
+uint64_t range_id_words(uint64_t n_bases) { return 4 * ((n_bases + P1_TILE - 1) / P1_TILE) + 4; }
+
 template <class K>
 __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys, uint64_t n, uint64_t *filter,
                                                      int sector_shift, const uint64_t *__restrict__ patterns,
@@ -422,6 +475,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
                                                           K *firsts, unsigned long long *first_count,
                                                           uint64_t first_cap, uint64_t *hist, int hist_passes,
                                                           int part_bits, uint32_t part_lo, uint32_t part_hi,
+                                                          const uint64_t *__restrict__ rid, uint32_t rid_value,
                                                           BucketGeom bg, uint64_t t_begin, uint64_t t_end,
                                                           uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -509,7 +563,9 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
             const int r = lane + WARP * i;
             const uint64_t s = base + r;
             bool in = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
-            if (in) {
+            if (in && rid) {  // the window's range id, written by k_range_ids
+                in = ((__ldg(rid + (s >> 5)) >> (2 * (s & 31))) & 3u) == rid_value;
+            } else if (in) {
                 const uint32_t pt = window_part<K>(P, s, k, part_bits);
                 in = pt >= part_lo && pt < part_hi;
             }
@@ -573,7 +629,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket, uint64_t t_begin,
-                  uint64_t t_end) {
+                  uint64_t t_end, const uint64_t *rid, uint32_t rid_value) {
     const uint64_t all_tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     if (t_end > all_tiles) t_end = all_tiles;
     if (t_begin >= t_end) return;
@@ -598,7 +654,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
         const uint64_t need = (tiles + P1_WARPS - 1) / P1_WARPS, cap = (uint64_t)c.sms * per_sm;
         rk<<<(int)(need < cap ? (need ? need : 1) : cap), P1_BLOCK, rsmem, c.stream>>>(
             P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask, cand, cand_count, cand_cap, firsts,
-            first_count, first_cap, hist, hist_passes, part_bits, part_lo, part_hi, bg, t_begin, t_end, err);
+            first_count, first_cap, hist, hist_passes, part_bits, part_lo, part_hi, rid, rid_value, bg, t_begin, t_end,
+            err);
         return;
     }
     const int mode = (n_libs ? P1_BATCHED : 0) | (part_bits ? P1_PARTED : 0) | (by_bucket ? P1_BY_BUCKET : 0);
@@ -627,12 +684,13 @@ void launch_filter_keys(const LaunchCfg &c, const K *keys, uint64_t n, const Fil
 template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
                                      unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, const uint64_t *, int,
-                                     const uint64_t *, uint32_t *, const BucketGeom *, uint64_t, uint64_t);
+                                     const uint64_t *, uint32_t *, const BucketGeom *, uint64_t, uint64_t,
+                                     const uint64_t *, uint32_t);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
                                    unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
                                    const uint64_t *, int, const uint64_t *, uint32_t *, const BucketGeom *, uint64_t,
-                                   uint64_t);
+                                   uint64_t, const uint64_t *, uint32_t);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

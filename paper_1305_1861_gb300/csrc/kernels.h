@@ -81,7 +81,12 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr, uint64_t t_begin = 0,
-                  uint64_t t_end = ~0ull);
+                  uint64_t t_end = ~0ull, const uint64_t *rid = nullptr, uint32_t rid_value = 0);
+// Range id of every valid window (two bits per position, range_id_words(n_bases) words): group[part].
+uint64_t range_id_words(uint64_t n_bases);
+template <class K>
+void launch_range_ids(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
+                      int part_bits, const uint8_t *part_group, uint64_t *rid);
 // a2+a3, filter-blocked form of pass 1 (one library, bucketed sort-and-compact): the valid windows (of
 // parts [part_lo, part_hi) when part_bits > 0) are binned by the top 8 bits of their hash into bin_keys
 // (room for every such window), then probed bin after bin, so the filter blocks being probed stay in L2;
