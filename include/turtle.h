@@ -213,8 +213,9 @@ const char *turtle_strerror(int code);
 void turtle_trim(void);
 
 /* ------------------------------------------------------------------ contexts and the device form */
-/* A context owns device scratch (grown on demand, kept between calls), the
- * device result of its last call, an error word and timing events. */
+/* A context owns device scratch (a memory pool grown on demand and kept between calls: its idle
+ * memory counts as free for the context's own budget; turtle_ctx_trim gives it back), the device
+ * result of its last call, an error word and timing events. */
 typedef struct turtle_ctx turtle_ctx;
 
 /* Create a context on CUDA device `device`. */
@@ -309,6 +310,10 @@ typedef struct {
 
 /* Statistics of the context's last successful call. */
 int turtle_ctx_stats(const turtle_ctx *ctx, turtle_stats *st);
+
+/* Give back to the device the memory the context's pool keeps unused between calls (its last
+ * device result stays valid). Waits for the context's work. */
+void turtle_ctx_trim(turtle_ctx *ctx);
 
 /* Device memory of the context's pool: *used = bytes held by live buffers (the last call's device
  * result, between calls), *reserved = bytes the pool keeps from the driver for later calls. After a

@@ -124,6 +124,7 @@ def load():
         "turtle_ctx_stats": (ctypes.c_int, [_p, _p]),
         "turtle_shard_bounds": (ctypes.c_int, [_p, u32, u32, _p]),
         "turtle_ctx_pool_bytes": (ctypes.c_int, [_p, _p, _p]),
+        "turtle_ctx_trim": (None, [_p]),
         "turtle_test_inject": (ctypes.c_int, [ctypes.c_int, u64]),
         "turtle_tune_select": (ctypes.c_int, [_p, _p, _p, _p, _p]),
         "turtle_autotune": (ctypes.c_int, [_p, _p, u64, _p, u64, ctypes.c_int, u32, _p, _p, _p, _p]),
@@ -472,6 +473,10 @@ class Context:
                                        ctypes.byref(best), ctypes.byref(rep))
         _check(rc, "turtle_autotune")
         return best, rep
+
+    def trim(self):
+        """Give back the device memory this context's pool keeps unused between calls."""
+        self._lib.turtle_ctx_trim(self._h)
 
     def pool_bytes(self):
         """(bytes used by live buffers, bytes reserved) of this context's device memory pool."""

@@ -170,20 +170,12 @@ void ctx_begin(turtle_ctx *c, cudaStream_t s) {
     ck(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * C_N, s));
 }
 
-// Free this call's scratch. The pool keeps freed memory for the next call (re-growing a
-// pool from the driver is slow); only when the device runs short of free memory (below a
-// quarter) does it give back everything above a quarter of the device.
+// Free this call's scratch. The pool keeps freed memory for the next call: re-growing a pool maps
+// physical memory again, which cost a large input hundreds of milliseconds per call when the pool
+// was trimmed at the end of each call. The context's budget counts the pool's idle memory as free;
+// turtle_ctx_trim (or turtle_ctx_destroy) gives it back to the device.
 void ctx_end(turtle_ctx *c, cudaStream_t s) {
     free_list(c->scratch, s);
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b < total_b / 4) {
-        uint64_t reserved = 0;
-        if (cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
-            reserved > total_b / 4) {
-            cudaStreamSynchronize(s);
-            cudaMemPoolTrimTo(c->pool, total_b / 4);
-        }
-    }
     cudaGetLastError();
 }
 
@@ -2025,6 +2017,18 @@ void turtle_ctx_destroy(turtle_ctx *c) {
     if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
+}
+
+void turtle_ctx_trim(turtle_ctx *c) {
+    if (!c) return;
+    if (cudaSetDevice(c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(c->pool, 0);
+    cudaGetLastError();
 }
 
 int turtle_ctx_pool_bytes(const turtle_ctx *c, uint64_t *used, uint64_t *reserved) {
