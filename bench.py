@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--member-filter", action="store_true", help="screen first sightings with a membership bitmap")
     ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..3 (-1 = default)")
     ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
+    ap.add_argument("--bucket-windows", type=int, default=0, help="windows per bucket, about (0 = default 16384)")
     ap.add_argument("--compact", type=int, default=-1,
                     help="0 = bucketed, 1 = global sort-and-compact, 2 = hash-table counting, "
                          "3 = lazy sort-and-compact phases (memory-capped, chunked)")
@@ -335,6 +336,8 @@ def make_params(pkg, args, **kw):
         prm.probe_order = args.probe_order
     if args.host_transfer >= 0:
         prm.host_transfer = args.host_transfer
+    if args.bucket_windows:
+        prm.bucket_windows = args.bucket_windows
     return prm
 
 
