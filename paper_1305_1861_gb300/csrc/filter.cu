@@ -411,13 +411,17 @@ __global__ void __launch_bounds__(256) k_range_ids(const uint64_t *__restrict__ 
     for (uint64_t t = (uint64_t)blockIdx.x * 8 + warp; t < tiles; t += (uint64_t)gridDim.x * 8) {
         const uint64_t base = t * P1_TILE;
         const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+        uint32_t g[P1_ILP];  // all four windows' tests first, so their loads overlap; then the ballots
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
             const int r = lane + WARP * i;
             const uint64_t s = base + r;
-            uint32_t g = 0;
-            if (s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1)) g = s_pg[window_part<K>(P, s, k, part_bits)];
-            const uint32_t lo = __ballot_sync(FULL, g & 1u), hi = __ballot_sync(FULL, (g >> 1) & 1u);
+            g[i] = 0;
+            if (s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1)) g[i] = s_pg[window_part<K>(P, s, k, part_bits)];
+        }
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const uint32_t lo = __ballot_sync(FULL, g[i] & 1u), hi = __ballot_sync(FULL, (g[i] >> 1) & 1u);
             if (lane == 0) rid[4 * t + i] = spread_bits(lo) | (spread_bits(hi) << 1);
         }
     }
@@ -558,19 +562,23 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
     for (uint64_t t = t_begin + (uint64_t)blockIdx.x * P1_WARPS + warp; t < t_end; t += (uint64_t)gridDim.x * P1_WARPS) {
         const uint64_t base = t * P1_TILE;
         const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+        bool in[P1_ILP];  // all four windows' tests first, so their loads overlap; then the ballots
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
             const int r = lane + WARP * i;
             const uint64_t s = base + r;
-            bool in = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
-            if (in && rid) {  // the window's range id, written by k_range_ids
-                in = ((__ldg(rid + (s >> 5)) >> (2 * (s & 31))) & 3u) == rid_value;
-            } else if (in) {
+            in[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
+            if (in[i] && rid) {  // the window's range id, written by k_range_ids
+                in[i] = ((__ldg(rid + (s >> 5)) >> (2 * (s & 31))) & 3u) == rid_value;
+            } else if (in[i]) {
                 const uint32_t pt = window_part<K>(P, s, k, part_bits);
-                in = pt >= part_lo && pt < part_hi;
+                in[i] = pt >= part_lo && pt < part_hi;
             }
-            const uint32_t m = __ballot_sync(FULL, in);
-            if (in) q[nq + __popc(m & lt)] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < P1_ILP; i++) {
+            const uint32_t m = __ballot_sync(FULL, in[i]);
+            if (in[i]) q[nq + __popc(m & lt)] = base + lane + WARP * i;
             nq += __popc(m);
         }
         __syncwarp();
