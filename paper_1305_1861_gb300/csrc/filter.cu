@@ -384,19 +384,16 @@ template void launch_part_count<uint64_t>(const LaunchCfg &, const PackLayout &,
 template void launch_part_count<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
                                         const uint64_t *, int, unsigned long long *);
 
-// Key range of every window, two bits per position (bits 2j+1..2j of word w for position 32w + j), for up
-// to four ranges: range id = group[part of the window's key]. Each range's pass 1 then selects its
-// windows from these words and the validity bitmap, without computing any other window's key.
+// Key range of every window, two bits per position, for up to four ranges: range id = group[part of the
+// window's key]. Word w covers positions 32w .. 32w+31 as two bit planes: bit j of its low half is the
+// low bit of position 32w + j's id, bit j of its high half the high bit. Each range's pass 1 then
+// selects its windows from these words and the validity bitmap, without computing any other key.
 constexpr int MAX_PARTS = 64;  // key-range parts of a library (part_bits <= 6)
 
-__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {  // bit j of x -> bit 2j
-    uint64_t v = x;
-    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
-    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
-    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
-    v = (v | (v << 2)) & 0x3333333333333333ull;
-    v = (v | (v << 1)) & 0x5555555555555555ull;
-    return v;
+__device__ __forceinline__ uint32_t range_id_of(const uint64_t *__restrict__ rid, uint64_t s) {
+    const uint64_t w = __ldg(rid + (s >> 5));
+    const int j = (int)(s & 31);
+    return (uint32_t)(((w >> j) & 1u) | (((w >> (32 + j)) & 1u) << 1));
 }
 
 template <class K>
@@ -422,7 +419,7 @@ __global__ void __launch_bounds__(256) k_range_ids(const uint64_t *__restrict__ 
 #pragma unroll
         for (int i = 0; i < P1_ILP; i++) {
             const uint32_t lo = __ballot_sync(FULL, g[i] & 1u), hi = __ballot_sync(FULL, (g[i] >> 1) & 1u);
-            if (lane == 0) rid[4 * t + i] = spread_bits(lo) | (spread_bits(hi) << 1);
+            if (lane == 0) rid[4 * t + i] = (uint64_t)lo | ((uint64_t)hi << 32);
         }
     }
 }
@@ -569,7 +566,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
             const uint64_t s = base + r;
             in[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
             if (in[i] && rid) {  // the window's range id, written by k_range_ids
-                in[i] = ((__ldg(rid + (s >> 5)) >> (2 * (s & 31))) & 3u) == rid_value;
+                in[i] = range_id_of(rid, s) == rid_value;
             } else if (in[i]) {
                 const uint32_t pt = window_part<K>(P, s, k, part_bits);
                 in[i] = pt >= part_lo && pt < part_hi;

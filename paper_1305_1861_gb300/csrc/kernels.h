@@ -82,7 +82,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr, uint64_t t_begin = 0,
                   uint64_t t_end = ~0ull, const uint64_t *rid = nullptr, uint32_t rid_value = 0);
-// Range id of every valid window (two bits per position, range_id_words(n_bases) words): group[part].
+// Range id of every valid window (two bits per position as two bit planes per 32 positions,
+// range_id_words(n_bases) words): group[part].
 uint64_t range_id_words(uint64_t n_bases);
 template <class K>
 void launch_range_ids(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
