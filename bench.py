@@ -763,23 +763,29 @@ def run_batched(args):
                                   "R in {100,150}, 1%% substitutions, k in {21,31,55}, min_count 2; %.2f Gbase"
                                   % (0.1 * args.scale, 20 * args.scale, n_bases / 1e9)},
            "batched": res["batched"], "plain": res["plain_64_calls"], "batched_autotune": res["batched_autotune"],
+           "batched_mixed": res["batched_mixed"],
            "speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched"]["s_per_batch"],
            "autotune_speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched_autotune"]["s_per_batch"],
+           "mixed_speedup_vs_plain": res["plain_64_calls"]["s_per_batch"] / res["batched_mixed"]["s_per_batch"],
            "identical_results": ok}
     if args.scale == 1.0:  # the same recipe at 1/50 scale: small libraries, where per-call costs dominate
         res_s, ok_s, nb_s = compare(0.02)
         out["small_libraries"] = {"bases": nb_s, "batched": res_s["batched"], "plain": res_s["plain_64_calls"],
                                   "batched_autotune": res_s["batched_autotune"],
+                                  "batched_mixed": res_s["batched_mixed"],
                                   "speedup_vs_plain": res_s["plain_64_calls"]["s_per_batch"]
                                   / res_s["batched"]["s_per_batch"],
                                   "autotune_speedup_vs_plain": res_s["plain_64_calls"]["s_per_batch"]
-                                  / res_s["batched_autotune"]["s_per_batch"], "identical_results": ok_s}
+                                  / res_s["batched_autotune"]["s_per_batch"],
+                                  "mixed_speedup_vs_plain": res_s["plain_64_calls"]["s_per_batch"]
+                                  / res_s["batched_mixed"]["s_per_batch"], "identical_results": ok_s}
     return out
 
 
 def batched_vs_plain(pkg, jobs, args):
-    """64 sequential turtle_count calls vs one turtle_count_batch on the same jobs: medians of alternating
-    steps, and whether every result is identical."""
+    """64 sequential turtle_count calls vs one turtle_count_batch on the same jobs (runs of one k chosen
+    automatically, autotuned, and mixed-k runs): medians of alternating steps, and whether every result
+    is identical."""
 
     def plain():
         return [pkg.turtle_count(b, o, k, m) for b, o, k, m in jobs]
@@ -788,15 +794,20 @@ def batched_vs_plain(pkg, jobs, args):
         return pkg.turtle_count_batch(jobs)
 
     tuned_params = pkg.Params.default(autotune=1)
+    mixed_params = pkg.Params.default(batch_mixed=1)
 
     def batched_tuned():
         return pkg.turtle_count_batch(jobs, tuned_params)
+
+    def batched_mixed():  # libraries of every k (<= 61) in shared runs of up to 64, 128-bit keys
+        return pkg.turtle_count_batch(jobs, mixed_params)
 
     # The forms alternate step by step and each reports its median, so a drift in the host's speed
     # during the run (boxes differ and vary by up to 2x on the host side) hits all alike. The autotuned
     # batch tunes each group's class in its warm-up call; the timed calls reuse the cached knobs.
     pkg.load().turtle_tune_cache_clear()
-    fns = (("plain_64_calls", plain), ("batched", batched), ("batched_autotune", batched_tuned))
+    fns = (("plain_64_calls", plain), ("batched", batched), ("batched_autotune", batched_tuned),
+           ("batched_mixed", batched_mixed))
     for _ in range(max(1, args.warmup)):
         for _, fn in fns:
             out = fn()
@@ -815,8 +826,8 @@ def batched_vs_plain(pkg, jobs, args):
         dt = float(np.median(times[name]))
         res[name] = {"s_per_batch": dt, "kmers_per_s": W / dt, "windows": W,
                      "s_per_batch_all": [round(t, 4) for t in times[name]]}
-    ok = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[0], c[0])
-             and np.array_equal(a[1], c[1]) for a, b, c in zip(plain(), batched(), batched_tuned()))
+    ok = all(all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for b in others)
+             for a, *others in zip(plain(), batched(), batched_tuned(), batched_mixed()))
     return res, ok
 
 

@@ -148,6 +148,12 @@ typedef struct {
                                       vary from run to run and box to box (8 to 190 GB/s measured), locked ones
                                       run at 170-210 GB/s; 1 = always page-lock them; 2 = copy pageable
                                       memory directly. Memory the caller locked already is used as it is. */
+    uint32_t batch_mixed;          /* turtle_count_batch, bucketed form (compact = 0): libraries with different k
+                                      (each at most 61) and the same min_count in one run, keyed with 128 bits
+                                      and tagged in the top 6: fewer runs (each has a fixed cost), but 128-bit
+                                      work for libraries with k <= 32. 0 = when a cost model expects it to be
+                                      faster (many small libraries over several k), 1 = always, 2 = never
+                                      (one run per k, as many libraries as its key bits can tag). */
 } turtle_params;
 
 /* Fill *p with the defaults above. */
@@ -399,9 +405,11 @@ typedef struct {
  * on the device and every window's key carries its library index in the key bits above
  * 2k, so each stage is one launch for the whole group and libraries never mix; a group
  * holds up to 64 libraries (fewer when 2k leaves less room: k = 31 takes 4 per run,
- * k = 32 and k = 64 one). outs[i] receives job i's result, identical to turtle_count on
- * that job (free each with turtle_result_free). Uses the internal context of the
- * current device.
+ * k = 32 and k = 64 one). With params->batch_mixed, libraries of different k (at most 61)
+ * and the same min_count can share a run instead: 128-bit keys, the library in the top 6
+ * bits, up to 64 libraries per run. outs[i] receives job i's result, identical to
+ * turtle_count on that job (free each with turtle_result_free). Uses the internal context
+ * of the current device.
  */
 int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_params *params, void *stream,
                        turtle_result *outs);

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
                 ("compact", u32), ("bucket_slots", u32),
                 ("cturtle_bits_per_window", u32), ("hash_slots_log2", u32), ("shard_count", u32),
                 ("shard_index", u32), ("probe_order", u32), ("bucket_windows", u32), ("autotune", u32),
-                ("host_transfer", u32)]
+                ("host_transfer", u32), ("batch_mixed", u32)]
 
     @classmethod
     def default(cls, **kw) -> "Params":

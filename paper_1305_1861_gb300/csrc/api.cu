@@ -225,7 +225,7 @@ bool params_ok(const turtle_params &p) {
            p.shard_count <= TURTLE_PARTS && p.shard_index < (p.shard_count ? p.shard_count : 1) &&
            !(p.shard_count > 1 && p.compact == 3) && p.probe_order <= 1 &&
            (p.bucket_windows == 0 || (p.bucket_windows >= 1024 && p.bucket_windows <= (1u << 20))) &&
-           p.host_transfer <= 2;
+           p.host_transfer <= 2 && p.batch_mixed <= 2;
 }
 
 // Shard s of n takes the key-range parts [bounds[s], bounds[s+1]): bounds[s] is the first part at which
@@ -270,11 +270,18 @@ struct PrePacked {
 };
 
 // Batched form: positions [lib_starts[l], lib_starts[l+1]) are library l; keys carry l above their 2k bits.
+// A mixed batch (libraries of different k, 128-bit keys) carries each library's k and puts the tag in the
+// key's top bits; its libraries start on 128-position boundaries, so no pass-1 tile or validity word
+// spans two libraries.
 struct BatchTag {
     const uint64_t *lib_starts;  // device, n_libs + 1
     int n_libs;
     int tag_bits;
     unsigned long long *lib_windows;  // device, n_libs counters (zeroed by run_count)
+    const int *lib_k = nullptr;       // mixed batch: device, each library's k
+    int tag_shift = 0;                // mixed batch: bit of the tag (128 - tag_bits); else 2k
+    const uint64_t *host_starts = nullptr;  // mixed batch: lib_starts on the host
+    const int *host_k = nullptr;            // mixed batch: each library's k on the host
 };
 
 struct DeviceOut {
@@ -537,13 +544,14 @@ uint64_t lib_filter_regions(turtle_ctx *c, const std::vector<unsigned long long>
 
 // Batch: each library its own range of buckets, sized by its windows (lib_w); *bits = index bits.
 BucketGeom lib_buckets(turtle_ctx *c, const std::vector<unsigned long long> &lib_w, int k, int *bits,
-                       cudaStream_t s, uint64_t per_bucket = BUCKET_WINDOWS) {
+                       cudaStream_t s, uint64_t per_bucket = BUCKET_WINDOWS, const BatchTag *tag = nullptr) {
     std::vector<int> lb;
     *bits = batch_bucket_bits(lib_w, lb, per_bucket);
     std::vector<uint4> lg(lib_w.size());
     uint32_t at = 0;
+    const bool mixed = tag && tag->lib_k;
     for (size_t l = 0; l < lib_w.size(); l++) {
-        lg[l] = make_uint4(at, 1u << lb[l], (uint32_t)(62 - lb[l]), 0u);
+        lg[l] = make_uint4(at, 1u << lb[l], (uint32_t)(62 - lb[l]), mixed ? (uint32_t)tag->host_k[l] : 0u);
         at += 1u << lb[l];
     }
     uint4 *d_lg = (uint4 *)ctx_alloc(c, sizeof(uint4) * lg.size(), s);
@@ -551,7 +559,7 @@ BucketGeom lib_buckets(turtle_ctx *c, const std::vector<unsigned long long> &lib
     BucketGeom bg{};
     bg.k = k;
     bg.n_buckets = at;
-    bg.tag_shift = 2 * k;
+    bg.tag_shift = mixed ? tag->tag_shift : 2 * k;
     bg.lib = d_lg;
     return bg;
 }
@@ -850,9 +858,16 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         st.stage_launches[TURTLE_STAGE_PACK] = 2;
     }
     tm.start(TURTLE_STAGE_VALID);
-    launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS);
+    if (tag && tag->lib_k) {  // mixed batch: each library's windows with its own k, over its own words
+        for (int l = 0; l < tag->n_libs; l++)
+            launch_valid(lc, L, tag->host_k[l], B, S, V, ctr + C_WINDOWS, tag->host_starts[l] / 64,
+                         (tag->host_starts[l + 1] + 63) / 64);
+        st.stage_launches[TURTLE_STAGE_VALID] = (uint32_t)tag->n_libs;
+    } else {
+        launch_valid(lc, L, k, B, S, V, ctr + C_WINDOWS);
+        st.stage_launches[TURTLE_STAGE_VALID] = 1;
+    }
     tm.stop(TURTLE_STAGE_VALID);
-    st.stage_launches[TURTLE_STAGE_VALID] = 1;
     std::vector<unsigned long long> lib_w;
     if (tag) {
         ck(cudaMemsetAsync(tag->lib_windows, 0, 8 * tag->n_libs, s));
@@ -888,7 +903,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     const bool hashed = prm.compact == 2;
     // batches and the hash-table form recount from first sightings
     const bool firsts_mode = use_filter && (!prm.recount_windows || tag || hashed);
-    const int key_bits = 2 * k + (tag ? tag->tag_bits : 0);
+    const int key_bits = tag && tag->lib_k ? 128 : 2 * k + (tag ? tag->tag_bits : 0);
     const int passes = sort_passes_for(key_bits);
     const uint64_t *patterns = use_filter ? ctx_patterns(c, prm, s) : nullptr;
 
@@ -1010,7 +1025,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         int bucket_bits = 0;
         BucketGeom bg{};
         if (bucketed && tag) {  // batch: each library its own range of buckets, sized by its windows
-            bg = lib_buckets(c, lib_w, k, &bucket_bits, s, bucket_windows_of(prm));
+            bg = lib_buckets(c, lib_w, k, &bucket_bits, s, bucket_windows_of(prm), tag);
         } else if (bucketed) {  // every window of the range becomes a candidate or a first sighting: Wg of them
             bg = bucket_geom(Wg, parted ? groups[g].first : 0u, parted ? groups[g].second : (1u << PART_BITS),
                              PART_BITS, k, &bucket_bits, bucket_windows_of(prm));
@@ -1035,7 +1050,8 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
             launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cand_cap, firsts, ctr + C_FIRST, Wg,
                             hist, hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
                             tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
-                            bucketed ? &bg : nullptr, 0, ~0ull, rid, (uint32_t)g);
+                            bucketed ? &bg : nullptr, 0, ~0ull, rid, (uint32_t)g, tag ? tag->lib_k : nullptr,
+                            tag ? tag->tag_shift : 0);
         }
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;
@@ -1680,20 +1696,30 @@ void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, u
 
 // One batched run: libraries `idx` (same k and min_count) concatenated on the device, counted by
 // one pipeline with library-tagged keys, results split back per library into outs[] by a host
-// thread of bo, which also frees the run's device results.
+// thread of bo, which also frees the run's device results. A mixed run (K = Key128) holds libraries
+// of different k (same min_count): each starts on a 128-position boundary (the gap filled with N,
+// so no window crosses it), windows are keyed with their library's k and the tag sits in the top
+// 6 key bits; results of libraries with k <= 32 are narrowed to 64-bit keys on the device.
 template <class K>
 int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, int tag_bits,
               const turtle_params *params, cudaStream_t s, turtle_result *outs, BatchOutput &bo,
-              std::function<void(int)> done) {
-    const int k = jobs[idx[0]].k;
-    const uint32_t min_count = jobs[idx[0]].min_count;
+              std::function<void(int)> done, bool mixed = false) {
     const int n_libs = (int)idx.size();
+    int k = 0;  // the widest k (a mixed run's libraries carry their own)
+    std::vector<int> lib_k(n_libs);
+    for (int l = 0; l < n_libs; l++) {
+        lib_k[l] = jobs[idx[l]].k;
+        k = std::max(k, lib_k[l]);
+    }
+    const uint32_t min_count = jobs[idx[0]].min_count;
     const turtle_params prm = resolve(params);
     if (!params_ok(prm) || prm.shard_count > 1) return TURTLE_E_ARG;
+    if (mixed && (sizeof(K) != 16 || n_libs > 64 || k > MIXED_K_MAX || prm.compact != 0)) return TURTLE_E_ARG;
     std::vector<uint64_t> lib_starts(n_libs + 1, 0), entry_starts(n_libs + 1, 0);
     for (int l = 0; l < n_libs; l++) {
         const turtle_job &j = jobs[idx[l]];
         lib_starts[l + 1] = lib_starts[l] + (j.offsets[j.n_reads] - j.offsets[0]);
+        if (mixed && l + 1 < n_libs) lib_starts[l + 1] = (lib_starts[l + 1] + 127) & ~127ull;
         entry_starts[l + 1] = entry_starts[l] + j.n_reads;
     }
     const uint64_t n_bases = lib_starts[n_libs], n_reads = entry_starts[n_libs];
@@ -1716,22 +1742,35 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         uint64_t *d_tab = (uint64_t *)ctx_alloc(c, 8 * 2 * (n_libs + 1), s);  // lib_starts, entry_starts
         unsigned long long *d_lw = (unsigned long long *)ctx_alloc(c, 8 * n_libs, s);
         // the bucketed form overlaps the copy of the bases with pass 1; the global form copies first
-        const bool overlapped = prm.compact == 0 && n_bases >= OVERLAP_MIN;
+        const bool overlapped = prm.compact == 0 && n_bases >= OVERLAP_MIN && !mixed;
         std::vector<HostPiece> pieces;
         std::vector<unsigned long long> w_est(n_libs);
         for (int l = 0; l < n_libs; l++) {
             const turtle_job &j = jobs[idx[l]];
-            const uint64_t nb = lib_starts[l + 1] - lib_starts[l];
-            const uint64_t lost = j.n_reads * (uint64_t)(k - 1);
+            const uint64_t nb = j.offsets[j.n_reads] - j.offsets[0];
+            const uint64_t lost = j.n_reads * (uint64_t)(lib_k[l] - 1);
             w_est[l] = std::max<uint64_t>(nb > lost ? nb - lost : 0, nb / 4);
             if (overlapped) pieces.push_back(HostPiece{lib_starts[l], nb, j.bases + j.offsets[0]});
             else if (nb) locks.copy(d_bases + lib_starts[l], j.bases + j.offsets[0], nb, cudaMemcpyHostToDevice, s);
+            if (mixed && lib_starts[l + 1] > lib_starts[l] + nb)  // the gap up to the next library: N
+                ck(cudaMemsetAsync(d_bases + lib_starts[l] + nb, 'N', lib_starts[l + 1] - lib_starts[l] - nb, s));
             locks.copy(d_src + entry_starts[l] + l, j.offsets, 8 * (j.n_reads + 1), cudaMemcpyHostToDevice, s);
+        }
+        int *d_libk = nullptr;
+        if (mixed) {
+            d_libk = (int *)ctx_alloc(c, 4 * n_libs, s);
+            ck(cudaMemcpyAsync(d_libk, lib_k.data(), 4 * n_libs, cudaMemcpyHostToDevice, s));
         }
         ck(cudaMemcpyAsync(d_tab, lib_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
         ck(cudaMemcpyAsync(d_tab + n_libs + 1, entry_starts.data(), 8 * (n_libs + 1), cudaMemcpyHostToDevice, s));
         launch_batch_offsets(lc, d_src, d_tab + n_libs + 1, d_tab, n_libs, d_off, n_reads + 1);
-        BatchTag tag{d_tab, n_libs, tag_bits, d_lw};
+        BatchTag tag{d_tab, n_libs, mixed ? MIXED_TAG_BITS : tag_bits, d_lw};
+        if (mixed) {
+            tag.lib_k = d_libk;
+            tag.tag_shift = 128 - MIXED_TAG_BITS;
+            tag.host_starts = lib_starts.data();
+            tag.host_k = lib_k.data();
+        }
         L2Fetch l2(prm.l2_fetch_bytes);
         if (overlapped)
             run_count_overlapped<K>(c, pieces, n_bases, n_reads, d_bases, d_off, k, min_count, prm, s, o, locks, &tag,
@@ -1739,10 +1778,10 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         else run_count<K>(c, d_bases, n_bases, d_off, n_reads, k, min_count, prm, s, o, nullptr, &tag);
         // split on the device: library boundaries + tag bits cleared, then one copy per library
         std::vector<uint64_t> starts(n_libs + 1, ~0ull);
-        if (tag_bits) {
+        if (tag.tag_bits) {
             uint64_t *d_starts = (uint64_t *)ctx_alloc(c, 8 * n_libs, s);
             ck(cudaMemsetAsync(d_starts, 0xff, 8 * n_libs, s));
-            launch_split_tags<K>(lc, (K *)o.keys, o.n, 2 * k, d_starts);
+            launch_split_tags<K>(lc, (K *)o.keys, o.n, mixed ? tag.tag_shift : 2 * k, d_starts);
             ck(cudaMemcpyAsync(starts.data(), d_starts, 8 * n_libs, cudaMemcpyDeviceToHost, s));
         } else {
             starts[0] = 0;
@@ -1752,21 +1791,41 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
         starts[n_libs] = o.n;
         for (int l = n_libs - 1; l >= 0; l--)
             if (starts[l] == ~0ull) starts[l] = starts[l + 1];  // no entries: an empty range
+        // a mixed run: the keys of its libraries with k <= 32, narrowed to 64 bits, at narrow_at[l]
+        std::vector<uint64_t> narrow_at(n_libs, ~0ull);
+        uint64_t *d_narrow = nullptr;
+        if (mixed) {
+            uint64_t n_narrow = 0;
+            for (int l = 0; l < n_libs; l++)
+                if (lib_k[l] <= 32) {
+                    narrow_at[l] = n_narrow;
+                    n_narrow += starts[l + 1] - starts[l];
+                }
+            if (n_narrow) {
+                d_narrow = (uint64_t *)ctx_alloc(c, 8 * n_narrow, s, true);
+                for (int l = 0; l < n_libs; l++)
+                    if (lib_k[l] <= 32)
+                        launch_narrow_keys(lc, (const Key128 *)o.keys + starts[l], starts[l + 1] - starts[l],
+                                           d_narrow + narrow_at[l]);
+                ck(cudaStreamSynchronize(s));  // the copy-out runs on its own stream
+            }
+        }
         // the device results now belong to the copy-out thread (the next run must not free them)
         for (auto it = c->result.begin(); it != c->result.end();)
-            it = (*it == o.keys || *it == (void *)o.counts) ? c->result.erase(it) : it + 1;
+            it = (*it == o.keys || *it == (void *)o.counts || *it == (void *)d_narrow) ? c->result.erase(it) : it + 1;
         ctx_end(c, s);
         std::vector<size_t> lib_idx = idx;
         const int dev = c->device;
         const uint32_t transfer = prm.host_transfer;
         cudaStream_t os = bo.stream();
         bo.post([=, &bo]() {
-            const int kw = sizeof(K) / 8;
             int rc = TURTLE_OK;
             if (cudaSetDevice(dev) != cudaSuccess) rc = TURTLE_E_CUDA;
             for (int l = 0; l < n_libs && rc == TURTLE_OK; l++) {
                 turtle_result &r = outs[lib_idx[l]];
-                r.k = k;
+                const bool narrowed = narrow_at[l] != ~0ull;
+                const int kw = narrowed ? 1 : (int)(sizeof(K) / 8);
+                r.k = lib_k[l];
                 r.n = starts[l + 1] - starts[l];
                 r.n_windows = lib_windows[l];
                 bool fk = true, fc = true;
@@ -1783,7 +1842,9 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
                         HostLocks rl(c, transfer);
                         rl.add(r.keys, 8 * kw * r.n);
                         rl.add(r.counts, 4 * r.n);
-                        copy_to_host(rl, r.keys, (const K *)o.keys + starts[l], 8 * kw * r.n, os, false);
+                        const void *src = narrowed ? (const void *)(d_narrow + narrow_at[l])
+                                                   : (const void *)((const K *)o.keys + starts[l]);
+                        copy_to_host(rl, r.keys, src, 8 * kw * r.n, os, false);
                         copy_to_host(rl, r.counts, o.counts + starts[l], 4 * r.n, os, false);
                     } catch (Fail f) {
                         rc = f.code;
@@ -1792,6 +1853,7 @@ int batch_run(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &
             }
             cudaFreeAsync(o.keys, os);
             cudaFreeAsync(o.counts, os);
+            if (d_narrow) cudaFreeAsync(d_narrow, os);
             cudaGetLastError();
             if (rc) bo.fail(rc);
             if (done) done(rc);
@@ -1903,8 +1965,33 @@ size_t batch_capacity(int k) {
     return room >= 6 ? 64 : ((size_t)1 << room);
 }
 
+// Whether libraries idx (same min_count, k <= MIXED_K_MAX) are expected to finish sooner in mixed runs
+// than in runs grouped by k. A run costs a fixed time (its launches, host synchronisations and copy
+// set-up: RUN_MS) plus time per base; in a mixed run the libraries with k <= 32 are keyed with 128 bits
+// instead of 64, which costs them MIX_EXTRA_NS more per base. Both measured on GB300 (host arrays in
+// and out): 12 to 48 libraries of 20 kbase to 10 Mbase over 3 to 12 k.
+bool mixed_runs_pay(const turtle_job *jobs, const std::vector<size_t> &idx) {
+    constexpr double RUN_MS = 0.25, MIX_EXTRA_NS = 0.025;
+    std::map<int, size_t> per_k;
+    double narrow_bases = 0;
+    for (size_t i : idx) {
+        per_k[jobs[i].k]++;
+        if (jobs[i].k <= 32) narrow_bases += (double)(jobs[i].offsets[jobs[i].n_reads] - jobs[i].offsets[0]);
+    }
+    size_t grouped = 0;
+    for (auto &kv : per_k) grouped += (kv.second + batch_capacity(kv.first) - 1) / batch_capacity(kv.first);
+    const size_t mixed = (idx.size() + 63) / 64;
+    return grouped > mixed && (double)(grouped - mixed) * RUN_MS > narrow_bases * MIX_EXTRA_NS * 1e-6;
+}
+
 int batch_run_jobs(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, const turtle_params *params,
-                   cudaStream_t s, turtle_result *outs, BatchOutput &bo, std::function<void(int)> done) {
+                   cudaStream_t s, turtle_result *outs, BatchOutput &bo, std::function<void(int)> done, bool mixed) {
+    if (mixed) {
+        if (idx.empty() || idx.size() > 64 || !bo.ok()) return TURTLE_E_ARG;
+        for (size_t i : idx)
+            if (jobs[i].k > MIXED_K_MAX || jobs[i].min_count != jobs[idx[0]].min_count) return TURTLE_E_ARG;
+        return batch_run<Key128>(c, jobs, idx, MIXED_TAG_BITS, params, s, outs, bo, done, true);
+    }
     if (idx.empty() || idx.size() > batch_capacity(jobs[idx[0]].k) || !bo.ok()) return TURTLE_E_ARG;
     const int k = jobs[idx[0]].k;
     int tag_bits = 0;
@@ -2335,9 +2422,32 @@ int turtle_count_batch(const turtle_job *jobs, size_t n_jobs, const turtle_param
     BatchOutput bo;
     if (!bo.ok()) return TURTLE_E_CUDA;
     // group by (k, min_count); a run holds as many libraries as the spare key bits can tag (<= 64)
-    std::map<std::pair<int, uint32_t>, std::vector<size_t>> groups;
-    for (size_t i = 0; i < n_jobs; i++) groups[{jobs[i].k, jobs[i].min_count}].push_back(i);
     const turtle_params prm = resolve(params);
+    std::map<std::pair<int, uint32_t>, std::vector<size_t>> groups;
+    std::map<uint32_t, std::vector<size_t>> mixed;  // min_count -> libraries counted in mixed runs
+    for (size_t i = 0; i < n_jobs; i++) groups[{jobs[i].k, jobs[i].min_count}].push_back(i);
+    if (prm.batch_mixed != 2 && prm.compact == 0 && params_ok(prm)) {
+        std::map<uint32_t, std::vector<size_t>> cand;  // min_count -> libraries that a mixed run can hold
+        for (auto &kv : groups)
+            if (kv.first.first <= MIXED_K_MAX) cand[kv.first.second].insert(cand[kv.first.second].end(),
+                                                                              kv.second.begin(), kv.second.end());
+        for (auto &kv : cand)
+            if (prm.batch_mixed == 1 || mixed_runs_pay(jobs, kv.second)) {
+                mixed[kv.first] = kv.second;
+                for (size_t i : kv.second) groups.erase({jobs[i].k, jobs[i].min_count});
+            }
+    }
+    for (auto &kv : mixed) {
+        std::vector<size_t> &all = kv.second;
+        // libraries in order of k, so that each run's keys of one width come out together
+        std::stable_sort(all.begin(), all.end(), [&](size_t a, size_t b) { return jobs[a].k < jobs[b].k; });
+        turtle_params gp = prm;
+        if (prm.autotune && rc == TURTLE_OK) rc = tune_group(c, jobs, all, prm, s, &gp);
+        for (size_t a = 0; a < all.size() && rc == TURTLE_OK; a += 64) {
+            std::vector<size_t> idx(all.begin() + a, all.begin() + std::min(all.size(), a + 64));
+            rc = batch_run_jobs(c, jobs, idx, &gp, s, outs, bo, nullptr, true);
+        }
+    }
     for (auto &kv : groups) {
         const size_t per_run = batch_capacity(kv.first.first);
         const std::vector<size_t> &all = kv.second;

@@ -11,13 +11,14 @@ namespace turtle {
 // their library's range of buckets; tags are the most significant key bits, so the order holds.
 template <class K>
 __device__ __forceinline__ uint32_t bucket_of(K key, const BucketGeom &g) {
-    const uint64_t v = top31(key, g.k);
-    const uint64_t f = v * ((1ull << 32) - v);
     if (g.lib) {
         const uint4 e = __ldg(g.lib + tag_of(key, g.tag_shift));
-        const uint64_t b = f >> e.z;
+        const uint64_t v = top31(key, e.w ? (int)e.w : g.k);  // a mixed batch: the library's own k
+        const uint64_t b = (v * ((1ull << 32) - v)) >> e.z;
         return e.x + (b < e.y ? (uint32_t)b : e.y - 1);
     }
+    const uint64_t v = top31(key, g.k);
+    const uint64_t f = v * ((1ull << 32) - v);
     const uint64_t b = f >= g.f_lo ? (f - g.f_lo) >> g.shift : 0;
     return b < g.n_buckets ? (uint32_t)b : g.n_buckets - 1;
 }

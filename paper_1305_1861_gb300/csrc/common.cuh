@@ -117,8 +117,9 @@ __device__ __forceinline__ uint64_t top31(uint64_t key, int k) {
     return (b >= 31 ? key >> (b - 31) : key << (31 - b)) & 0x7fffffffull;
 }
 __device__ __forceinline__ uint64_t top31(Key128 key, int k) {
-    const int b = 2 * k;  // 66..128 bits: the top 31 start inside hi or straddle hi/lo
-    const int sh = b - 31;
+    const int b = 2 * k;  // 2..128 bits (a mixed batch also keeps short keys in 128 bits)
+    if (b < 31) return (key.lo << (31 - b)) & 0x7fffffffull;
+    const int sh = b - 31;  // 1..97: the top 31 bits lie in lo, straddle hi/lo, or lie in hi
     if (sh >= 64) return (key.hi >> (sh - 64)) & 0x7fffffffull;
     return ((key.hi << (64 - sh)) | (key.lo >> sh)) & 0x7fffffffull;
 }

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
                                                     uint64_t *hist, int hist_passes, int part_bits, uint32_t part_lo,
                                                     uint32_t part_hi, const uint64_t *__restrict__ lib_starts,
                                                     int n_libs, const uint64_t *__restrict__ lib_filter,
+                                                    const int *__restrict__ lib_k, int tag_shift,
                                                     BucketGeom bg, int by_bucket, uint64_t t_begin, uint64_t t_end,
                                                     uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -119,8 +120,11 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
     uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
     __shared__ uint64_t s_lib[65];
     __shared__ uint64_t s_lf[128];  // per-library filter region: first sector, shift of the hash
+    __shared__ int s_libk[64];      // mixed batches: each library's k
     if (BATCHED)
         for (int i = threadIdx.x; i <= n_libs; i += P1_BLOCK) s_lib[i] = lib_starts[i];
+    if (BATCHED && lib_k)
+        for (int i = threadIdx.x; i < n_libs; i += P1_BLOCK) s_libk[i] = lib_k[i];
     if (BATCHED && lib_filter)
         for (int i = threadIdx.x; i < 2 * n_libs; i += P1_BLOCK) s_lf[i] = lib_filter[i];
     if (USE_FILTER)
@@ -156,12 +160,15 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1(const uint64_t *__restrict__
             const uint64_t s = base + r;
             ok[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
             if (ok[i]) {
-                key[i] = canonical<K>(P, s, k);
                 if (BATCHED) {  // batched form: tag the key with its library (the tile's, or a later one)
                     int lo = lib0;
                     while (lo + 1 < n_libs && s_lib[lo + 1] <= s) lo++;
-                    key[i] = add_tag(key[i], (uint32_t)lo, 2 * k);
+                    // mixed batches: every library its own k, the tag in the key's top bits
+                    key[i] = canonical<K>(P, s, lib_k ? s_libk[lo] : k);
+                    key[i] = add_tag(key[i], (uint32_t)lo, lib_k ? tag_shift : 2 * k);
                     libi[i] = (uint32_t)lo;
+                } else {
+                    key[i] = canonical<K>(P, s, k);
                 }
                 if (PARTED) {  // keys of other key ranges wait for their own super-partition
                     const uint32_t pt = key_part(key[i], k, part_bits);
@@ -634,7 +641,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket, uint64_t t_begin,
-                  uint64_t t_end, const uint64_t *rid, uint32_t rid_value) {
+                  uint64_t t_end, const uint64_t *rid, uint32_t rid_value, const int *lib_k, int tag_shift) {
     const uint64_t all_tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     if (t_end > all_tiles) t_end = all_tiles;
     if (t_begin >= t_end) return;
@@ -675,7 +682,7 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
     kern<<<grid, P1_BLOCK, smem, c.stream>>>(P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask,
                                              cand, cand_count, cand_cap, firsts, first_count, first_cap, hist,
                                              hist_passes, part_bits, part_lo, part_hi, lib_starts, n_libs,
-                                             lib_filter, bg, by_bucket, t_begin, t_end, err);
+                                             lib_filter, lib_k, tag_shift, bg, by_bucket, t_begin, t_end, err);
 }
 
 template <class K>
@@ -690,12 +697,12 @@ template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
                                      unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, const uint64_t *, int,
                                      const uint64_t *, uint32_t *, const BucketGeom *, uint64_t, uint64_t,
-                                     const uint64_t *, uint32_t);
+                                     const uint64_t *, uint32_t, const int *, int);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
                                    unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
                                    const uint64_t *, int, const uint64_t *, uint32_t *, const BucketGeom *, uint64_t,
-                                   uint64_t, const uint64_t *, uint32_t);
+                                   uint64_t, const uint64_t *, uint32_t, const int *, int);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

@@ -46,12 +46,22 @@ private:
 // Libraries one batched run can hold for this k (the key bits above 2k tag the library).
 size_t batch_capacity(int k);
 
+// Mixed runs: libraries of different k share a run with 128-bit keys, the library in the top 6 bits.
+constexpr int MIXED_TAG_BITS = 6;                     // up to 64 libraries
+constexpr int MIXED_K_MAX = 64 - MIXED_TAG_BITS / 2;  // their keys below the tag: 2k <= 122
+
+// Whether jobs[idx[...]] (same min_count, each k <= MIXED_K_MAX) are expected to finish sooner in mixed
+// runs than in runs grouped by k (fewer runs, each with a fixed cost, against 128-bit keys for k <= 32).
+bool mixed_runs_pay(const turtle_job *jobs, const std::vector<size_t> &idx);
+
 // One batched run: jobs[idx[...]] (same k and min_count, at most batch_capacity(k)) concatenated
 // on the device and counted by one pipeline on stream s. On TURTLE_OK the per-library copy-out
 // into outs[idx[...]] is posted to bo and done(rc) is called on bo's thread when it finishes;
-// on an error nothing is posted and done is not called.
+// on an error nothing is posted and done is not called. mixed: a run of up to 64 libraries with
+// different k (each at most 61) and the same min_count, keyed with 128 bits (bucketed form only).
 int batch_run_jobs(turtle_ctx *c, const turtle_job *jobs, const std::vector<size_t> &idx, const turtle_params *params,
-                   cudaStream_t s, turtle_result *outs, BatchOutput &bo, std::function<void(int)> done);
+                   cudaStream_t s, turtle_result *outs, BatchOutput &bo, std::function<void(int)> done,
+                   bool mixed = false);
 
 // Autotuner cache: the tuned knobs of (k's key width, min_count >= 2, start.compact, log2 n_bases) merged into
 // *best = start, if that class was tuned before.

@@ -27,7 +27,8 @@ struct PackLayout {
 // Bucket of a key (bucketed sort-and-compact): ((f(top31(key)) - f_lo) >> shift), clamped to
 // [0, n_buckets), with the monotone map f(v) = v (2^32 - v) of the key-range parts: buckets are
 // consecutive key ranges. Batches (lib != null): library l = the key's tag owns the buckets
-// [lib[l].x, lib[l].x + lib[l].y), indexed by f >> lib[l].z.
+// [lib[l].x, lib[l].x + lib[l].y), indexed by f >> lib[l].z; lib[l].w = the library's k in a mixed
+// batch (0: every library has k).
 struct BucketGeom {
     uint64_t f_lo;
     int shift;
@@ -81,7 +82,11 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr, uint64_t t_begin = 0,
-                  uint64_t t_end = ~0ull, const uint64_t *rid = nullptr, uint32_t rid_value = 0);
+                  uint64_t t_end = ~0ull, const uint64_t *rid = nullptr, uint32_t rid_value = 0,
+                  const int *lib_k = nullptr, int tag_shift = 0);
+// (lib_k: mixed batches, each library's k (device, n_libs entries); the library tag then sits at bit tag_shift.)
+// 64-bit keys of a mixed batch's libraries with k <= 32: out[i] <- in[i].lo.
+void launch_narrow_keys(const LaunchCfg &c, const Key128 *in, uint64_t n, uint64_t *out);
 // Range id of every valid window (two bits per position as two bit planes per 32 positions,
 // range_id_words(n_bases) words): group[part].
 uint64_t range_id_words(uint64_t n_bases);

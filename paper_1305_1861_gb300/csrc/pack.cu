@@ -269,6 +269,15 @@ void launch_batch_offsets(const LaunchCfg &c, const uint64_t *src, const uint64_
                                                                             dst, n_entries);
 }
 
+__global__ void k_narrow_keys(const Key128 *__restrict__ in, uint64_t n, uint64_t *__restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = in[i].lo;
+}
+
+void launch_narrow_keys(const LaunchCfg &c, const Key128 *in, uint64_t n, uint64_t *out) {
+    if (n) k_narrow_keys<<<grid_for(n, 256, c.sms, 8), 256, 0, c.stream>>>(in, n, out);
+}
+
 void launch_extract(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
                     uint64_t *keys) {
     if (k <= 32)

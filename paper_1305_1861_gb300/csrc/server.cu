@@ -6,10 +6,13 @@
 // executor is free it takes the oldest queued job whose footprint estimate fits what is left of
 // the budget, plus every other queued job with the same k and min_count that still fits (up to
 // max_batch jobs, and as many as the spare key bits can tag), and runs them as one batched
-// pipeline: each stage is one launch for all of them. A run's results are split and copied to
+// pipeline: each stage is one launch for all of them. With params.batch_mixed (1, or 0 when the
+// batched form's cost model expects it to pay) queued jobs of other k (at most 61) and the same
+// min_count join the run as a mixed run. A run's results are split and copied to
 // the host by the executor's copy-out thread while its next run executes. A job whose estimate
 // exceeds the whole budget is refused at submit time (TURTLE_E_BUSY). Results are exactly those
 // of turtle_count on the same reads.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -100,23 +103,40 @@ static void executor_loop(turtle_server *sv, Executor *ex) {
             return sv->in_use + sv->tickets[sv->queue.front()]->footprint <= sv->budget;  // admission
         });
         if (sv->stop) return;
-        // continuous batching: the oldest job and the queued jobs that can share its pipeline
+        // continuous batching: the oldest job and the queued jobs that can share its pipeline (the same
+        // k and min_count; in a mixed run any k <= MIXED_K_MAX with the same min_count)
         const turtle_job head = sv->tickets[sv->queue.front()]->job;
-        const size_t cap = std::min<size_t>((size_t)sv->max_batch, batch_capacity(head.k));
-        std::vector<uint64_t> ids, fps;
-        uint64_t room = sv->budget - sv->in_use;
-        for (auto it = sv->queue.begin(); it != sv->queue.end() && ids.size() < cap;) {
-            Ticket *t = sv->tickets[*it].get();
-            const bool same = t->job.k == head.k && t->job.min_count == head.min_count;
-            if ((ids.empty() || same) && t->footprint <= room) {
-                room -= t->footprint;
-                ids.push_back(*it);
-                fps.push_back(t->footprint);
-                it = sv->queue.erase(it);
-            } else {
-                ++it;
+        auto pick = [&](bool mixed, size_t cap, std::vector<uint64_t> &ids, std::vector<uint64_t> &fps) {
+            uint64_t room = sv->budget - sv->in_use;
+            for (uint64_t id : sv->queue) {
+                if (ids.size() >= cap) break;
+                const Ticket *t = sv->tickets[id].get();
+                const bool joins = mixed ? t->job.k <= MIXED_K_MAX && t->job.min_count == head.min_count
+                                         : t->job.k == head.k && t->job.min_count == head.min_count;
+                if ((ids.empty() || joins) && t->footprint <= room) {
+                    room -= t->footprint;
+                    ids.push_back(id);
+                    fps.push_back(t->footprint);
+                }
             }
+        };
+        std::vector<uint64_t> ids, fps;
+        bool mixed = false;
+        if (sv->params.batch_mixed != 2 && sv->params.compact == 0 && head.k <= MIXED_K_MAX) {
+            pick(true, std::min<size_t>((size_t)sv->max_batch, 64), ids, fps);
+            std::vector<turtle_job> js;
+            std::vector<size_t> idx;
+            bool several_k = false;
+            for (uint64_t id : ids) {
+                js.push_back(sv->tickets[id]->job);
+                idx.push_back(idx.size());
+                several_k |= js.back().k != head.k;
+            }
+            mixed = several_k && (sv->params.batch_mixed == 1 || mixed_runs_pay(js.data(), idx));
+            if (!mixed) ids.clear(), fps.clear();
         }
+        if (!mixed) pick(false, std::min<size_t>((size_t)sv->max_batch, batch_capacity(head.k)), ids, fps);
+        for (uint64_t id : ids) sv->queue.erase(std::find(sv->queue.begin(), sv->queue.end(), id));
         const double t0 = now_ms();
         std::vector<turtle_job> jobs(ids.size());
         for (size_t i = 0; i < ids.size(); i++) {
@@ -137,7 +157,7 @@ static void executor_loop(turtle_server *sv, Executor *ex) {
         std::vector<size_t> idx(ids.size());
         for (size_t i = 0; i < idx.size(); i++) idx[i] = i;
         const int rc = batch_run_jobs(ex->ctx, jobs.data(), idx, &sv->params, ex->stream, outs->data(), *ex->out,
-                                      [sv, ids, fps, outs](int r) { finish(sv, ids, fps, outs->data(), r); });
+                                      [sv, ids, fps, outs](int r) { finish(sv, ids, fps, outs->data(), r); }, mixed);
         if (rc) finish(sv, ids, fps, outs->data(), rc);  // nothing was posted
         lk.lock();
         sv->running_batches--;  // this run's device work is done (its copy-out may still be running)

@@ -103,3 +103,27 @@ def test_one_executor_runs_one_batch_at_a_time(have_gpu):
     st = srv.stats()
     srv.close()
     assert st["executors"] == 1 and st["peak_running_batches"] == 1 and st["batches"] == 4
+
+
+def test_queued_jobs_of_different_k_share_a_mixed_run(have_gpu):
+    """With batch_mixed = 1, queued jobs of different k (and the same min_count) join one run; every
+    result is still the oracle's."""
+    import paper_1305_1861_gb300 as pkg
+
+    big = synth.fly(seed=3, scale=0.05)  # keeps the one executor busy while the others queue
+    small = _jobs(8, seed=9)
+    ks = [15, 25, 31, 45] * 2
+    jobs = [(b, o, k, 2) for (b, o, _, _), k in zip(small, ks)]
+    srv = pkg.Server(0, hbm_budget_bytes=64 << 30, max_batch=8, params=pkg.Params.default(batch_mixed=1),
+                     executors=1)
+    t_big = srv.submit(big.bases, big.offsets, 31, 2)
+    tickets = [srv.submit(*j) for j in jobs]
+    srv.poll(t_big)
+    got = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 9 and st["failed"] == 0
+    assert st["largest_batch"] >= 3  # runs of one k would hold at most the two jobs of that k
+    for (b, o, k, m), (keys, counts, nw, _) in zip(jobs, got):
+        ok, oc, onw = oracle.count(b, o, k, m)
+        assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
