@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--l2-fetch", type=int, default=-1, help="L2 fetch granularity hint in bytes (-1 = default)")
     ap.add_argument("--recount-windows", action="store_true", help="recount by re-extracting every window")
     ap.add_argument("--member-filter", action="store_true", help="screen first sightings with a membership bitmap")
-    ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..3 (-1 = default)")
+    ap.add_argument("--sort-tile", type=int, default=-1, help="onesweep tile shape 0..4 (4: persistent, bulk-copied tiles; -1 = default)")
     ap.add_argument("--bucket-slots", type=int, default=0, help="bucket CTA table slots: 4096 or 8192 (0 = default)")
     ap.add_argument("--bucket-windows", type=int, default=0, help="windows per bucket, about (0 = default 16384)")
     ap.add_argument("--compact", type=int, default=-1,

@@ -216,11 +216,22 @@ const uint64_t *ctx_patterns(turtle_ctx *c, const turtle_params &p, cudaStream_t
 // pointer passes (the entry points check NULL separately).
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
+// params.sort_tile -> onesweep variant (keys per thread and CTAs per SM; 3 = persistent with bulk-copied
+// tiles). Default: variant 0 for the global sort, 1 for the bucket sort.
+int sort_variant(const turtle_params &p, bool bucket) {
+    switch (p.sort_tile) {
+    case 0: return bucket ? 1 : 0;
+    case 3: return 0;
+    case 4: return 3;
+    default: return (int)p.sort_tile;
+    }
+}
+
 bool params_ok(const turtle_params &p) {
     return (p.l2_fetch_bytes == 0 || (p.l2_fetch_bytes >= 32 && p.l2_fetch_bytes <= 128)) && p.pattern_bits >= 1 &&
            p.pattern_bits <= 64 && p.n_patterns >= 1 && p.n_patterns <= 4096 &&
            (p.n_patterns & (p.n_patterns - 1)) == 0 && p.filter_bits_per_window > 0.f &&
-           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 3 && p.compact <= 3 && p.hash_slots_log2 <= 40 &&
+           p.filter_bits_per_window <= 1024.f && p.sort_tile <= 4 && p.compact <= 3 && p.hash_slots_log2 <= 40 &&
            (p.bucket_slots == 0 || p.bucket_slots == 4096 || p.bucket_slots == 8192) &&
            p.shard_count <= TURTLE_PARTS && p.shard_index < (p.shard_count ? p.shard_count : 1) &&
            !(p.shard_count > 1 && p.compact == 3) && p.probe_order <= 1 &&
@@ -509,7 +520,7 @@ PartOut hashed_part(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats 
     tm.start(TURTLE_STAGE_SORT);
     int passes = 0;
     K *sorted = launch_radix_sort<K>(lc, kept, n_out, key_bits, ss, err, false, 0, &passes,
-                                     prm.sort_tile == 3 ? 0 : (int)prm.sort_tile);
+                                     sort_variant(prm, false));
     launch_hash_lookup<K>(lc, sorted, n_out, table, lines, ocounts, err);
     tm.stop(TURTLE_STAGE_SORT);
     st.sort_passes = (uint32_t)passes;
@@ -700,7 +711,7 @@ void run_lazy(turtle_ctx *c, const LaunchCfg &lc, Timer &tm, turtle_stats &st, c
     K *R = nullptr;
     uint32_t *Rc = nullptr;
     uint64_t nR = 0;
-    const int variant = prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile);
+    const int variant = sort_variant(prm, true);
     for (uint64_t t0 = 0; t0 < all_tiles; t0 += tiles) {
         const uint64_t t1 = std::min(all_tiles, t0 + tiles);
         ck(cudaMemsetAsync(ctr + C_CAND, 0, 8 * (C_N - C_CAND), s));
@@ -1067,7 +1078,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         if (bucketed) {
             po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, const_cast<K *>(first_keys), n_first, bg,
                                   bucket_bits, hist, !parted,
-                                  prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
+                                  sort_variant(prm, true),
                                   prm.bucket_slots != 4096, s, bin_keys);
         } else if (hashed) {
             po = hashed_part<K>(c, lc, tm, st, min_count, cand, n_cand, first_keys, n_first, key_bits,
@@ -1087,7 +1098,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         tm.start(TURTLE_STAGE_SORT);
         int passes_run = 0;
         K *sorted = launch_radix_sort<K>(lc, cand, n_cand, key_bits, ss, err, true, skip, &passes_run,
-                                         prm.sort_tile == 3 ? 0 : (int)prm.sort_tile);
+                                         sort_variant(prm, false));
         tm.stop(TURTLE_STAGE_SORT);
         st.sort_passes = (uint32_t)passes_run;
         st.stage_launches[TURTLE_STAGE_SORT] += n_cand > 1 ? passes_run + 1 : 0;
@@ -1674,7 +1685,7 @@ void run_count_overlapped(turtle_ctx *c, const std::vector<HostPiece> &pieces, u
     out.n_windows = W;
     const PartOut po = bucketed_part<K>(c, lc, tm, st, min_count, cand, n_cand, use_filter ? cand + (Wmax - n_first) : nullptr,
                                         n_first, bg, bucket_bits, hist, true,
-                                        prm.sort_tile == 0 ? 1 : (prm.sort_tile == 3 ? 0 : (int)prm.sort_tile),
+                                        sort_variant(prm, true),
                                         prm.bucket_slots != 4096, s);
     out.keys = po.keys;
     out.counts = po.counts;

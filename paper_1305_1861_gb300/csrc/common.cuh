@@ -14,6 +14,7 @@ enum : uint32_t {
     ERR_BAD_OFFSETS = 16u,    // offsets not monotone or past n_bases
     ERR_NOT_FOUND = 32u,      // threshold lookup missed a key that was inserted
     ERR_PART_MISMATCH = 64u,  // a window's key-range test disagreed with its canonical key's range
+    ERR_BULK_WAIT = 128u,     // a bulk copy into shared memory did not complete within its wait limit
 };
 
 constexpr int WARP = 32;

@@ -24,16 +24,21 @@ constexpr int MAX_PASSES = 16;
 // Variant 0 is the default; the others trade tile size against occupancy.
 template <class K> struct SortCfg;
 constexpr int min3(const int (&v)[3]) { return v[0] < v[1] ? (v[0] < v[2] ? v[0] : v[2]) : (v[1] < v[2] ? v[1] : v[2]); }
+// Variant 3 (BULK_VARIANT) is the persistent form with bulk-copied tiles, BULK_ITEMS keys per thread,
+// 2 CTAs/SM.
 template <> struct SortCfg<uint64_t> {
     static constexpr int V_ITEMS[3] = {32, 16, 24};  // default: 8192 keys (64 KB) per tile, 2 CTAs/SM
     static constexpr int V_MINB[3] = {2, 4, 2};
+    static constexpr int BULK_ITEMS = 16;
     static constexpr int MIN_TILE = 256 * min3(V_ITEMS);  // sizes the look-back status array
 };
 template <> struct SortCfg<Key128> {
     static constexpr int V_ITEMS[3] = {16, 8, 12};   // default: 4096 keys (64 KB) per tile
     static constexpr int V_MINB[3] = {2, 3, 2};
+    static constexpr int BULK_ITEMS = 8;
     static constexpr int MIN_TILE = 256 * min3(V_ITEMS);
 };
+constexpr int BULK_VARIANT = 3;
 
 int sort_passes_for(int key_bits) { return (key_bits + 7) / 8; }
 
@@ -75,35 +80,37 @@ __global__ void k_scan_bins(uint64_t *hist) {
     h[threadIdx.x] = s[threadIdx.x];
 }
 
+// Shared state of one onesweep tile, besides the staged keys and their digits.
+struct OsShared {
+    uint32_t whist[S_WARPS][BINS];  // per-warp digit counters
+    uint32_t texcl[BINS];
+    uint64_t glob[BINS];
+    uint32_t scan[S_WARPS];
+    uint32_t uniform;
+};
+
+// One onesweep tile: keys src[0 .. min(TILE, n - start)) (global memory, or a shared-memory copy) are
+// ranked by digit into skeys/sdig and scattered to out. On entry sh.whist is zero and a barrier has
+// passed since; skeys may be the buffer src points into (every read of src ends before the first
+// barrier here, every write of skeys comes after it). The caller synchronises before reusing skeys,
+// sdig or sh.
+//
 // STABLE = false: the first pass of a sort, whose input order carries no information. Each key
 // then takes its place with one shared-memory atomic on its warp's digit counter, in any order
 // among the warp's keys of the same digit, without the warp match and broadcast.
-template <class K, int ITEMS, int MINB, class D, bool STABLE>
-__global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
-                                                            int shift, const uint64_t *__restrict__ bin_base,
-                                                            uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
-                                                            uint32_t *err, D digit) {
+template <class K, int ITEMS, class D, bool STABLE>
+__device__ __forceinline__ void onesweep_tile(const K *src, uint64_t start, uint64_t n, K *skeys, uint8_t *sdig,
+                                              OsShared &sh, K *__restrict__ out, int shift,
+                                              const uint64_t *__restrict__ bin_base, uint64_t *lookback,
+                                              uint64_t tile, uint32_t epoch, uint32_t *err, D digit) {
     constexpr int TILE = S_BLOCK * ITEMS;
-    extern __shared__ __align__(16) unsigned char os_smem[];
-    K *skeys = reinterpret_cast<K *>(os_smem);  // TILE keys (dynamic: up to 64 KB)
-    __shared__ uint8_t sdig[TILE];  // digit of each staged key: the scatter does not recompute it
-    __shared__ uint32_t whist[S_WARPS][BINS];
-    __shared__ uint32_t s_texcl[BINS];
-    __shared__ uint64_t s_glob[BINS];
-    __shared__ uint32_t s_scan[S_WARPS];
-    __shared__ uint32_t s_tile, s_uniform;
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < S_WARPS * BINS; i += S_BLOCK) (&whist[0][0])[i] = 0;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // tiles start in launch order: look-back always progresses
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    const uint64_t start = tile * TILE;
-    const uint64_t wstart = start + (uint64_t)warp * ITEMS * WARP;  // warp w owns a contiguous run of the tile
+    const uint32_t wofs = (uint32_t)warp * ITEMS * WARP;  // warp w owns a contiguous run of the tile
     const uint32_t lt = lanemask_lt();
 
     // A full tile (every tile but the last) needs no bounds checks.
     const bool full = start + TILE <= n;
+    const uint64_t wstart = start + wofs;
     const uint32_t n_in_warp = full ? (uint32_t)(ITEMS * WARP)
                                     : (uint32_t)(wstart >= n ? 0 : (n - wstart < (uint64_t)ITEMS * WARP ? n - wstart
                                                                                                        : ITEMS * WARP));
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
         const uint32_t r = (uint32_t)(i * WARP + lane);
-        if (full || r < n_in_warp) key[i] = in[wstart + r];
+        if (full || r < n_in_warp) key[i] = src[wofs + r];
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
@@ -126,27 +133,28 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     // relative order (equal digits there mean equal sort keys so far), and the tile ranks like a
     // first pass: one shared atomic per key.
     if (STABLE && tid == 0) {
-        const uint64_t last = (full ? start + TILE : n) - 1;
-        s_uniform = digit.same_low(in[start], in[last], shift) ? 1u : 0u;
+        const uint64_t last = (full ? TILE : n - start) - 1;
+        sh.uniform = digit.same_low(src[0], src[last], shift) ? 1u : 0u;
     }
     // 1. early counts: per-warp digit counts (order-free shared atomics)
 #pragma unroll
     for (int i = 0; i < ITEMS; i++)
-        if (full || (uint32_t)(i * WARP + lane) < n_in_warp) atomicAdd(&whist[warp][(dig[i >> 2] >> (8 * (i & 3))) & 0xffu], 1u);
+        if (full || (uint32_t)(i * WARP + lane) < n_in_warp)
+            atomicAdd(&sh.whist[warp][(dig[i >> 2] >> (8 * (i & 3))) & 0xffu], 1u);
     __syncthreads();
     // 2. thread tid owns digit tid: tile count, publish it, tile-local start, per-warp starts
     uint32_t tcount = 0;
 #pragma unroll
-    for (int w = 0; w < S_WARPS; w++) tcount += whist[w][tid];
+    for (int w = 0; w < S_WARPS; w++) tcount += sh.whist[w][tid];
     if (tile > 0) st_relaxed(lookback + tile * BINS + tid, lb_pack(LB_AGG, epoch, tcount));
-    const uint32_t texcl = block_exclusive_scan<S_BLOCK>(tcount, s_scan, nullptr);
-    s_texcl[tid] = texcl;
+    const uint32_t texcl = block_exclusive_scan<S_BLOCK>(tcount, sh.scan, nullptr);
+    sh.texcl[tid] = texcl;
     {
         uint32_t run = texcl;
 #pragma unroll
         for (int w = 0; w < S_WARPS; w++) {
-            const uint32_t v = whist[w][tid];
-            whist[w][tid] = run;
+            const uint32_t v = sh.whist[w][tid];
+            sh.whist[w][tid] = run;
             run += v;
         }
     }
@@ -154,13 +162,13 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     // 3. ranking straight into shared memory. Unstable (a first pass, or a tile with one value of
     //    the lower digits): one shared atomic per key. Stable: rows in order, lanes in order within
     //    a row, equal digits found by ballots.
-    const bool by_atomics = !STABLE || s_uniform;  // read after the barriers that follow its write
+    const bool by_atomics = !STABLE || sh.uniform;  // read after the barriers that follow its write
     if (by_atomics) {
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             if (full || (uint32_t)(i * WARP + lane) < n_in_warp) {
                 const uint32_t d = (dig[i >> 2] >> (8 * (i & 3))) & 0xffu;
-                const uint32_t pos = atomicAdd(&whist[warp][d], 1u);
+                const uint32_t pos = atomicAdd(&sh.whist[warp][d], 1u);
                 skeys[pos] = key[i];
                 sdig[pos] = (uint8_t)d;
             }
@@ -182,9 +190,9 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
             // it by the group size (one writer per digit: the warp owns its counters).
             const int leader = 31 - __clz(peers);
             uint32_t pos = 0;
-            if (valid) pos = whist[warp][d];
+            if (valid) pos = sh.whist[warp][d];
             __syncwarp();
-            if (valid && lane == leader) whist[warp][d] = pos + (uint32_t)__popc(peers);
+            if (valid && lane == leader) sh.whist[warp][d] = pos + (uint32_t)__popc(peers);
             __syncwarp();
             if (valid) {
                 skeys[pos + __popc(peers & lt)] = key[i];
@@ -194,25 +202,183 @@ __global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict_
     }
     // 4. global offsets of this tile's digits (predecessors have usually published by now)
     const uint64_t excl = lookback_prefix(lookback + tid, BINS, tile, tcount, epoch, err);
-    s_glob[tid] = bin_base[tid] + excl - texcl;
+    sh.glob[tid] = bin_base[tid] + excl - texcl;
     __syncthreads();
     if (full) {
 #pragma unroll 4
         for (uint32_t p = tid; p < (uint32_t)TILE; p += S_BLOCK) {
-            out[s_glob[sdig[p]] + p] = skeys[p];
+            out[sh.glob[sdig[p]] + p] = skeys[p];
         }
     } else {
         const uint32_t tile_n = (uint32_t)(n - start);
         for (uint32_t p = tid; p < tile_n; p += S_BLOCK) {
-            out[s_glob[sdig[p]] + p] = skeys[p];
+            out[sh.glob[sdig[p]] + p] = skeys[p];
         }
+    }
+}
+
+// One CTA per tile, the tile's keys loaded by its threads.
+template <class K, int ITEMS, int MINB, class D, bool STABLE>
+__global__ void __launch_bounds__(S_BLOCK, MINB) k_onesweep(const K *__restrict__ in, K *__restrict__ out, uint64_t n,
+                                                            int shift, const uint64_t *__restrict__ bin_base,
+                                                            uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
+                                                            uint32_t *err, D digit) {
+    constexpr int TILE = S_BLOCK * ITEMS;
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    K *skeys = reinterpret_cast<K *>(os_smem);  // TILE keys (dynamic: up to 64 KB)
+    __shared__ uint8_t sdig[TILE];  // digit of each staged key: the scatter does not recompute it
+    __shared__ OsShared sh;
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < S_WARPS * BINS; i += S_BLOCK) (&sh.whist[0][0])[i] = 0;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // tiles start in launch order: look-back always progresses
+    __syncthreads();
+    const uint64_t tile = s_tile, start = tile * TILE;
+    onesweep_tile<K, ITEMS, D, STABLE>(in + start, start, n, skeys, sdig, sh, out, shift, bin_base, lookback, tile,
+                                       epoch, err, digit);
+}
+
+// ---------------------------------------------------------------- bulk-copy (TMA) tile loads
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Make the barriers' initialisation visible to the copy engine.
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Order this thread's earlier generic accesses of shared memory before later bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to shared memory,
+// completing on `bar`, which expects this many bytes in its current phase.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// Wait until `bar` has completed the phase of the given parity: at most `limit` polls, each of
+// which may suspend the thread for a short, hardware-defined time. False when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr uint32_t BULK_WAIT_LIMIT = 1u << 22;
+constexpr uint32_t NO_BULK = ~0u;
+
+// Persistent form: each CTA takes tiles by ticket, and while it ranks and scatters one tile the copy
+// engine already loads its next one into the other of two shared-memory buffers (cp.async.bulk,
+// completion counted on an mbarrier), so the next tile's loads do not wait for this one's scatter. A
+// tile is taken before the one it prefetches is processed and every CTA processes its current tile
+// before its prefetched one, so the lowest unfinished ticket is always some CTA's current tile and the
+// look-back chain always progresses. The buffer a tile was loaded into also stages its ranked keys.
+// Bulk copies need 16-byte aligned addresses: a tile of 64-bit keys that starts between two 16-byte
+// boundaries is copied from the boundary below, one key earlier; the first and the last full tile,
+// where that could read outside the keys, and a partial last tile are loaded by the threads.
+template <class K, int ITEMS, class D, bool STABLE>
+__global__ void __launch_bounds__(S_BLOCK, 2) k_onesweep_bulk(const K *__restrict__ in, K *__restrict__ out,
+                                                              uint64_t n, int shift,
+                                                              const uint64_t *__restrict__ bin_base,
+                                                              uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch,
+                                                              uint32_t *err, D digit) {
+    constexpr int TILE = S_BLOCK * ITEMS;
+    constexpr int SLACK = 16 / (int)sizeof(K) - 1;  // keys before and after a tile copied from a boundary
+    constexpr int BUF = TILE + 2 * SLACK;
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    K *buf[2] = {reinterpret_cast<K *>(os_smem), reinterpret_cast<K *>(os_smem) + BUF};
+    uint8_t *sdig = reinterpret_cast<uint8_t *>(reinterpret_cast<K *>(os_smem) + 2 * BUF);
+    __shared__ OsShared sh;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_tile[2], s_off[2];  // tile staged in each buffer; its key offset, or NO_BULK
+    const int tid = threadIdx.x;
+    const uint64_t tiles = (n + TILE - 1) / TILE;
+
+    // tid 0: take the next ticket into buffer b and start its copy (full tiles whose aligned span
+    // stays inside the keys)
+    auto stage = [&](int b) {
+        const uint32_t t = atomicAdd(tile_ctr, 1u);
+        uint32_t how = NO_BULK;
+        if (t < tiles) {
+            const uint64_t start = (uint64_t)t * TILE;
+            const uint32_t off = (uint32_t)((reinterpret_cast<uintptr_t>(in + start) & 15) / sizeof(K));
+            const uint32_t bytes = (uint32_t)(((uint64_t)(TILE + off) * sizeof(K) + 15) & ~(uint64_t)15);
+            const bool aligned = (reinterpret_cast<uintptr_t>(in + (start - off)) & 15) == 0;
+            if (aligned && start >= off && start - off + bytes / sizeof(K) <= n) {
+                bulk_load(buf[b], in + (start - off), bytes, &s_bar[b]);
+                how = off;
+            }
+        }
+        s_tile[b] = t;
+        s_off[b] = how;
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_init_fence();
+        stage(0);
+    }
+    uint32_t parity = 0;  // bit b: parity of buffer b's next phase
+    int cur = 0;
+    for (;;) {
+        for (int i = tid; i < S_WARPS * BINS; i += S_BLOCK) (&sh.whist[0][0])[i] = 0;
+        __syncthreads();  // the previous tile is done with every buffer and with sh; s_tile/s_off visible
+        const uint32_t t = s_tile[cur], off = s_off[cur];
+        if (t >= tiles) break;  // nothing was copied for a ticket past the last tile
+        if (tid == 0) stage(cur ^ 1);  // buffer cur ^ 1 held the previous tile, now finished
+        const uint64_t start = (uint64_t)t * TILE;
+        const K *src = in + start;
+        if (off != NO_BULK) {
+            const bool ok = mbar_wait(&s_bar[cur], (parity >> cur) & 1u, BULK_WAIT_LIMIT);
+            parity ^= 1u << cur;
+            if (__syncthreads_or(!ok)) {  // a copy did not land in time: flag it, let the copies end, stop
+                if (tid == 0) {
+                    atomicOr(err, ERR_BULK_WAIT);
+                    mbar_wait(&s_bar[cur], ((parity >> cur) & 1u) ^ 1u, BULK_WAIT_LIMIT);
+                    if (s_off[cur ^ 1] != NO_BULK)  // the prefetch this thread started above
+                        mbar_wait(&s_bar[cur ^ 1], (parity >> (cur ^ 1)) & 1u, BULK_WAIT_LIMIT);
+                }
+                return;
+            }
+            src = buf[cur] + off;
+        }
+        onesweep_tile<K, ITEMS, D, STABLE>(src, start, n, buf[cur], sdig, sh, out, shift, bin_base, lookback, t,
+                                           epoch, err, digit);
+        fence_proxy_async_smem();  // this thread's accesses of buf[cur] come before the copy that reuses it
+        cur ^= 1;
     }
 }
 
 template <class K, int V, class D, bool STABLE>
 static void onesweep_launch(const LaunchCfg &c, const K *src, K *dst, uint64_t n, int shift, const uint64_t *bin_base,
                             uint64_t *lookback, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err, D digit) {
-    constexpr int ITEMS = SortCfg<K>::V_ITEMS[V], MINB = SortCfg<K>::V_MINB[V];
+    if constexpr (V == BULK_VARIANT) {
+        constexpr int ITEMS = SortCfg<K>::BULK_ITEMS, TILE = S_BLOCK * ITEMS;
+        static_assert(TILE >= SortCfg<K>::MIN_TILE, "look-back array sized for larger tiles");
+        const uint64_t tiles = (n + TILE - 1) / TILE;
+        const size_t smem = 2 * sizeof(K) * (TILE + 2 * (16 / sizeof(K) - 1)) + TILE;
+        auto kern = k_onesweep_bulk<K, ITEMS, D, STABLE>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S_BLOCK, smem);
+        if (per_sm < 1) per_sm = 1;
+        const uint64_t cap = (uint64_t)c.sms * per_sm;
+        kern<<<(int)(tiles < cap ? tiles : cap), S_BLOCK, smem, c.stream>>>(src, dst, n, shift, bin_base, lookback,
+                                                                           tile_ctr, epoch, err, digit);
+        return;
+    }
+    constexpr int VV = V < 3 ? V : 0;
+    constexpr int ITEMS = SortCfg<K>::V_ITEMS[VV], MINB = SortCfg<K>::V_MINB[VV];
     static_assert(S_BLOCK * ITEMS >= SortCfg<K>::MIN_TILE, "look-back array sized for larger tiles");
     const uint64_t tiles = (n + S_BLOCK * ITEMS - 1) / (S_BLOCK * ITEMS);
     const size_t smem = sizeof(K) * S_BLOCK * ITEMS;
@@ -236,8 +402,9 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
     const int passes = sort_passes_for(key_bits);
     if (passes_run) *passes_run = 0;
     if (n <= 1 || passes == 0) return keys;
-    if (variant < 0 || variant > 2) variant = 0;
-    const uint64_t TILE = (uint64_t)S_BLOCK * SortCfg<K>::V_ITEMS[variant];
+    if (variant < 0 || variant > BULK_VARIANT) variant = 0;
+    const uint64_t TILE = (uint64_t)S_BLOCK * (variant == BULK_VARIANT ? SortCfg<K>::BULK_ITEMS
+                                                                       : SortCfg<K>::V_ITEMS[variant]);
     const uint64_t tiles = (n + TILE - 1) / TILE;
     cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
     cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
@@ -252,7 +419,10 @@ K *launch_radix_sort(const LaunchCfg &c, K *keys, uint64_t n, int key_bits, cons
     int done = 0;  // the first pass run needs no stability: the input order carries no information
     for (int p = 0; p < passes; p++) {
         if ((skip_mask >> p) & 1u) continue;  // every key has the same digit here: the pass would be a copy
-        auto pass = variant == 0 ? onesweep_pass<K, 0> : (variant == 1 ? onesweep_pass<K, 1> : onesweep_pass<K, 2>);
+        auto pass = variant == 0   ? onesweep_pass<K, 0>
+                    : variant == 1 ? onesweep_pass<K, 1>
+                    : variant == 2 ? onesweep_pass<K, 2>
+                                   : onesweep_pass<K, BULK_VARIANT>;
         pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err,
              RawDigit<K>{}, done > 0);
         done++;
@@ -272,9 +442,10 @@ K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom 
     const int passes = (bits + 7) / 8;
     if (passes_run) *passes_run = 0;
     if (n <= 1 || passes == 0) return keys;
-    if (variant < 0 || variant > 2) variant = 0;
+    if (variant < 0 || variant > BULK_VARIANT) variant = 0;
     const BucketDigit<K> dig{g};
-    const uint64_t TILE = (uint64_t)S_BLOCK * SortCfg<K>::V_ITEMS[variant];
+    const uint64_t TILE = (uint64_t)S_BLOCK * (variant == BULK_VARIANT ? SortCfg<K>::BULK_ITEMS
+                                                                       : SortCfg<K>::V_ITEMS[variant]);
     const uint64_t tiles = (n + TILE - 1) / TILE;
     cudaMemsetAsync(s.tile_ctr, 0, sizeof(uint32_t) * (MAX_PASSES + 2), c.stream);
     cudaMemsetAsync(s.lookback, 0, sizeof(uint64_t) * tiles * BINS, c.stream);
@@ -287,8 +458,10 @@ K *launch_bucket_sort(const LaunchCfg &c, K *keys, uint64_t n, const BucketGeom 
     k_scan_bins<<<passes, BINS, 0, c.stream>>>(s.hist);
     K *src = keys, *dst = reinterpret_cast<K *>(s.alt);
     for (int p = 0; p < passes; p++) {
-        auto pass = variant == 0 ? onesweep_pass<K, 0, BucketDigit<K>>
-                                 : (variant == 1 ? onesweep_pass<K, 1, BucketDigit<K>> : onesweep_pass<K, 2, BucketDigit<K>>);
+        auto pass = variant == 0   ? onesweep_pass<K, 0, BucketDigit<K>>
+                    : variant == 1 ? onesweep_pass<K, 1, BucketDigit<K>>
+                    : variant == 2 ? onesweep_pass<K, 2, BucketDigit<K>>
+                                   : onesweep_pass<K, BULK_VARIANT, BucketDigit<K>>;
         pass(c, src, dst, n, 8 * p, s.hist + (uint64_t)p * BINS, s.lookback, s.tile_ctr + p, (uint32_t)(p + 1), err,
              dig, p > 0);
         if (passes_run) (*passes_run)++;

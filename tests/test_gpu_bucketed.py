@@ -25,8 +25,9 @@ def ctx(have_gpu):
     c.close()
 
 
-# (compact, bucket_slots, sort_tile): bucketed with both table sizes and two tile shapes, global, hash table
-FORMS = [(0, 0, 0), (0, 8192, 3), (1, 0, 0), (2, 0, 0)]
+# (compact, bucket_slots, sort_tile): bucketed with both table sizes and three tile shapes (4: persistent
+# sort with bulk-copied tiles), global (with both tile loads), hash table
+FORMS = [(0, 0, 0), (0, 8192, 3), (0, 0, 4), (1, 0, 0), (1, 0, 4), (2, 0, 0)]
 
 
 def _run(ctx, bases, offs, k, min_count, form):

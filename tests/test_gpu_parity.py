@@ -374,3 +374,18 @@ def test_trim_gives_back_cached_memory_and_calls_still_work(have_gpu):
     assert free_after > free_before + (256 << 20)  # the internal context's pool held its scratch between calls
     keys, counts, _ = pkg.turtle_count(lib.bases, lib.offsets, 31, 2)
     assert np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+
+
+# ---------------------------------------------------------------- persistent sort with bulk-copied tiles
+@pytest.mark.parametrize("k", [21, 31, 45, 64])
+@pytest.mark.parametrize("compact", [0, 1])
+@pytest.mark.parametrize("genome", [3_000, 60_000, 700_000])
+def test_bulk_copied_sort_tiles_match_oracle(ctx, k, compact, genome):
+    """sort_tile = 4: one tile or many, the first and last full tiles loaded by the threads, a ragged last
+    tile, first sightings starting between two 16-byte boundaries (64-bit keys), both key widths."""
+    import paper_1305_1861_gb300 as pkg
+
+    g = synth.genome_iid(900 + genome + k, genome)
+    b, o = synth.reads_uniform(g, 901 + k, max(1, int(12 * genome / 120)), 120, 0.01)
+    st = _check_count(ctx, b, o, k, 2, pkg.Params.default(compact=compact, sort_tile=4))
+    assert st["n_candidates"] > 0
