@@ -992,18 +992,20 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
     }
     const bool parted = groups.size() > 1 || sharded;
     st.super_partitions = (uint32_t)groups.size();
-    // With two to four key ranges, one pass writes each window's range id (two bits per position) and
-    // each range's pass 1 selects its windows from those bits; with more, each pass 1 tests every window.
+    // With two to four key ranges, the first range's pass 1 also writes each window's range id (two bits
+    // per position) and the other ranges' passes select their windows from those bits; with more, each
+    // pass 1 tests every window. (The filter-blocked pass 1 tests every window itself.)
+    const bool binned_mode = bucketed && !tag && use_filter && firsts_mode && prm.probe_order == 1;
     uint64_t *rid = nullptr;
-    if (groups.size() >= 2 && groups.size() <= 4 && use_filter) {
+    uint8_t *d_pg = nullptr;
+    bool rid_written = false;
+    if (groups.size() >= 2 && groups.size() <= 4 && use_filter && !binned_mode) {
         std::vector<uint8_t> pg(1u << PART_BITS, 0);
         for (size_t g = 0; g < groups.size(); g++)
             for (uint32_t p = groups[g].first; p < groups[g].second; p++) pg[p] = (uint8_t)g;
-        uint8_t *d_pg = (uint8_t *)ctx_alloc(c, pg.size(), s);
+        d_pg = (uint8_t *)ctx_alloc(c, pg.size(), s);
         ck(cudaMemcpyAsync(d_pg, pg.data(), pg.size(), cudaMemcpyHostToDevice, s));
         rid = (uint64_t *)ctx_alloc(c, 8 * range_id_words(n_bases), s);
-        launch_range_ids<K>(lc, L, k, P, V, PART_BITS, d_pg, rid);
-        st.stage_launches[TURTLE_STAGE_VALID] += 1;
     }
 
     std::vector<PartOut> outs;
@@ -1048,7 +1050,7 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
         const uint64_t cand_cap = inj_cap && inj_cap < Wg ? inj_cap : Wg;
         // filter-blocked pass 1: the windows' keys are binned into what becomes the bucket sort's second
         // buffer (the bins are dead once probed), so it costs no memory
-        const bool binned = bucketed && !tag && use_filter && firsts_mode && prm.probe_order == 1;
+        const bool binned = binned_mode;
         K *bin_keys = nullptr;
         if (binned) {
             bin_keys = (K *)ctx_alloc(c, sizeof(K) * Wg, s);
@@ -1058,11 +1060,15 @@ void run_count(turtle_ctx *c, const uint8_t *bases, uint64_t n_bases, const uint
                                    groups[g].second, err, &bg);
             st.stage_launches[TURTLE_STAGE_FILTER] += 3;  // + the bin-offset scan, counted with the filter stage
         } else {
+            // the first range to run writes the range ids that the later ones read
+            const bool write_rid = rid && !rid_written;
             launch_pass1<K>(lc, L, k, P, V, use_filter, fg, cand, ctr + C_CAND, cand_cap, firsts, ctr + C_FIRST, Wg,
                             hist, hist_passes, parted ? PART_BITS : 0, groups[g].first, groups[g].second,
                             tag ? tag->lib_starts : nullptr, tag ? tag->n_libs : 0, lib_filter, err,
-                            bucketed ? &bg : nullptr, 0, ~0ull, rid, (uint32_t)g, tag ? tag->lib_k : nullptr,
-                            tag ? tag->tag_shift : 0);
+                            bucketed ? &bg : nullptr, 0, ~0ull, write_rid ? nullptr : rid, (uint32_t)g,
+                            tag ? tag->lib_k : nullptr, tag ? tag->tag_shift : 0, write_rid ? rid : nullptr,
+                            write_rid ? d_pg : nullptr);
+            rid_written |= write_rid;
         }
         tm.stop(TURTLE_STAGE_FILTER);
         st.stage_launches[TURTLE_STAGE_FILTER] += 1;

@@ -392,9 +392,10 @@ template void launch_part_count<Key128>(const LaunchCfg &, const PackLayout &, i
                                         const uint64_t *, int, unsigned long long *);
 
 // Key range of every window, two bits per position, for up to four ranges: range id = group[part of the
-// window's key]. Word w covers positions 32w .. 32w+31 as two bit planes: bit j of its low half is the
-// low bit of position 32w + j's id, bit j of its high half the high bit. Each range's pass 1 then
-// selects its windows from these words and the validity bitmap, without computing any other key.
+// window's key], written by the first range's pass 1. Word w covers positions 32w .. 32w+31 as two bit
+// planes: bit j of its low half is the low bit of position 32w + j's id, bit j of its high half the high
+// bit. The other ranges' passes select their windows from these words and the validity bitmap, without
+// computing any other key.
 constexpr int MAX_PARTS = 64;  // key-range parts of a library (part_bits <= 6)
 
 __device__ __forceinline__ uint32_t range_id_of(const uint64_t *__restrict__ rid, uint64_t s) {
@@ -403,46 +404,6 @@ __device__ __forceinline__ uint32_t range_id_of(const uint64_t *__restrict__ rid
     return (uint32_t)(((w >> j) & 1u) | (((w >> (32 + j)) & 1u) << 1));
 }
 
-template <class K>
-__global__ void __launch_bounds__(256) k_range_ids(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
-                                                   uint64_t n_pos, int k, int part_bits,
-                                                   const uint8_t *__restrict__ part_group, uint64_t *rid) {
-    __shared__ uint8_t s_pg[MAX_PARTS];
-    for (int i = threadIdx.x; i < (1 << part_bits); i += blockDim.x) s_pg[i] = part_group[i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t tiles = (n_pos + P1_TILE - 1) / P1_TILE;
-    for (uint64_t t = (uint64_t)blockIdx.x * 8 + warp; t < tiles; t += (uint64_t)gridDim.x * 8) {
-        const uint64_t base = t * P1_TILE;
-        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
-        uint32_t g[P1_ILP];  // all four windows' tests first, so their loads overlap; then the ballots
-#pragma unroll
-        for (int i = 0; i < P1_ILP; i++) {
-            const int r = lane + WARP * i;
-            const uint64_t s = base + r;
-            g[i] = 0;
-            if (s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1)) g[i] = s_pg[window_part<K>(P, s, k, part_bits)];
-        }
-#pragma unroll
-        for (int i = 0; i < P1_ILP; i++) {
-            const uint32_t lo = __ballot_sync(FULL, g[i] & 1u), hi = __ballot_sync(FULL, (g[i] >> 1) & 1u);
-            if (lane == 0) rid[4 * t + i] = (uint64_t)lo | ((uint64_t)hi << 32);
-        }
-    }
-}
-
-template <class K>
-void launch_range_ids(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
-                      int part_bits, const uint8_t *part_group, uint64_t *rid) {
-    const uint64_t tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
-    const uint64_t need = (tiles + 7) / 8, cap = (uint64_t)c.sms * 8;
-    k_range_ids<K><<<(int)(need < cap ? (need ? need : 1) : cap), 256, 0, c.stream>>>(P, V, L.n_bases, k, part_bits,
-                                                                                   part_group, rid);
-}
-template void launch_range_ids<uint64_t>(const LaunchCfg &, const PackLayout &, int, const uint64_t *,
-                                         const uint64_t *, int, const uint8_t *, uint64_t *);
-template void launch_range_ids<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
-                                       int, const uint8_t *, uint64_t *);
 uint64_t range_id_words(uint64_t n_bases) { return 4 * ((n_bases + P1_TILE - 1) / P1_TILE) + 4; }
 
 template <class K>
@@ -475,7 +436,7 @@ __global__ void __launch_bounds__(256) k_filter_keys(const K *__restrict__ keys,
 // full key; the probe phase checks every key against the range once more.
 constexpr int PQ_CAP = 2 * P1_TILE;  // queue of in-range positions per warp: one tile's worth beyond a full batch
 
-template <class K, bool EMIT_FIRSTS, bool BY_BUCKET>
+template <class K, bool EMIT_FIRSTS, bool BY_BUCKET, bool WRITE_RID>
 __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__restrict__ P, const uint64_t *__restrict__ V,
                                                           uint64_t n_pos, int k, uint64_t *filter, int sector_shift,
                                                           const uint64_t *__restrict__ patterns, uint32_t pat_mask,
@@ -484,6 +445,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
                                                           uint64_t first_cap, uint64_t *hist, int hist_passes,
                                                           int part_bits, uint32_t part_lo, uint32_t part_hi,
                                                           const uint64_t *__restrict__ rid, uint32_t rid_value,
+                                                          uint64_t *rid_out, const uint8_t *__restrict__ part_group,
                                                           BucketGeom bg, uint64_t t_begin, uint64_t t_end,
                                                           uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -494,8 +456,11 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_queue + PQ_CAP * P1_WARPS);
     uint32_t *s_fhist = s_hist + 256 * hist_passes;
     uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
+    __shared__ uint8_t s_pg[MAX_PARTS];  // WRITE_RID: range of each key-range part
     for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
     for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK) s_hist[i] = 0;
+    if (WRITE_RID)
+        for (int i = threadIdx.x; i < (1 << part_bits); i += P1_BLOCK) s_pg[i] = part_group[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
@@ -567,16 +532,33 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
         const uint64_t base = t * P1_TILE;
         const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
         bool in[P1_ILP];  // all four windows' tests first, so their loads overlap; then the ballots
+        if (WRITE_RID) {  // the first range's pass: every window's range id, written for the later passes
+            uint32_t g[P1_ILP];
 #pragma unroll
-        for (int i = 0; i < P1_ILP; i++) {
-            const int r = lane + WARP * i;
-            const uint64_t s = base + r;
-            in[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
-            if (in[i] && rid) {  // the window's range id, written by k_range_ids
-                in[i] = range_id_of(rid, s) == rid_value;
-            } else if (in[i]) {
-                const uint32_t pt = window_part<K>(P, s, k, part_bits);
-                in[i] = pt >= part_lo && pt < part_hi;
+            for (int i = 0; i < P1_ILP; i++) {
+                const int r = lane + WARP * i;
+                const uint64_t s = base + r;
+                const bool valid = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
+                g[i] = valid ? s_pg[window_part<K>(P, s, k, part_bits)] : 0u;
+                in[i] = valid && g[i] == rid_value;
+            }
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++) {
+                const uint32_t lo = __ballot_sync(FULL, g[i] & 1u), hi = __ballot_sync(FULL, (g[i] >> 1) & 1u);
+                if (lane == 0) rid_out[4 * t + i] = (uint64_t)lo | ((uint64_t)hi << 32);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++) {
+                const int r = lane + WARP * i;
+                const uint64_t s = base + r;
+                in[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
+                if (in[i] && rid) {  // the window's range id, written by the first range's pass
+                    in[i] = range_id_of(rid, s) == rid_value;
+                } else if (in[i]) {
+                    const uint32_t pt = window_part<K>(P, s, k, part_bits);
+                    in[i] = pt >= part_lo && pt < part_hi;
+                }
             }
         }
 #pragma unroll
@@ -641,7 +623,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   K *firsts, unsigned long long *first_count, uint64_t first_cap, uint64_t *hist, int hist_passes,
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket, uint64_t t_begin,
-                  uint64_t t_end, const uint64_t *rid, uint32_t rid_value, const int *lib_k, int tag_shift) {
+                  uint64_t t_end, const uint64_t *rid, uint32_t rid_value, const int *lib_k, int tag_shift,
+                  uint64_t *rid_out, const uint8_t *part_group) {
     const uint64_t all_tiles = (L.n_bases + P1_TILE - 1) / P1_TILE;
     if (t_end > all_tiles) t_end = all_tiles;
     if (t_begin >= t_end) return;
@@ -657,8 +640,14 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
         const size_t rsmem = sizeof(K) * P1_BUF * P1_WARPS * (emit_firsts ? 2 : 1) + 8 * PQ_CAP * P1_WARPS +
                              4 * 256 * hist_passes * (by_bucket && emit_firsts ? 2 : 1) +
                              sizeof(uint64_t) * (f.pat_mask + 1);
-        auto rk = emit_firsts ? (by_bucket ? k_pass1_range<K, true, true> : k_pass1_range<K, true, false>)
-                              : (by_bucket ? k_pass1_range<K, false, true> : k_pass1_range<K, false, false>);
+        auto rk = rid_out ? (emit_firsts ? (by_bucket ? k_pass1_range<K, true, true, true>
+                                                      : k_pass1_range<K, true, false, true>)
+                                         : (by_bucket ? k_pass1_range<K, false, true, true>
+                                                      : k_pass1_range<K, false, false, true>))
+                          : (emit_firsts ? (by_bucket ? k_pass1_range<K, true, true, false>
+                                                      : k_pass1_range<K, true, false, false>)
+                                         : (by_bucket ? k_pass1_range<K, false, true, false>
+                                                      : k_pass1_range<K, false, false, false>));
         cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk, P1_BLOCK, rsmem);
@@ -666,8 +655,8 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
         const uint64_t need = (tiles + P1_WARPS - 1) / P1_WARPS, cap = (uint64_t)c.sms * per_sm;
         rk<<<(int)(need < cap ? (need ? need : 1) : cap), P1_BLOCK, rsmem, c.stream>>>(
             P, V, L.n_bases, k, f.words, f.sector_shift, f.patterns, f.pat_mask, cand, cand_count, cand_cap, firsts,
-            first_count, first_cap, hist, hist_passes, part_bits, part_lo, part_hi, rid, rid_value, bg, t_begin, t_end,
-            err);
+            first_count, first_cap, hist, hist_passes, part_bits, part_lo, part_hi, rid, rid_value, rid_out,
+            part_group, bg, t_begin, t_end, err);
         return;
     }
     const int mode = (n_libs ? P1_BATCHED : 0) | (part_bits ? P1_PARTED : 0) | (by_bucket ? P1_BY_BUCKET : 0);
@@ -697,12 +686,13 @@ template void launch_pass1<uint64_t>(const LaunchCfg &, const PackLayout &, int,
                                      bool, const FilterGeom &, uint64_t *, unsigned long long *, uint64_t, uint64_t *,
                                      unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t, const uint64_t *, int,
                                      const uint64_t *, uint32_t *, const BucketGeom *, uint64_t, uint64_t,
-                                     const uint64_t *, uint32_t, const int *, int);
+                                     const uint64_t *, uint32_t, const int *, int, uint64_t *, const uint8_t *);
 template void launch_pass1<Key128>(const LaunchCfg &, const PackLayout &, int, const uint64_t *, const uint64_t *,
                                    bool, const FilterGeom &, Key128 *, unsigned long long *, uint64_t, Key128 *,
                                    unsigned long long *, uint64_t, uint64_t *, int, int, uint32_t, uint32_t,
                                    const uint64_t *, int, const uint64_t *, uint32_t *, const BucketGeom *, uint64_t,
-                                   uint64_t, const uint64_t *, uint32_t, const int *, int);
+                                   uint64_t, const uint64_t *, uint32_t, const int *, int, uint64_t *,
+                                   const uint8_t *);
 template void launch_filter_keys<uint64_t>(const LaunchCfg &, const uint64_t *, uint64_t, const FilterGeom &, int,
                                            uint8_t *);
 template void launch_filter_keys<Key128>(const LaunchCfg &, const Key128 *, uint64_t, const FilterGeom &, int,

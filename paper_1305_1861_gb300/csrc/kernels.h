@@ -83,16 +83,17 @@ void launch_pass1(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t
                   int part_bits, uint32_t part_lo, uint32_t part_hi, const uint64_t *lib_starts, int n_libs,
                   const uint64_t *lib_filter, uint32_t *err, const BucketGeom *bucket = nullptr, uint64_t t_begin = 0,
                   uint64_t t_end = ~0ull, const uint64_t *rid = nullptr, uint32_t rid_value = 0,
-                  const int *lib_k = nullptr, int tag_shift = 0);
-// (lib_k: mixed batches, each library's k (device, n_libs entries); the library tag then sits at bit tag_shift.)
+                  const int *lib_k = nullptr, int tag_shift = 0, uint64_t *rid_out = nullptr,
+                  const uint8_t *part_group = nullptr);
+// (lib_k: mixed batches, each library's k (device, n_libs entries); the library tag then sits at bit tag_shift.
+// rid_out: a key range's pass (rid == nullptr) that also writes every window's range id, part_group[part of
+// its key], for the passes of the other ranges; word w holds positions 32w .. 32w+31, bit j of its low
+// half the low bit of position 32w + j's id, bit j of its high half the high bit.)
 // 64-bit keys of a mixed batch's libraries with k <= 32: out[i] <- in[i].lo.
 void launch_narrow_keys(const LaunchCfg &c, const Key128 *in, uint64_t n, uint64_t *out);
-// Range id of every valid window (two bits per position as two bit planes per 32 positions,
-// range_id_words(n_bases) words): group[part].
+// Words of the range ids a key range's pass 1 writes (rid_out of launch_pass1): two bits per position, as
+// two bit planes per 32 positions.
 uint64_t range_id_words(uint64_t n_bases);
-template <class K>
-void launch_range_ids(const LaunchCfg &c, const PackLayout &L, int k, const uint64_t *P, const uint64_t *V,
-                      int part_bits, const uint8_t *part_group, uint64_t *rid);
 // a2+a3, filter-blocked form of pass 1 (one library, bucketed sort-and-compact): the valid windows (of
 // parts [part_lo, part_hi) when part_bits > 0) are binned by the top 8 bits of their hash into bin_keys
 // (room for every such window), then probed bin after bin, so the filter blocks being probed stay in L2;
