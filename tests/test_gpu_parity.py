@@ -389,3 +389,18 @@ def test_bulk_copied_sort_tiles_match_oracle(ctx, k, compact, genome):
     b, o = synth.reads_uniform(g, 901 + k, max(1, int(12 * genome / 120)), 120, 0.01)
     st = _check_count(ctx, b, o, k, 2, pkg.Params.default(compact=compact, sort_tile=4))
     assert st["n_candidates"] > 0
+
+
+def test_host_form_large_arrays_locked_for_their_copies(have_gpu):
+    """750 Mbase of host reads page-locked for their copies, which overlap pass 1 in chunks, and a fresh
+    result buffer first touched and locked: the oracle's result, twice (the second call reuses the
+    recycled result buffers)."""
+    import paper_1305_1861_gb300 as pkg
+
+    lib = synth.fly(seed=13, scale=0.25)
+    assert lib.bases.size > (512 << 20)
+    ok, oc, onw = oracle.count(lib.bases, lib.offsets, 31, 2)
+    for _ in range(2):
+        keys, counts, nw = pkg.turtle_count(lib.bases, lib.offsets, 31, 2, pkg.Params.default(host_transfer=1))
+        assert nw == onw and np.array_equal(keys, ok) and np.array_equal(counts.astype(np.uint64), oc)
+        del keys, counts
