@@ -398,11 +398,14 @@ template void launch_part_count<Key128>(const LaunchCfg &, const PackLayout &, i
 // computing any other key.
 constexpr int MAX_PARTS = 64;  // key-range parts of a library (part_bits <= 6)
 
-__device__ __forceinline__ uint32_t range_id_of(const uint64_t *__restrict__ rid, uint64_t s) {
-    const uint64_t w = __ldg(rid + (s >> 5));
-    const int j = (int)(s & 31);
-    return (uint32_t)(((w >> j) & 1u) | (((w >> (32 + j)) & 1u) << 1));
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned), and its group bookkeeping.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 uint64_t range_id_words(uint64_t n_bases) { return 4 * ((n_bases + P1_TILE - 1) / P1_TILE) + 4; }
 
@@ -457,6 +460,7 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
     uint32_t *s_fhist = s_hist + 256 * hist_passes;
     uint64_t *s_pat = reinterpret_cast<uint64_t *>(s_hist + n_hist);
     __shared__ uint8_t s_pg[MAX_PARTS];  // WRITE_RID: range of each key-range part
+    __shared__ __align__(16) uint64_t s_stage[P1_WARPS][2][6];  // each warp's next tiles' words
     for (uint32_t i = threadIdx.x; i <= pat_mask; i += P1_BLOCK) s_pat[i] = patterns[i];
     for (int i = threadIdx.x; i < n_hist; i += P1_BLOCK) s_hist[i] = 0;
     if (WRITE_RID)
@@ -528,9 +532,31 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
             }
         }
     };
-    for (uint64_t t = t_begin + (uint64_t)blockIdx.x * P1_WARPS + warp; t < t_end; t += (uint64_t)gridDim.x * P1_WARPS) {
+    // A warp's tiles are strided across the grid; each tile's two validity words and (with range ids) its
+    // four range-id words are copied to shared memory (cp.async, lanes 0-2) while the warp works on the
+    // previous tile, so a tile's test does not wait for its words and the copy overlaps the probes.
+    uint64_t(*stage)[6] = s_stage[warp];
+    const uint64_t stride = (uint64_t)gridDim.x * P1_WARPS;
+    auto fetch = [&](uint64_t tt, int b) {
+        if (tt < t_end) {
+            if (lane == 0) cp_async16(&stage[b][0], V + 2 * tt);
+            else if (rid && lane < 3) cp_async16(&stage[b][2 * lane], rid + 4 * tt + 2 * (lane - 1));
+        }
+        cp_async_commit();
+    };
+    uint64_t t = t_begin + (uint64_t)blockIdx.x * P1_WARPS + warp;
+    int sb = 0;
+    fetch(t, 0);
+    for (; t < t_end; t += stride, sb ^= 1) {
+        cp_async_wait_all();
+        __syncwarp();  // the tile's words have landed; every lane is done with the other buffer
         const uint64_t base = t * P1_TILE;
-        const uint64_t v0 = V[2 * t], v1 = V[2 * t + 1];
+        const uint64_t v0 = stage[sb][0], v1 = stage[sb][1];
+        uint64_t rw[P1_ILP];
+        if (rid)
+#pragma unroll
+            for (int i = 0; i < P1_ILP; i++) rw[i] = stage[sb][2 + i];
+        fetch(t + stride, sb ^ 1);
         bool in[P1_ILP];  // all four windows' tests first, so their loads overlap; then the ballots
         if (WRITE_RID) {  // the first range's pass: every window's range id, written for the later passes
             uint32_t g[P1_ILP];
@@ -554,7 +580,8 @@ __global__ void __launch_bounds__(P1_BLOCK) k_pass1_range(const uint64_t *__rest
                 const uint64_t s = base + r;
                 in[i] = s < n_pos && (((r < 64 ? v0 : v1) >> (r & 63)) & 1);
                 if (in[i] && rid) {  // the window's range id, written by the first range's pass
-                    in[i] = range_id_of(rid, s) == rid_value;
+                    const uint32_t id = (uint32_t)(((rw[i] >> lane) & 1u) | (((rw[i] >> (32 + lane)) & 1u) << 1));
+                    in[i] = id == rid_value;
                 } else if (in[i]) {
                     const uint32_t pt = window_part<K>(P, s, k, part_bits);
                     in[i] = pt >= part_lo && pt < part_hi;
