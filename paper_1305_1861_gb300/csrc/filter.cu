@@ -337,12 +337,16 @@ __device__ __forceinline__ uint32_t window_part<uint64_t>(const uint64_t *__rest
 template <>
 __device__ __forceinline__ uint32_t window_part<Key128>(const uint64_t *__restrict__ P, uint64_t s, int k,
                                                         int part_bits) {
-    const uint64_t e = s + (uint64_t)k - 32;  // k >= 33: the window's last 32 bases start at e >= s
+    const uint64_t e = s + (uint64_t)k - 16;  // k >= 33: the window's last 16 bases start at e > s
     const uint64_t a = stream_bits(__ldg(P + (s >> 5)), __ldg(P + (s >> 5) + 1), (int)(s & 31) << 1);
-    const uint64_t b = stream_bits(__ldg(P + (e >> 5)), __ldg(P + (e >> 5) + 1), (int)(e & 31) << 1);
-    const uint64_t vf = a >> 33, vr = (~rev2(b)) >> 33;  // top 31 bits of forward / reverse complement
-    const uint64_t v = vf < vr ? vf : vr;
-    return (uint32_t)((v * ((1ull << 32) - v)) >> (62 - part_bits));
+    const uint32_t b = (uint32_t)(stream_bits(__ldg(P + (e >> 5)), __ldg(P + (e >> 5) + 1), (int)(e & 31) << 1) >> 32);
+    // the reverse complement begins with the complements of the last 16 bases, last first
+    uint32_t r = __brev(b);
+    r = ((r >> 1) & 0x55555555u) | ((r & 0x55555555u) << 1);
+    const uint32_t vf = (uint32_t)(a >> 33), vr = (~r) >> 1;  // top 31 bits of forward / reverse complement
+    const uint32_t v = vf < vr ? vf : vr;
+    // (v (2^32 - v)) >> (62 - part_bits), from the high word of the 32 x 32-bit product (v < 2^31)
+    return v ? __umulhi(v, 0u - v) >> (30 - part_bits) : 0u;
 }
 
 // Number of valid windows in each of the 2^part_bits key-range parts (sizes the super-partitions and the

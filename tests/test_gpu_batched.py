@@ -85,6 +85,10 @@ def _mixed_jobs():
     jobs.append((np.concatenate([np.frombuffer(b"TTT", np.uint8), b]), o + 3, 45, 2))  # offsets start past 0
     b, o = brute.pack(["ACGTTGCA" * 16])  # exactly 128 bases, then the next library without a gap
     jobs.append((b, o, 31, 2))
+    b, o = brute.pack(["ACGTNACGGT" * 20, "TTTT", "N" * 40])  # k = 1 (single bases), reads of Ns only
+    jobs.append((b, o, 1, 2))
+    b, o = brute.pack(["N" * 300])  # no valid window at all
+    jobs.append((b, o, 21, 2))
     return jobs
 
 
