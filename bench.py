@@ -42,9 +42,9 @@ HEADLINE = "canonical k-mers/s and HBM roofline fraction at k=31/k=64; batched/s
 NCU_BYTES_PER_UNIT = {"k_pass1": 98.96, "k_onesweep": 16.0, "k_bucket_count": 8.66, "k_hash_insert": 221.8}
 # long-k (k = 64, 128-bit keys, four key ranges), from a capture at 1/50 scale whose ranges have the full-size
 # 1 GiB filter (profiles/k_pass1_range_longk_scale0.02.md): k_pass1_range per library window per launch (every
-# launch tests every window for its range; the mean of the first launch, which also writes the range ids, 17.90,
-# and the other three, 17.06), k_bucket_count per key of its range (the range's keys taken as W/4)
-NCU_BYTES_PER_UNIT_U128 = {"k_pass1_range": 17.27, "k_bucket_count": 17.09}
+# launch tests every window for its range; the mean of the first launch, which also writes the range ids, 17.87,
+# and the other three, 17.23-17.26), k_bucket_count per key of its range (the range's keys taken as W/4)
+NCU_BYTES_PER_UNIT_U128 = {"k_pass1_range": 17.40, "k_bucket_count": 17.09}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
