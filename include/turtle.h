@@ -89,7 +89,8 @@ typedef struct {
                                       copied in chunks that overlap pass 1, and smaller ones at once. Every
                                       copy reads the caller's memory directly, pageable or page-locked. */
     uint32_t sort_tile;            /* onesweep tile shape (256 threads): 0 = default (global sort: 32 keys per
-                                      thread, 16 for 128-bit keys, 2 CTAs/SM; bucket sort: 16, 4 CTAs/SM (8, 3/SM));
+                                      thread, 16 for 128-bit keys, 2 CTAs/SM; bucket sort: 16, 4 CTAs/SM for
+                                      64-bit keys, 16, 2 CTAs/SM for 128-bit keys);
                                       1 = 16, 4/SM (8, 3/SM); 2 = 24 (12), 2/SM; 3 = 32 (16), 2/SM;
                                       4 = persistent, 16 (8), 2/SM: each CTA's next tile is bulk-copied
                                       (cp.async.bulk) into shared memory while it sorts the current one */
